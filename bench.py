@@ -1,0 +1,395 @@
+#!/usr/bin/env python
+"""Benchmark: Deep Potential MD throughput (atom-steps/s) on GB300.
+
+Workload (default): 4,096 H2O = 12,288 atoms in a 49.7 A periodic box, the
+water model (se_a, rcut 6 A, rcut_smth 0.5 A, sel 46/92, embedding 25-50-100,
+M2 = 16, fitting 240-240-240, seeded FP64 weights), velocity Verlet at
+dt = 0.5 fs from 300 K, candidates with a 2 A skin rebuilt every 10 steps.
+One benchmark step = 10 MD steps = one rebuild period, so every step runs
+the whole path: candidate build, Algorithm 1, environment matrix, embedding,
+descriptor, fitting, backward, ProdForce/ProdVirial, energy sum, integrator.
+
+Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle
+on the same system instead (one MD step per benchmark step).
+Multi-GPU (--gpus N under torchrun): N independent replicas, one per GPU
+(the path has no exchange step on one box); value sums all ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "atom-steps/s"
+MD_PER_STEP = 10
+DT_FS = 0.5
+SKIN = 2.0
+T0 = 300.0
+L2_BYTES = 129 * 1024 * 1024
+
+# FP64 pipe peak of a GB300: 152 SMs x 2 FP64 FMA/clk/SM x 2 FLOP x 2.07 GHz.
+# The per-SM rate is the one that reproduces the nominal 1.25 TFLOP/s.
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+# DRAM bytes per launch of the dominant kernel from one ncu capture (see
+# profiles/); reported only while the kernel source is the one captured.
+TRAFFIC = {}
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--workload", default="water12288")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+def emb_row_flops(desc):
+    """Algorithmic FLOPs per real neighbour row (one embedding net pass)."""
+    e = list(desc["emb"])
+    g = 2 * e[0]
+    for a, b in zip(e[:-1], e[1:]):
+        g += 2 * a * b
+    return g
+
+
+def fit_atom_flops(desc):
+    M = desc["emb"][-1]
+    prev = desc["m2"] * M
+    f = 0
+    for w in desc["fit"]:
+        f += 2 * prev * w
+        prev = w
+    return f + 2 * prev
+
+
+def kernel_flops(desc, rows, natoms):
+    """FLOPs per launch of each kernel group, counted from the algorithm
+    (multiply-add = 2, tanh not counted):
+      embed_fwd: embedding GEMMs per real row + T = R~^T G (8 M per row)
+                 + D = T_<^T T (8 M2 M per atom)
+      embed_bwd: embedding recomputed + its s-tangent (2x GEMMs) + the two
+                 4 x M contractions with gT (16 M per row) + gT (16 M2 M per atom)
+      fit:       fitting forward + backward to the descriptor (2x forward)."""
+    M, m2 = desc["emb"][-1], desc["m2"]
+    g = emb_row_flops(desc)
+    return {
+        "embed_fwd": rows * (g + 8 * M) + natoms * 8 * m2 * M,
+        "embed_bwd": rows * (2 * g + 16 * M) + natoms * 16 * m2 * M,
+        "fit": natoms * 2 * fit_atom_flops(desc),
+    }
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+        if self.gpu_id is not None:
+            cmd += ["-i", str(self.gpu_id)]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def source_sha(fn):
+    with open(os.path.join(ROOT, "paper_2004_11658_gb300", "csrc", fn), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+# ------------------------------------------------------------ reference --
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    from oracle import oracle as O
+    from paper_2004_11658_gb300 import synth
+    w = synth.workload(args.workload)
+    desc = w["model"]
+    P = synth.model_params(desc, 0)
+    m = np.array(w["masses"])[w["types"]]
+    x, v = w["coords"].copy(), synth.maxwell_velocities(m, T0, seed=2)
+    F = None
+    N = len(x)
+    times = []
+    for k in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        x, v, F, th, _ = O.md(desc, P, x, v, w["types"], w["box"], w["masses"], DT_FS, 1,
+                              rebuild_every=MD_PER_STEP, skin=SKIN, force=F)
+        dt = time.perf_counter() - t0
+        if k >= args.warmup:
+            times.append(dt)
+    total = sum(times)
+    value = N * len(times) / total
+    cores = O.num_threads()
+    sample = (f"{args.steps} oracle velocity-Verlet steps of the {N}-atom system, each with a "
+              f"brute-force candidate rebuild, Algorithm 1 and the FP64 evaluation")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * total / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": args.workload, "atoms": N, "md_steps_per_step": 1,
+                                        "dt_fs": DT_FS, "skin": SKIN, "rebuild_every": MD_PER_STEP},
+        "cpu_baseline": {"value": value, "unit": METRIC, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def cpu_baseline(w, desc, P):
+    """The oracle as it stands on this host's cores: one candidate build
+    (amortised over the 10-step rebuild period) plus one Algorithm 1 +
+    evaluation, i.e. the cost of one MD step; two samples."""
+    from oracle import oracle as O
+    x, t, box = w["coords"], w["types"], w["box"]
+    N = len(x)
+    cap = O.default_cap(desc, box, N, SKIN)
+    t0 = time.perf_counter()
+    ncand, cand, _ = O.candidates(x, box, desc["rcut"] + SKIN, cap)
+    t_cand = time.perf_counter() - t0
+    ts = []
+    for _ in range(2):
+        t0 = time.perf_counter()
+        nl, _, _ = O.format_nlist(x, t, box, ncand, cand, desc["sel"], desc["rcut"])
+        O.eval_nlist(desc, P, x, t, box, nl)
+        ts.append(time.perf_counter() - t0)
+    per_step = min(ts) + t_cand / MD_PER_STEP
+    return {"value": N / per_step, "unit": METRIC, "cores": O.num_threads(), "kind": "oracle",
+            "sample": f"1 candidate build (/{MD_PER_STEP}) + 2 x (Algorithm 1 + FP64 evaluation) of the "
+                      f"{N}-atom system, best of 2; {per_step:.2f} s per MD step"}
+
+
+# ------------------------------------------------------------------ ours --
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+    from paper_2004_11658_gb300 import dp, synth
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    w = synth.workload(args.workload)
+    desc = w["model"]
+    P = synth.model_params(desc, 0)
+    m = np.array(w["masses"])[w["types"]]
+    v0 = synth.maxwell_velocities(m, T0, seed=2)
+    N = len(m)
+    model = dp.Model(desc, P)
+    ctx = dp.Context(model, N)
+    x = torch.tensor(w["coords"], dtype=torch.float64, device=dev)
+    v = torch.tensor(v0, dtype=torch.float64, device=dev)
+    t = torch.tensor(w["types"], dtype=torch.int32, device=dev)
+    th = torch.empty((MD_PER_STEP, 4), dtype=torch.float64, device=dev)
+    flush = torch.empty(2 * L2_BYTES, dtype=torch.uint8, device=dev)
+
+    def step():
+        dp.dp_md_step(ctx, x, v, t, w["box"], w["masses"], DT_FS, MD_PER_STEP, rebuild_every=MD_PER_STEP,
+                      skin=SKIN, thermo=th)
+
+    for _ in range(args.warmup):
+        step()
+    thermo0 = th.cpu().numpy().copy()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    barrier()
+    torch.cuda.synchronize()
+    ctx.set_timing(1)
+    launches0 = ctx.launches
+    gpu_id = None
+    try:
+        gpu_id = str(torch.cuda.get_device_properties(dev).uuid)
+        gpu_id = gpu_id if gpu_id.startswith("GPU-") else "GPU-" + gpu_id
+    except Exception:
+        gpu_id = None
+    sampler = ClockSampler(gpu_id)
+    sampler.start()
+    evs = []
+    thermo_all = []
+    for k in range(args.steps):
+        flush.fill_(k & 0xFF)                       # L2 flush, outside the timed events
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        step()
+        e1.record()
+        evs.append((e0, e1))
+        thermo_all.append(th.clone())
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop()
+    launches = ctx.launches - launches0
+    kt = ctx.kernel_times()
+    ctx.set_timing(0)
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    total_ms = sum(step_ms)
+    tmax = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    total_ms = float(tmax.item())
+    value = world * N * MD_PER_STEP * args.steps / (total_ms / 1000.0)
+
+    # rows actually evaluated (real neighbours, Algorithm 1 on the final positions)
+    nl, nr, _ = dp.dp_format_nlist(ctx, x, t, w["box"], check=False)
+    rows = int(nr.sum().item())
+    flops = kernel_flops(desc, rows, N)
+    groups = {g: {"ms": ms, "launches": n} for g, (ms, n) in kt.items()}
+    timed_groups = {g: d for g, d in groups.items() if d["launches"] > 0}
+    dom = max(timed_groups, key=lambda g: timed_groups[g]["ms"])
+    roof = None
+    if dom in flops:
+        per_launch_s = groups[dom]["ms"] / groups[dom]["launches"] / 1000.0
+        achieved = flops[dom] / per_launch_s / 1e12
+        tr = TRAFFIC.get(dom)
+        traffic = tr["bytes_per_launch"] if tr and tr.get("src_sha") == source_sha(tr["file"]) else None
+        roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
+                "peak_source": "FP64 pipe: 152 SMs x 2 FMA/clk x 2 FLOP x 2.07 GHz (nominal 1.25 TFLOP/s)",
+                "flops_per_launch": flops[dom], "rows_per_launch": rows}
+    th_all = torch.stack(thermo_all).cpu().numpy().reshape(-1, 4)
+    etot = th_all[:, 0] + th_all[:, 1]
+
+    # end to end: host buffers in pinned memory, copies inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        xh = x.cpu().pin_memory()
+        vh = v.cpu().pin_memory()
+        thh = torch.empty_like(th, device="cpu").pin_memory()
+        th_h_bytes = thh.numel() * 8
+        th_dev_t = t.cpu().pin_memory()
+        ev = []
+        for k in range(args.steps):
+            flush.fill_(k & 0xFF)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            x.copy_(xh, non_blocking=True)
+            v.copy_(vh, non_blocking=True)
+            t.copy_(th_dev_t, non_blocking=True)
+            step()
+            xh.copy_(x, non_blocking=True)
+            vh.copy_(v, non_blocking=True)
+            thh.copy_(th, non_blocking=True)
+            b.record()
+            ev.append((a, b))
+        torch.cuda.synchronize()
+        e_ms = sum(a.elapsed_time(b) for a, b in ev)
+        te = torch.tensor([e_ms], dtype=torch.float64, device=dev)
+        if world > 1:
+            dist.all_reduce(te, op=dist.ReduceOp.MAX)
+        e_ms = float(te.item())
+        e2e = {"value": world * N * MD_PER_STEP * args.steps / (e_ms / 1000.0), "unit": METRIC,
+               "h2d_bytes_per_step": int(2 * N * 3 * 8 + N * 4),
+               "d2h_bytes_per_step": int(2 * N * 3 * 8 + th_h_bytes)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(w, desc, P)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "atoms": N, "md_steps_per_step": MD_PER_STEP, "dt_fs": DT_FS,
+                       "skin": SKIN, "rebuild_every": MD_PER_STEP, "T0_K": T0,
+                       "model": "se_a water 25-50-100 / M2 16 / fit 240x3, seeded FP64 weights",
+                       "l2": "flushed between steps (256 MB write)",
+                       "parallelism": f"replicas x{world}"},
+            "gpu_launches": launches,
+            "roofline": roof,
+            "kernels_ms_per_step": {g: d["ms"] / args.steps for g, d in timed_groups.items()},
+            "nve": {"etot_first": float(etot[0]), "etot_last": float(etot[-1]),
+                    "max_abs_drift_eV_per_atom": float(np.abs(etot - etot[0]).max() / N),
+                    "T_last_K": float(th_all[-1, 2])},
+            "clocks": clocks,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    try:
+        return run_ours(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,189 @@
+/*
+ * dp.h -- C ABI of the GB300 Deep Potential hot path.
+ *
+ * Method: Lu et al., "86 PFLOPS Deep Potential Molecular Dynamics simulation
+ * of 100 million atoms with ab initio accuracy" (arXiv 2004.11658).  One call
+ * of dp_eval computes the energy E = sum_i E_i (Sec. 2, Eq. ei), the forces
+ * F_i = -grad_{r_i} E (Remark 2, Eq. dp-force) and the virial of a
+ * smooth-edition Deep Potential model on one GPU; dp_md_step advances
+ * velocity-Verlet molecular dynamics (Sec. 4).
+ *
+ * Conventions (all entry points):
+ *   - Units: Angstrom, eV, fs, amu, K.
+ *   - Arrays named "device" are caller-owned CUDA device pointers, contiguous,
+ *     row-major; the library never frees them.  Arrays named "host" are
+ *     caller-owned host memory, read during the call only.
+ *   - Coordinates are [N][3] float64, types [N] int32 in [0, ntypes).
+ *   - box is host double[9], a row-major 3x3 cell; only orthorhombic
+ *     (diagonal) cells are supported, others give DP_ERR_BOX.
+ *   - Work is enqueued on the stream given to dp_ctx_create.  With sync mode
+ *     on (the default) each call ends by reading a 4-byte device status word,
+ *     which synchronises that stream; with sync mode off the call returns
+ *     after enqueueing and device-side conditions are read by dp_ctx_status.
+ *   - No C++ exception crosses this boundary.  On error a message is kept in
+ *     thread-local storage (dp_last_error).
+ *   - A context is not thread safe: use one context per host thread.
+ */
+#ifndef DP_GB300_H
+#define DP_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t dp_status;
+
+#define DP_OK                 0
+#define DP_ERR_ARG           -1   /* bad pointer, size or descriptor           */
+#define DP_ERR_BOX           -2   /* non-orthorhombic or too small cell        */
+#define DP_ERR_SEL_OVERFLOW  -3   /* a neighbour within rcut did not fit sel;
+                                     results are written for the truncated list */
+#define DP_ERR_NLIST_STALE   -4   /* an atom moved more than skin/2 since the
+                                     last candidate build; results are written  */
+#define DP_ERR_NONFINITE     -5   /* NaN/Inf in the energy or virial           */
+#define DP_ERR_FILE          -6   /* model file missing, truncated or corrupt  */
+#define DP_ERR_CUDA          -7   /* a CUDA call failed                        */
+#define DP_ERR_UNSUPPORTED   -8   /* widths or type counts beyond the limits   */
+#define DP_ERR_CAPACITY      -9   /* an atom had more candidates than cand_cap */
+#define DP_ERR_NOMEM        -10   /* device allocation failed                  */
+#define DP_ERR_TYPE         -11   /* a type id outside [0, ntypes)             */
+
+#define DP_MAX_TYPES   8
+#define DP_MAX_LAYERS  4
+
+/* Model hyper-parameters (Sec. 2; the paper's models are described in Sec. 4).
+ *   sel[a]      : neighbour slots for type a; N_m = sum(sel) (Sec. 2, Sec. 3.2.2)
+ *   emb[0..n_emb): embedding widths s_1..s_m, s_m = M (Eqs. embedding-first/-rest)
+ *   m2          : M^<, the columns of G kept in G^< (Eq. descrpt)
+ *   fit[0..n_fit): hidden widths of the fitting net (Eqs. fitting, fitting-detail)
+ *   desc_scale_nm: 1 -> the descriptor uses T = R~^T G / N_m; 0 -> unscaled
+ *   rcut, rcut_smth: the gate w(r) is 1 below rcut_smth, 0 from rcut on.
+ * Limits: ntypes <= 8, 1 <= n_emb <= 4 with widths <= 128, n_fit <= 4 with
+ * widths <= 256, m2 <= M, N_m <= 1024. */
+typedef struct {
+    int32_t ntypes;
+    int32_t sel[DP_MAX_TYPES];
+    int32_t n_emb;
+    int32_t emb[DP_MAX_LAYERS];
+    int32_t m2;
+    int32_t n_fit;
+    int32_t fit[DP_MAX_LAYERS];
+    int32_t desc_scale_nm;
+    int32_t reserved;
+    double rcut;
+    double rcut_smth;
+} dp_model_desc;
+
+typedef struct dp_model dp_model;
+typedef struct dp_ctx dp_ctx;
+
+/* Precision modes of a context. */
+#define DP_PREC_FP64  0   /* every step in float64 */
+
+/* Thread-local text of the last error (never NULL). */
+const char *dp_last_error(void);
+/* Static text for a status code. */
+const char *dp_status_string(dp_status s);
+
+/* Number of float64 parameters of a model with this descriptor, or -1 if the
+ * descriptor is invalid.  Flat layout: for every ordered type pair (a, b),
+ * a-major, the embedding net G^{a,b} (Remark 1): W0[s1], b0[s1], then per
+ * layer l W[s_l][s_{l+1}] (input index first), b[s_{l+1}]; then for every
+ * type a the fitting net N_a: W1[m2*M][f1], b1[f1], W_l[f_{l-1}][f_l], b_l[f_l],
+ * w_out[f_last], b_out. */
+int64_t dp_model_nparams(const dp_model_desc *desc);
+
+/* Create a model from a host descriptor and host parameters (copied to the
+ * current CUDA device).  *out is owned by the caller; free with dp_model_free. */
+dp_status dp_model_create(const dp_model_desc *desc, const double *params, int64_t nparams,
+                          dp_model **out);
+/* Load / save the binary model file: "DPGB300M" magic, uint32 version 1,
+ * the descriptor fields as little-endian int32/float64 in declaration order,
+ * int64 nparams, nparams float64.  DP_ERR_FILE on a short or corrupt file. */
+dp_status dp_model_load(const char *path, dp_model **out);
+dp_status dp_model_save(const dp_model *model, const char *path);
+void dp_model_free(dp_model *model);
+
+/* Create a context for up to natoms_max atoms.  cand_cap is the capacity of
+ * one atom's candidate list (neighbours within rcut + skin); 0 picks a
+ * default from the density at the first dp_build_nlist.  stream is a
+ * cudaStream_t (NULL = legacy default stream).  The context owns all scratch
+ * memory of the path (O(natoms_max * N_m) words); it does not own the model,
+ * which must outlive it. */
+dp_status dp_ctx_create(const dp_model *model, int64_t natoms_max, int32_t cand_cap,
+                        int32_t precision, void *stream, dp_ctx **out);
+void dp_ctx_free(dp_ctx *ctx);
+/* sync = 1 (default): every call reads the device status word at its end.
+ * sync = 0: calls only enqueue; dp_ctx_status reads the accumulated word. */
+dp_status dp_ctx_set_sync(dp_ctx *ctx, int32_t sync);
+dp_status dp_ctx_status(dp_ctx *ctx);
+/* Kernels launched through this context since creation. */
+int64_t dp_ctx_launches(const dp_ctx *ctx);
+
+/* Per-kernel-group device time, measured with CUDA events recorded on the
+ * context's stream around every launch while timing is on.  Groups:
+ * 0 build (cell list + candidates + type order), 1 format (Algorithm 1),
+ * 2 embed_fwd, 3 fit, 4 embed_bwd, 5 force (ProdForce gather), 6 reduce
+ * (energy/virial sums), 7 md (integrator and thermo kernels). */
+#define DP_KERNEL_GROUPS 8
+/* on = 1 starts timing and clears the accumulators; on = 0 stops it. */
+dp_status dp_ctx_set_timing(dp_ctx *ctx, int32_t on);
+/* Accumulated milliseconds ms[8] and launch counts launches[8] (either may
+ * be NULL); synchronises the context's stream. */
+dp_status dp_ctx_kernel_times(dp_ctx *ctx, double *ms, int64_t *launches);
+/* Static name of a kernel group ("build", "format", ...), or "?". */
+const char *dp_kernel_group_name(int32_t group);
+
+/* Cell-list neighbour candidates (the neighbour list with a buffer of width
+ * skin, Sec. 3.2.2 and Sec. 4): for every atom, all j != i with minimum-image
+ * |r_ij| <= rcut + skin.  coords, types: device.  Also records the reference
+ * positions for the staleness check and the type-sorted atom order.
+ * Requires box edges >= 2 (rcut + skin).  Enqueued; see sync mode. */
+dp_status dp_build_nlist(dp_ctx *ctx, const double *coords, const int32_t *types,
+                         const double box[9], int64_t N, double skin);
+
+/* Algorithm 1 (formatted neighbour list) from the current coordinates and the
+ * candidates of the last dp_build_nlist.  Writes nlist[N][N_m] (int32 atom
+ * indices, -1 = padding; type blocks of sel[a] slots in type order, each
+ * sorted by (floor(|r_ij| * 1e8), j)) and nreal[N][ntypes] (1 + the last slot
+ * of the block with |r_ij| < rcut, 0 if none).  Either output may be NULL.
+ * Device pointers.  DP_ERR_SEL_OVERFLOW if a neighbour within rcut was cut. */
+dp_status dp_format_nlist(dp_ctx *ctx, const double *coords, const int32_t *types,
+                          const double box[9], int64_t N, int32_t *nlist, int32_t *nreal);
+
+/* Energy, forces and virial (Sec. 2; Algorithms 1 and 2; Eqs. embedding,
+ * descrpt, fitting; Remark 2).  energy: device double[1]; force: device
+ * [N][3]; virial: device double[9], Xi[a][b] = -sum_{i,j} r_ij[a] dE_i/dr_ij[b]
+ * (= sum_i r_i[a] F_i[b] for an isolated cluster); atom_energy: device [N] or
+ * NULL.  Uses the candidates of the last dp_build_nlist for the same N (built
+ * with skin 0 when there is none). */
+dp_status dp_eval(dp_ctx *ctx, const double *coords, const int32_t *types, const double box[9],
+                  int64_t N, double *energy, double *force, double *virial,
+                  double *atom_energy);
+
+/* nsteps of velocity-Verlet NVE (Sec. 4): v += F/m dt/2; x += v dt; wrap
+ * into the cell; rebuild the candidates when the context's MD step counter
+ * is a multiple of rebuild_every (and at the first step of a context);
+ * Algorithm 1 + evaluation; v += F/m dt/2.  coords, vel: device [N][3],
+ * updated in place.  mass_per_type: host [ntypes] (amu).  thermo: device
+ * [nsteps][4] = (E_pot, E_kin, T, P) per step (eV, eV, K, eV/A^3,
+ * P = (2 E_kin + tr Xi)/(3V), T with 3N-3 degrees of freedom) or NULL.
+ * The force of the current coordinates is kept in the context between calls
+ * (computed first when absent).  DP_ERR_NLIST_STALE if an atom moved more
+ * than skin/2 from its reference position between rebuilds. */
+dp_status dp_md_step(dp_ctx *ctx, double *coords, double *vel, const int32_t *types,
+                     const double box[9], const double *mass_per_type, int64_t N,
+                     double dt_fs, int32_t nsteps, int32_t rebuild_every, double skin,
+                     double *thermo);
+/* Copy the context's MD force ([N][3]) to a device buffer. */
+dp_status dp_md_get_force(dp_ctx *ctx, double *force, int64_t N);
+/* Forget the MD force and step counter (next dp_md_step recomputes both). */
+dp_status dp_md_reset(dp_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DP_GB300_H */

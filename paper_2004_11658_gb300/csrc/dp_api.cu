@@ -1,0 +1,822 @@
+// dp_api.cu -- host runtime behind the C ABI of include/dp.h: model and
+// context objects, scratch memory, argument checks, the launch sequence of one
+// evaluation and of velocity-Verlet MD, and the device status word.
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "dp_internal.cuh"
+
+namespace {
+
+thread_local std::string g_last_error = "";
+
+dp_status fail(dp_status s, const std::string &msg)
+{
+    g_last_error = msg;
+    return s;
+}
+
+dp_status cuda_fail(cudaError_t e, const char *where)
+{
+    return fail(DP_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define DP_CUDA(call, where)                                  \
+    do {                                                      \
+        cudaError_t e_ = (call);                              \
+        if (e_ != cudaSuccess) return cuda_fail(e_, where);   \
+    } while (0)
+
+const double kAccConv = 9.648533212e-3;  // (eV/A/amu) -> A/fs^2
+
+int64_t desc_nparams(const dp_model_desc &d)
+{
+    const int T = d.ntypes;
+    int64_t emb = 0;
+    int prev = 1;
+    for (int l = 0; l < d.n_emb; ++l) {
+        emb += (int64_t)prev * d.emb[l] + d.emb[l];
+        prev = d.emb[l];
+    }
+    const int M = d.emb[d.n_emb - 1];
+    int64_t fit = 0;
+    prev = d.m2 * M;
+    for (int l = 0; l < d.n_fit; ++l) {
+        fit += (int64_t)prev * d.fit[l] + d.fit[l];
+        prev = d.fit[l];
+    }
+    fit += prev + 1;
+    return (int64_t)T * T * emb + (int64_t)T * fit;
+}
+
+dp_status check_desc(const dp_model_desc *d)
+{
+    if (!d) return fail(DP_ERR_ARG, "descriptor is NULL");
+    if (d->ntypes < 1 || d->ntypes > DP_MAX_TYPES) return fail(DP_ERR_UNSUPPORTED, "ntypes must be in [1, 8]");
+    int nm = 0;
+    for (int a = 0; a < d->ntypes; ++a) {
+        if (d->sel[a] < 0) return fail(DP_ERR_ARG, "sel must be >= 0");
+        nm += d->sel[a];
+    }
+    if (nm < 1 || nm > DP_MAX_NM) return fail(DP_ERR_UNSUPPORTED, "sum(sel) must be in [1, 1024]");
+    if (d->n_emb < 1 || d->n_emb > DP_MAX_LAYERS) return fail(DP_ERR_UNSUPPORTED, "n_emb must be in [1, 4]");
+    for (int l = 0; l < d->n_emb; ++l)
+        if (d->emb[l] < 1 || d->emb[l] > DP_MAX_EMB_W)
+            return fail(DP_ERR_UNSUPPORTED, "embedding widths must be in [1, 128]");
+    const int M = d->emb[d->n_emb - 1];
+    if (d->m2 < 1 || d->m2 > M) return fail(DP_ERR_ARG, "m2 must be in [1, M]");
+    if (d->n_fit < 1 || d->n_fit > DP_MAX_LAYERS) return fail(DP_ERR_UNSUPPORTED, "n_fit must be in [1, 4]");
+    for (int l = 0; l < d->n_fit; ++l)
+        if (d->fit[l] < 1 || d->fit[l] > DP_MAX_FIT_W)
+            return fail(DP_ERR_UNSUPPORTED, "fitting widths must be in [1, 256]");
+    if (d->fit[0] == d->m2 * M || d->fit[0] == 2 * d->m2 * M)
+        return fail(DP_ERR_UNSUPPORTED, "a skip connection on the first fitting layer is not supported");
+    if (d->desc_scale_nm != 0 && d->desc_scale_nm != 1) return fail(DP_ERR_ARG, "desc_scale_nm must be 0 or 1");
+    if (!(d->rcut > 0.0) || !(d->rcut_smth >= 0.0) || !(d->rcut_smth < d->rcut))
+        return fail(DP_ERR_ARG, "need 0 <= rcut_smth < rcut");
+    return DP_OK;
+}
+
+}  // namespace
+
+struct dp_model {
+    dp_model_desc desc;
+    int64_t nparams;
+    double *d_params;
+    double *h_params;
+    DevModel dev;
+};
+
+struct dp_ctx {
+    const dp_model *model;
+    DevModel m;
+    int64_t natoms_max;
+    int32_t cap_fixed, cap;
+    int32_t precision;
+    cudaStream_t stream;
+    int num_sms;
+    int sync;
+    int64_t launches;
+    // device status word + pinned host mirror
+    int32_t *d_status;
+    int32_t *h_status;
+    // neighbour candidates
+    NlistBuffers nb;
+    int64_t ncell_cap;
+    int nc[3];
+    bool nlist_valid;
+    int64_t nlist_N;
+    double skin;
+    FormatBuffers fb;
+    EvalBuffers eb;
+    double *d_energy, *d_virial;
+    // MD state
+    double *md_force, *ke_part, *d_inv_mass_conv, *d_mass, *h_mass_stage;
+    double last_mass[DP_MAX_TYPES];
+    bool md_force_valid;
+    int64_t md_N;
+    int64_t md_step;
+    // kernel-group timing
+    bool timing;
+    std::vector<cudaEvent_t> events;
+    size_t events_used;
+    struct Span {
+        size_t a, b;
+        int group;
+    };
+    std::vector<Span> spans;
+    double group_ms[DP_KERNEL_GROUPS];
+    int64_t group_launches[DP_KERNEL_GROUPS];
+};
+
+namespace {
+
+template <class T>
+dp_status dev_alloc(T **p, size_t count, const char *what)
+{
+    *p = nullptr;
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc((void **)p, sizeof(T) * count);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        cudaGetLastError();
+        return fail(DP_ERR_NOMEM, std::string("cudaMalloc failed for ") + what);
+    }
+    return DP_OK;
+}
+
+void dev_free(void *p)
+{
+    if (p) cudaFree(p);
+}
+
+DevModel make_devmodel(const dp_model_desc &d, const double *dparams)
+{
+    DevModel m;
+    std::memset(&m, 0, sizeof(m));
+    m.ntypes = d.ntypes;
+    m.nm = 0;
+    for (int a = 0; a < d.ntypes; ++a) {
+        m.sel[a] = d.sel[a];
+        m.sel_off[a] = m.nm;
+        m.nm += d.sel[a];
+    }
+    m.n_emb = d.n_emb;
+    for (int l = 0; l < d.n_emb; ++l) m.emb[l] = d.emb[l];
+    m.M = d.emb[d.n_emb - 1];
+    m.m2 = d.m2;
+    m.n_fit = d.n_fit;
+    for (int l = 0; l < d.n_fit; ++l) m.fit[l] = d.fit[l];
+    m.rcut = d.rcut;
+    m.rcut_smth = d.rcut_smth;
+    m.desc_scale = d.desc_scale_nm ? 1.0 / (double)m.nm : 1.0;
+    m.params = dparams;
+    int64_t net = 2 * d.emb[0];
+    for (int l = 1; l < d.n_emb; ++l) net += (int64_t)d.emb[l - 1] * d.emb[l] + d.emb[l];
+    m.emb_net_size = (int)net;
+    int64_t off = 0;
+    for (int a = 0; a < d.ntypes; ++a)
+        for (int b = 0; b < d.ntypes; ++b) {
+            m.emb_base[a * d.ntypes + b] = off;
+            off += net;
+        }
+    for (int a = 0; a < d.ntypes; ++a) {
+        m.fit_base[a] = off;
+        int prev = d.m2 * m.M;
+        for (int l = 0; l < d.n_fit; ++l) {
+            off += (int64_t)prev * d.fit[l] + d.fit[l];
+            prev = d.fit[l];
+        }
+        off += prev + 1;
+    }
+    return m;
+}
+
+dp_status read_box(const double *box, Box3 &b)
+{
+    if (!box) return fail(DP_ERR_ARG, "box is NULL");
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c)
+            if (r != c && box[3 * r + c] != 0.0)
+                return fail(DP_ERR_BOX, "only orthorhombic (diagonal) cells are supported");
+    for (int a = 0; a < 3; ++a) {
+        b.L[a] = box[4 * a];
+        if (!(b.L[a] > 0.0) || !std::isfinite(b.L[a])) return fail(DP_ERR_BOX, "cell edges must be positive");
+    }
+    return DP_OK;
+}
+
+dp_status finish(dp_ctx *c)
+{
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+    if (!c->sync) return DP_OK;
+    return dp_ctx_status(c);
+}
+
+enum { G_BUILD = 0, G_FORMAT, G_EMBED_FWD, G_FIT, G_EMBED_BWD, G_FORCE, G_REDUCE, G_MD };
+
+dp_status flush_spans(dp_ctx *c)
+{
+    if (c->spans.empty()) return DP_OK;
+    DP_CUDA(cudaStreamSynchronize(c->stream), "timing");
+    for (const auto &sp : c->spans) {
+        float ms = 0.f;
+        DP_CUDA(cudaEventElapsedTime(&ms, c->events[sp.a], c->events[sp.b]), "timing");
+        c->group_ms[sp.group] += ms;
+    }
+    c->spans.clear();
+    c->events_used = 0;
+    return DP_OK;
+}
+
+// Records an event before a launch group and another after it (timing on only).
+struct GroupTimer {
+    dp_ctx *c;
+    int group;
+    size_t a;
+    int64_t before;
+    GroupTimer(dp_ctx *c_, int g) : c(c_), group(g), a(0), before(c_->launches)
+    {
+        if (c->timing) a = next_event();
+    }
+    size_t next_event()
+    {
+        if (c->events_used + 2 > 65536) flush_spans(c);
+        if (c->events_used >= c->events.size()) {
+            cudaEvent_t e;
+            cudaEventCreate(&e);
+            c->events.push_back(e);
+        }
+        size_t k = c->events_used++;
+        cudaEventRecord(c->events[k], c->stream);
+        return k;
+    }
+    ~GroupTimer()
+    {
+        c->group_launches[group] += c->launches - before;
+        if (c->timing) c->spans.push_back({a, next_event(), group});
+    }
+};
+
+int default_cap(const dp_ctx *c, const Box3 &b, int64_t N, double rlist)
+{
+    const double vol = b.L[0] * b.L[1] * b.L[2];
+    const double rho = (double)N / vol;
+    const double expect = rho * 4.0 / 3.0 * M_PI * rlist * rlist * rlist;
+    int cap = (int)std::ceil((1.5 * expect + 64.0) / 32.0) * 32;
+    if (cap > (int)N) cap = (int)((N + 31) / 32 * 32);
+    if (cap < 32) cap = 32;
+    if (cap > 1024) cap = 1024;
+    (void)c;
+    return cap;
+}
+
+dp_status check_common(dp_ctx *c, const double *coords, const int32_t *types, int64_t N)
+{
+    if (!c) return fail(DP_ERR_ARG, "context is NULL");
+    if (!coords || !types) return fail(DP_ERR_ARG, "coords/types is NULL");
+    if (N < 1 || N > c->natoms_max) return fail(DP_ERR_ARG, "N must be in [1, natoms_max]");
+    return DP_OK;
+}
+
+dp_status do_build(dp_ctx *c, const double *coords, const int32_t *types, const Box3 &b, int64_t N,
+                   double skin)
+{
+    if (!(skin >= 0.0)) return fail(DP_ERR_ARG, "skin must be >= 0");
+    const double rlist = c->m.rcut + skin;
+    for (int a = 0; a < 3; ++a)
+        if (b.L[a] < 2.0 * rlist)
+            return fail(DP_ERR_BOX, "every cell edge must be >= 2 (rcut + skin)");
+    // candidate capacity
+    int cap = c->cap_fixed > 0 ? c->cap_fixed : default_cap(c, b, N, rlist);
+    if (cap > c->cap || c->nb.cand == nullptr) {
+        dev_free(c->nb.cand);
+        c->nb.cand = nullptr;
+        dp_status s = dev_alloc(&c->nb.cand, (size_t)c->natoms_max * cap, "candidates");
+        if (s) return s;
+        c->cap = cap;
+    }
+    // cells
+    int nc[3];
+    int64_t ncell = 1;
+    for (int a = 0; a < 3; ++a) {
+        nc[a] = (int)std::floor(b.L[a] / rlist);
+        if (nc[a] < 1) nc[a] = 1;
+        if (nc[a] > 1024) nc[a] = 1024;
+        ncell *= nc[a];
+    }
+    if (nc[0] >= 3 && nc[1] >= 3 && nc[2] >= 3 && ncell > c->ncell_cap) {
+        dev_free(c->nb.cell_count);
+        dev_free(c->nb.cell_start);
+        dev_free(c->nb.cell_cursor);
+        c->nb.cell_count = c->nb.cell_start = c->nb.cell_cursor = nullptr;
+        dp_status s;
+        if ((s = dev_alloc(&c->nb.cell_count, (size_t)ncell, "cells"))) return s;
+        if ((s = dev_alloc(&c->nb.cell_start, (size_t)ncell + 1, "cells"))) return s;
+        if ((s = dev_alloc(&c->nb.cell_cursor, (size_t)ncell, "cells"))) return s;
+        c->ncell_cap = ncell;
+    }
+    for (int a = 0; a < 3; ++a) c->nc[a] = nc[a];
+    GroupTimer tm(c, G_BUILD);
+    cudaError_t e = dp_launch_build(c->stream, c->m, coords, types, b, (int)N, rlist, c->cap, nc, c->nb,
+                                    c->d_status, &c->launches);
+    if (e != cudaSuccess) return cuda_fail(e, "dp_build_nlist");
+    c->nlist_valid = true;
+    c->nlist_N = N;
+    c->skin = skin;
+    return DP_OK;
+}
+
+dp_status enqueue_format(dp_ctx *c, const double *coords, const int32_t *types, const Box3 &b, int64_t N)
+{
+    GroupTimer tm(c, G_FORMAT);
+    cudaError_t e = dp_launch_format(c->stream, c->m, coords, types, b, (int)N, c->cap, c->skin, c->nb,
+                                     c->fb, c->d_status, &c->launches);
+    if (e != cudaSuccess) return cuda_fail(e, "format");
+    return DP_OK;
+}
+
+dp_status enqueue_eval(dp_ctx *c, const double *coords, const int32_t *types, const Box3 &b, int64_t N,
+                       double *energy, double *force, double *virial, double *atom_energy)
+{
+    dp_status s = enqueue_format(c, coords, types, b, N);
+    if (s) return s;
+    cudaError_t e;
+    {
+        GroupTimer tm(c, G_EMBED_FWD);
+        if ((e = dp_launch_embed_fwd(c->stream, c->m, coords, types, b, (int)N, c->fb, c->nb, c->eb, c->num_sms,
+                                     &c->launches)) != cudaSuccess)
+            return cuda_fail(e, "embed_fwd");
+    }
+    {
+        GroupTimer tm(c, G_FIT);
+        if ((e = dp_launch_fit(c->stream, c->m, (int)N, c->nb, c->eb, &c->launches)) != cudaSuccess)
+            return cuda_fail(e, "fit");
+    }
+    {
+        GroupTimer tm(c, G_EMBED_BWD);
+        if ((e = dp_launch_embed_bwd(c->stream, c->m, coords, types, b, (int)N, c->fb, c->nb, c->eb, c->num_sms,
+                                     &c->launches)) != cudaSuccess)
+            return cuda_fail(e, "embed_bwd");
+    }
+    {
+        GroupTimer tm(c, G_FORCE);
+        if ((e = dp_launch_force(c->stream, c->m, coords, types, b, (int)N, c->cap, c->nb, c->fb, c->eb, force,
+                                 &c->launches)) != cudaSuccess)
+            return cuda_fail(e, "force");
+    }
+    {
+        GroupTimer tm(c, G_REDUCE);
+        if ((e = dp_launch_reduce(c->stream, (int)N, c->eb, energy, virial, atom_energy, c->d_status,
+                                  &c->launches)) != cudaSuccess)
+            return cuda_fail(e, "reduce");
+    }
+    return DP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *dp_last_error(void) { return g_last_error.c_str(); }
+
+const char *dp_status_string(dp_status s)
+{
+    switch (s) {
+    case DP_OK: return "ok";
+    case DP_ERR_ARG: return "invalid argument";
+    case DP_ERR_BOX: return "unsupported or too small cell";
+    case DP_ERR_SEL_OVERFLOW: return "a neighbour within rcut did not fit sel";
+    case DP_ERR_NLIST_STALE: return "neighbour candidates are stale (moved > skin/2)";
+    case DP_ERR_NONFINITE: return "non-finite energy or virial";
+    case DP_ERR_FILE: return "model file error";
+    case DP_ERR_CUDA: return "CUDA error";
+    case DP_ERR_UNSUPPORTED: return "unsupported model shape";
+    case DP_ERR_CAPACITY: return "candidate capacity exceeded";
+    case DP_ERR_NOMEM: return "device allocation failed";
+    case DP_ERR_TYPE: return "atom type out of range";
+    default: return "unknown status";
+    }
+}
+
+int64_t dp_model_nparams(const dp_model_desc *desc)
+{
+    if (check_desc(desc) != DP_OK) return -1;
+    return desc_nparams(*desc);
+}
+
+dp_status dp_model_create(const dp_model_desc *desc, const double *params, int64_t nparams, dp_model **out)
+{
+    if (!out) return fail(DP_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    dp_status s = check_desc(desc);
+    if (s) return s;
+    if (!params) return fail(DP_ERR_ARG, "params is NULL");
+    const int64_t need = desc_nparams(*desc);
+    if (nparams != need) return fail(DP_ERR_ARG, "nparams does not match the descriptor (" + std::to_string(need) + ")");
+    dp_model *m = new (std::nothrow) dp_model();
+    if (!m) return fail(DP_ERR_NOMEM, "host allocation failed");
+    m->desc = *desc;
+    m->nparams = need;
+    m->h_params = (double *)std::malloc(sizeof(double) * need);
+    if (!m->h_params) {
+        delete m;
+        return fail(DP_ERR_NOMEM, "host allocation failed");
+    }
+    std::memcpy(m->h_params, params, sizeof(double) * need);
+    for (int64_t q = 0; q < need; ++q)
+        if (!std::isfinite(params[q])) {
+            std::free(m->h_params);
+            delete m;
+            return fail(DP_ERR_ARG, "non-finite parameter");
+        }
+    if ((s = dev_alloc(&m->d_params, (size_t)need, "params"))) {
+        std::free(m->h_params);
+        delete m;
+        return s;
+    }
+    cudaError_t e = cudaMemcpy(m->d_params, params, sizeof(double) * need, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(m->d_params);
+        std::free(m->h_params);
+        delete m;
+        return cuda_fail(e, "dp_model_create");
+    }
+    m->dev = make_devmodel(*desc, m->d_params);
+    *out = m;
+    return DP_OK;
+}
+
+void dp_model_free(dp_model *m)
+{
+    if (!m) return;
+    dev_free(m->d_params);
+    std::free(m->h_params);
+    delete m;
+}
+
+static const char kMagic[8] = {'D', 'P', 'G', 'B', '3', '0', '0', 'M'};
+
+dp_status dp_model_save(const dp_model *m, const char *path)
+{
+    if (!m || !path) return fail(DP_ERR_ARG, "model/path is NULL");
+    FILE *f = std::fopen(path, "wb");
+    if (!f) return fail(DP_ERR_FILE, std::string("cannot open ") + path);
+    const dp_model_desc &d = m->desc;
+    uint32_t ver = 1;
+    bool ok = std::fwrite(kMagic, 1, 8, f) == 8 && std::fwrite(&ver, 4, 1, f) == 1;
+    int32_t ints[1 + DP_MAX_TYPES + 1 + DP_MAX_LAYERS + 1 + 1 + DP_MAX_LAYERS + 2];
+    int p = 0;
+    ints[p++] = d.ntypes;
+    for (int a = 0; a < DP_MAX_TYPES; ++a) ints[p++] = d.sel[a];
+    ints[p++] = d.n_emb;
+    for (int l = 0; l < DP_MAX_LAYERS; ++l) ints[p++] = d.emb[l];
+    ints[p++] = d.m2;
+    ints[p++] = d.n_fit;
+    for (int l = 0; l < DP_MAX_LAYERS; ++l) ints[p++] = d.fit[l];
+    ints[p++] = d.desc_scale_nm;
+    ints[p++] = d.reserved;
+    ok = ok && std::fwrite(ints, 4, p, f) == (size_t)p;
+    ok = ok && std::fwrite(&d.rcut, 8, 1, f) == 1 && std::fwrite(&d.rcut_smth, 8, 1, f) == 1;
+    ok = ok && std::fwrite(&m->nparams, 8, 1, f) == 1;
+    ok = ok && std::fwrite(m->h_params, 8, m->nparams, f) == (size_t)m->nparams;
+    ok = (std::fclose(f) == 0) && ok;
+    return ok ? DP_OK : fail(DP_ERR_FILE, std::string("short write to ") + path);
+}
+
+dp_status dp_model_load(const char *path, dp_model **out)
+{
+    if (!path || !out) return fail(DP_ERR_ARG, "path/out is NULL");
+    *out = nullptr;
+    FILE *f = std::fopen(path, "rb");
+    if (!f) return fail(DP_ERR_FILE, std::string("cannot open ") + path);
+    char magic[8];
+    uint32_t ver = 0;
+    dp_model_desc d;
+    std::memset(&d, 0, sizeof(d));
+    int32_t ints[1 + DP_MAX_TYPES + 1 + DP_MAX_LAYERS + 1 + 1 + DP_MAX_LAYERS + 2];
+    const int nint = (int)(sizeof(ints) / sizeof(ints[0]));
+    int64_t np = 0;
+    bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, kMagic, 8) == 0 &&
+              std::fread(&ver, 4, 1, f) == 1 && ver == 1 && std::fread(ints, 4, nint, f) == (size_t)nint &&
+              std::fread(&d.rcut, 8, 1, f) == 1 && std::fread(&d.rcut_smth, 8, 1, f) == 1 &&
+              std::fread(&np, 8, 1, f) == 1;
+    if (!ok) {
+        std::fclose(f);
+        return fail(DP_ERR_FILE, std::string("bad header in ") + path);
+    }
+    int p = 0;
+    d.ntypes = ints[p++];
+    for (int a = 0; a < DP_MAX_TYPES; ++a) d.sel[a] = ints[p++];
+    d.n_emb = ints[p++];
+    for (int l = 0; l < DP_MAX_LAYERS; ++l) d.emb[l] = ints[p++];
+    d.m2 = ints[p++];
+    d.n_fit = ints[p++];
+    for (int l = 0; l < DP_MAX_LAYERS; ++l) d.fit[l] = ints[p++];
+    d.desc_scale_nm = ints[p++];
+    d.reserved = ints[p++];
+    if (check_desc(&d) != DP_OK || np != desc_nparams(d)) {
+        std::fclose(f);
+        return fail(DP_ERR_FILE, std::string("inconsistent descriptor in ") + path);
+    }
+    double *buf = (double *)std::malloc(sizeof(double) * np);
+    if (!buf) {
+        std::fclose(f);
+        return fail(DP_ERR_NOMEM, "host allocation failed");
+    }
+    ok = std::fread(buf, 8, np, f) == (size_t)np;
+    std::fclose(f);
+    if (!ok) {
+        std::free(buf);
+        return fail(DP_ERR_FILE, std::string("truncated parameters in ") + path);
+    }
+    dp_status s = dp_model_create(&d, buf, np, out);
+    std::free(buf);
+    if (s == DP_ERR_ARG) return fail(DP_ERR_FILE, std::string("corrupt parameters in ") + path);
+    return s;
+}
+
+void dp_ctx_free(dp_ctx *c)
+{
+    if (!c) return;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    for (cudaEvent_t e : c->events) cudaEventDestroy(e);
+    dev_free(c->d_status);
+    if (c->h_status) cudaFreeHost(c->h_status);
+    if (c->h_mass_stage) cudaFreeHost(c->h_mass_stage);
+    void *bufs[] = {c->nb.cand, c->nb.ncand, c->nb.xref, c->nb.cell_count, c->nb.cell_start,
+                    c->nb.cell_cursor, c->nb.cell_atoms, c->nb.cell_sorted, c->nb.atom_cell,
+                    c->nb.type_perm, c->nb.type_start, c->fb.nlist, c->fb.keys, c->fb.nreal,
+                    c->eb.T, c->eb.D, c->eb.gD, c->eb.Ei, c->eb.pair_g, c->eb.f_own, c->eb.vir_part,
+                    c->d_energy, c->d_virial, c->md_force, c->ke_part, c->d_inv_mass_conv, c->d_mass};
+    for (void *p : bufs) dev_free(p);
+    delete c;
+}
+
+dp_status dp_ctx_create(const dp_model *model, int64_t natoms_max, int32_t cand_cap, int32_t precision,
+                        void *stream, dp_ctx **out)
+{
+    if (!out) return fail(DP_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!model) return fail(DP_ERR_ARG, "model is NULL");
+    if (natoms_max < 1 || natoms_max >= (1 << 26)) return fail(DP_ERR_ARG, "natoms_max must be in [1, 2^26)");
+    if (cand_cap < 0 || cand_cap > 1024) return fail(DP_ERR_ARG, "cand_cap must be in [0, 1024]");
+    if (precision != DP_PREC_FP64) return fail(DP_ERR_UNSUPPORTED, "precision mode not available");
+    dp_ctx *c = new (std::nothrow) dp_ctx();
+    if (!c) return fail(DP_ERR_NOMEM, "host allocation failed");
+    c->model = model;
+    c->m = model->dev;
+    c->natoms_max = natoms_max;
+    c->cap_fixed = cand_cap;
+    c->cap = 0;
+    c->precision = precision;
+    c->stream = (cudaStream_t)stream;
+    c->sync = 1;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (c->num_sms < 1) c->num_sms = 1;
+    const size_t N = (size_t)natoms_max, nm = (size_t)c->m.nm, T = (size_t)c->m.ntypes, M = (size_t)c->m.M;
+    const size_t nd = (size_t)c->m.m2 * M;
+    dp_status s = DP_OK;
+#define ALLOC(ptr, n) \
+    if (!s) s = dev_alloc(&(ptr), (n), #ptr)
+    ALLOC(c->d_status, 1);
+    ALLOC(c->nb.ncand, N);
+    ALLOC(c->nb.xref, 3 * N);
+    ALLOC(c->nb.cell_atoms, N);
+    ALLOC(c->nb.cell_sorted, N);
+    ALLOC(c->nb.atom_cell, N);
+    ALLOC(c->nb.type_perm, N);
+    ALLOC(c->nb.type_start, T + 1);
+    ALLOC(c->fb.nlist, N * nm);
+    ALLOC(c->fb.keys, N * nm);
+    ALLOC(c->fb.nreal, N * T);
+    ALLOC(c->eb.T, N * 4 * M);
+    ALLOC(c->eb.D, N * nd);
+    ALLOC(c->eb.gD, N * nd);
+    ALLOC(c->eb.Ei, N);
+    ALLOC(c->eb.pair_g, N * nm * 3);
+    ALLOC(c->eb.f_own, 3 * N);
+    ALLOC(c->eb.vir_part, 9 * N);
+    ALLOC(c->d_energy, 1);
+    ALLOC(c->d_virial, 9);
+    ALLOC(c->md_force, 3 * N);
+    ALLOC(c->ke_part, N);
+    ALLOC(c->d_inv_mass_conv, DP_MAX_TYPES);
+    ALLOC(c->d_mass, DP_MAX_TYPES);
+#undef ALLOC
+    if (!s && cudaMallocHost((void **)&c->h_status, sizeof(int32_t)) != cudaSuccess) {
+        c->h_status = nullptr;
+        s = fail(DP_ERR_NOMEM, "pinned allocation failed");
+    }
+    if (!s && cudaMallocHost((void **)&c->h_mass_stage, sizeof(double) * 2 * DP_MAX_TYPES) != cudaSuccess) {
+        c->h_mass_stage = nullptr;
+        s = fail(DP_ERR_NOMEM, "pinned allocation failed");
+    }
+    if (!s) {
+        cudaError_t e = cudaMemsetAsync(c->d_status, 0, sizeof(int32_t), c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) s = cuda_fail(e, "dp_ctx_create");
+    }
+    if (s) {
+        dp_ctx_free(c);
+        return s;
+    }
+    *out = c;
+    return DP_OK;
+}
+
+dp_status dp_ctx_set_sync(dp_ctx *c, int32_t sync)
+{
+    if (!c) return fail(DP_ERR_ARG, "context is NULL");
+    c->sync = sync ? 1 : 0;
+    return DP_OK;
+}
+
+int64_t dp_ctx_launches(const dp_ctx *c) { return c ? c->launches : -1; }
+
+dp_status dp_ctx_set_timing(dp_ctx *c, int32_t on)
+{
+    if (!c) return fail(DP_ERR_ARG, "context is NULL");
+    if (on) {
+        dp_status s = flush_spans(c);
+        if (s) return s;
+        for (int g = 0; g < DP_KERNEL_GROUPS; ++g) {
+            c->group_ms[g] = 0.0;
+            c->group_launches[g] = 0;
+        }
+    }
+    c->timing = on != 0;
+    return DP_OK;
+}
+
+dp_status dp_ctx_kernel_times(dp_ctx *c, double *ms, int64_t *launches)
+{
+    if (!c) return fail(DP_ERR_ARG, "context is NULL");
+    dp_status s = flush_spans(c);
+    if (s) return s;
+    for (int g = 0; g < DP_KERNEL_GROUPS; ++g) {
+        if (ms) ms[g] = c->group_ms[g];
+        if (launches) launches[g] = c->group_launches[g];
+    }
+    return DP_OK;
+}
+
+const char *dp_kernel_group_name(int32_t g)
+{
+    static const char *names[DP_KERNEL_GROUPS] = {"build", "format", "embed_fwd", "fit",
+                                                  "embed_bwd", "force", "reduce", "md"};
+    return (g >= 0 && g < DP_KERNEL_GROUPS) ? names[g] : "?";
+}
+
+dp_status dp_ctx_status(dp_ctx *c)
+{
+    if (!c) return fail(DP_ERR_ARG, "context is NULL");
+    DP_CUDA(cudaMemcpyAsync(c->h_status, c->d_status, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream),
+            "status read");
+    DP_CUDA(cudaStreamSynchronize(c->stream), "status read");
+    const int32_t f = *c->h_status;
+    DP_CUDA(cudaMemsetAsync(c->d_status, 0, sizeof(int32_t), c->stream), "status reset");
+    if (f & DPF_BAD_TYPE) return fail(DP_ERR_TYPE, "an atom type is outside [0, ntypes)");
+    if (f & DPF_CAND_OVERFLOW) return fail(DP_ERR_CAPACITY, "an atom has more candidates than cand_cap");
+    if (f & DPF_NONFINITE) return fail(DP_ERR_NONFINITE, "non-finite energy or virial");
+    if (f & DPF_SEL_OVERFLOW) return fail(DP_ERR_SEL_OVERFLOW, "a neighbour within rcut did not fit sel");
+    if (f & DPF_STALE) return fail(DP_ERR_NLIST_STALE, "an atom moved more than skin/2 since the last build");
+    return DP_OK;
+}
+
+dp_status dp_build_nlist(dp_ctx *c, const double *coords, const int32_t *types, const double box[9], int64_t N,
+                         double skin)
+{
+    dp_status s = check_common(c, coords, types, N);
+    if (s) return s;
+    Box3 b;
+    if ((s = read_box(box, b))) return s;
+    if ((s = do_build(c, coords, types, b, N, skin))) return s;
+    return finish(c);
+}
+
+dp_status dp_format_nlist(dp_ctx *c, const double *coords, const int32_t *types, const double box[9], int64_t N,
+                          int32_t *nlist, int32_t *nreal)
+{
+    dp_status s = check_common(c, coords, types, N);
+    if (s) return s;
+    Box3 b;
+    if ((s = read_box(box, b))) return s;
+    if (!c->nlist_valid || c->nlist_N != N)
+        if ((s = do_build(c, coords, types, b, N, 0.0))) return s;
+    if ((s = enqueue_format(c, coords, types, b, N))) return s;
+    if (nlist)
+        DP_CUDA(cudaMemcpyAsync(nlist, c->fb.nlist, sizeof(int32_t) * N * c->m.nm, cudaMemcpyDeviceToDevice,
+                                c->stream),
+                "dp_format_nlist");
+    if (nreal)
+        DP_CUDA(cudaMemcpyAsync(nreal, c->fb.nreal, sizeof(int32_t) * N * c->m.ntypes, cudaMemcpyDeviceToDevice,
+                                c->stream),
+                "dp_format_nlist");
+    return finish(c);
+}
+
+dp_status dp_eval(dp_ctx *c, const double *coords, const int32_t *types, const double box[9], int64_t N,
+                  double *energy, double *force, double *virial, double *atom_energy)
+{
+    dp_status s = check_common(c, coords, types, N);
+    if (s) return s;
+    if (!energy || !force || !virial) return fail(DP_ERR_ARG, "energy/force/virial is NULL");
+    Box3 b;
+    if ((s = read_box(box, b))) return s;
+    if (!c->nlist_valid || c->nlist_N != N)
+        if ((s = do_build(c, coords, types, b, N, 0.0))) return s;
+    if ((s = enqueue_eval(c, coords, types, b, N, energy, force, virial, atom_energy))) return s;
+    return finish(c);
+}
+
+dp_status dp_md_step(dp_ctx *c, double *coords, double *vel, const int32_t *types, const double box[9],
+                     const double *mass_per_type, int64_t N, double dt_fs, int32_t nsteps, int32_t rebuild_every,
+                     double skin, double *thermo)
+{
+    dp_status s = check_common(c, coords, types, N);
+    if (s) return s;
+    if (!vel || !mass_per_type) return fail(DP_ERR_ARG, "vel/mass_per_type is NULL");
+    if (nsteps < 0 || rebuild_every < 0 || !(dt_fs > 0.0)) return fail(DP_ERR_ARG, "bad nsteps/rebuild_every/dt");
+    Box3 b;
+    if ((s = read_box(box, b))) return s;
+    const int T = c->m.ntypes;
+    bool same = true;
+    for (int a = 0; a < T; ++a) {
+        if (!(mass_per_type[a] > 0.0)) return fail(DP_ERR_ARG, "masses must be positive");
+        same = same && c->last_mass[a] == mass_per_type[a];
+    }
+    if (!same) {
+        // the pinned staging buffer may still feed an earlier asynchronous copy
+        DP_CUDA(cudaStreamSynchronize(c->stream), "dp_md_step");
+        for (int a = 0; a < T; ++a) {
+            c->h_mass_stage[a] = kAccConv / mass_per_type[a];
+            c->h_mass_stage[DP_MAX_TYPES + a] = mass_per_type[a];
+            c->last_mass[a] = mass_per_type[a];
+        }
+        DP_CUDA(cudaMemcpyAsync(c->d_inv_mass_conv, c->h_mass_stage, sizeof(double) * T, cudaMemcpyHostToDevice,
+                                c->stream),
+                "dp_md_step");
+        DP_CUDA(cudaMemcpyAsync(c->d_mass, c->h_mass_stage + DP_MAX_TYPES, sizeof(double) * T,
+                                cudaMemcpyHostToDevice, c->stream),
+                "dp_md_step");
+    }
+    const double vol = b.L[0] * b.L[1] * b.L[2];
+    if (!c->md_force_valid || c->md_N != N) {
+        if ((s = do_build(c, coords, types, b, N, skin))) return s;
+        if ((s = enqueue_eval(c, coords, types, b, N, c->d_energy, c->md_force, c->d_virial, nullptr))) return s;
+        c->md_force_valid = true;
+        c->md_N = N;
+        c->md_step = 0;
+    }
+    for (int st = 1; st <= nsteps; ++st) {
+        cudaError_t e;
+        {
+            GroupTimer tm(c, G_MD);
+            e = dp_launch_kick_drift(c->stream, (int)N, coords, vel, c->md_force, types, c->d_inv_mass_conv, dt_fs,
+                                     b, &c->launches);
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "kick_drift");
+        c->md_step += 1;
+        if (rebuild_every > 0 && c->md_step % rebuild_every == 0)
+            if ((s = do_build(c, coords, types, b, N, skin))) return s;
+        if ((s = enqueue_eval(c, coords, types, b, N, c->d_energy, c->md_force, c->d_virial, nullptr))) return s;
+        {
+            GroupTimer tm(c, G_MD);
+            e = dp_launch_kick_thermo(c->stream, (int)N, vel, c->md_force, types, c->d_inv_mass_conv, c->d_mass,
+                                      dt_fs, c->ke_part, &c->launches);
+            if (e == cudaSuccess && thermo)
+                e = dp_launch_thermo(c->stream, (int)N, c->ke_part, c->d_energy, c->d_virial, vol,
+                                     thermo + (size_t)(st - 1) * 4, &c->launches);
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "kick_thermo");
+    }
+    return finish(c);
+}
+
+dp_status dp_md_get_force(dp_ctx *c, double *force, int64_t N)
+{
+    if (!c || !force) return fail(DP_ERR_ARG, "context/force is NULL");
+    if (!c->md_force_valid || c->md_N != N) return fail(DP_ERR_ARG, "no MD force for this N");
+    DP_CUDA(cudaMemcpyAsync(force, c->md_force, sizeof(double) * 3 * N, cudaMemcpyDeviceToDevice, c->stream),
+            "dp_md_get_force");
+    return finish(c);
+}
+
+dp_status dp_md_reset(dp_ctx *c)
+{
+    if (!c) return fail(DP_ERR_ARG, "context is NULL");
+    c->md_force_valid = false;
+    c->md_step = 0;
+    return DP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,171 @@
+// dp_internal.cuh -- types and helpers shared by the CUDA translation units
+// of the GB300 Deep Potential library (not part of the public ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/dp.h"
+
+#define DP_MAX_EMB_W 128     // widest embedding layer
+#define DP_MAX_FIT_W 256     // widest fitting layer
+#define DP_MAX_NM 1024       // N_m limit
+
+// Device-side status bits (accumulated with atomicOr, read by the host).
+enum : int32_t {
+    DPF_SEL_OVERFLOW = 1,
+    DPF_CAND_OVERFLOW = 2,
+    DPF_STALE = 4,
+    DPF_NONFINITE = 8,
+    DPF_BAD_TYPE = 16,
+};
+
+// Model description passed by value to kernels.
+struct DevModel {
+    int ntypes, nm;
+    int sel[DP_MAX_TYPES], sel_off[DP_MAX_TYPES];
+    int n_emb, emb[DP_MAX_LAYERS];
+    int M, m2;
+    int n_fit, fit[DP_MAX_LAYERS];
+    int emb_net_size;                       // doubles per embedding net
+    double rcut, rcut_smth, desc_scale;
+    const double *params;                   // device
+    int64_t emb_base[DP_MAX_TYPES * DP_MAX_TYPES];
+    int64_t fit_base[DP_MAX_TYPES];
+};
+
+struct Box3 {
+    double L[3];
+};
+
+// ---------------------------------------------------------------------------
+// Pinned distance arithmetic.  Candidate sets and sort keys must be identical
+// to the CPU reference bit for bit, so the minimum image and |r| are computed
+// with explicitly rounded operations (no FMA contraction):
+//   d = xj - xi; d -= L * rint(d / L); r = sqrt((dx*dx + dy*dy) + dz*dz).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double dp_min_image_1(double xj, double xi, double L)
+{
+    double v = __dsub_rn(xj, xi);
+    double n = rint(__ddiv_rn(v, L));
+    return __dsub_rn(v, __dmul_rn(L, n));
+}
+
+__device__ __forceinline__ double dp_pinned_dist(const double *xi, const double *xj, const Box3 &b,
+                                                 double d[3])
+{
+    d[0] = dp_min_image_1(xj[0], xi[0], b.L[0]);
+    d[1] = dp_min_image_1(xj[1], xi[1], b.L[1]);
+    d[2] = dp_min_image_1(xj[2], xi[2], b.L[2]);
+    double r2 = __dadd_rn(__dmul_rn(d[0], d[0]), __dmul_rn(d[1], d[1]));
+    r2 = __dadd_rn(r2, __dmul_rn(d[2], d[2]));
+    return __dsqrt_rn(r2);
+}
+
+// Packed sort key of Algorithm 1: (type, floor(|r| * 1e8), j) as
+// type << 60 | q << 26 | j  (4 + 34 + 26 bits; |r| < 171 A, j < 2^26).
+__device__ __forceinline__ uint64_t dp_pack_key(int type, double r, int j)
+{
+    uint64_t q = (uint64_t)floor(__dmul_rn(r, 1e8));
+    return ((uint64_t)type << 60) | (q << 26) | (uint64_t)j;
+}
+#define DP_KEY_NONE 0xFFFFFFFFFFFFFFFFull
+
+// Switching function s(r) = w(r)/r and ds/dr (w: quintic smooth step between
+// rcut_smth and rcut; the paper fixes only that w falls smoothly to 0 at rcut).
+__device__ __forceinline__ void dp_switch(double r, double rs, double rc, double &s, double &ds)
+{
+    if (r < rs) {
+        double inv = 1.0 / r;
+        s = inv;
+        ds = -inv * inv;
+    } else if (r < rc) {
+        double u = (r - rs) / (rc - rs);
+        double u2 = u * u;
+        double w = u2 * u * (-6.0 * u2 + 15.0 * u - 10.0) + 1.0;
+        double um1 = u - 1.0;
+        double dw = -30.0 * u2 * um1 * um1 / (rc - rs);
+        double inv = 1.0 / r;
+        s = w * inv;
+        ds = (dw - w * inv) * inv;
+    } else {
+        s = 0.0;
+        ds = 0.0;
+    }
+}
+
+// Skip kind of an (in -> out) layer: 2 = (x, x), 1 = x, 0 = none.
+__host__ __device__ __forceinline__ int dp_skip_kind(int in, int out)
+{
+    return out == 2 * in ? 2 : (out == in ? 1 : 0);
+}
+
+// ---------------------------------------------------------------------------
+// Kernel launchers (each returns cudaGetLastError()).
+// ---------------------------------------------------------------------------
+struct NlistBuffers {
+    int32_t *cand;        // [N][cap]
+    int32_t *ncand;       // [N]
+    double *xref;         // [N][3]
+    int32_t *cell_count;  // [ncell]
+    int32_t *cell_start;  // [ncell + 1]
+    int32_t *cell_cursor; // [ncell]
+    int32_t *cell_atoms;  // [N]
+    int32_t *cell_sorted; // [N]
+    int32_t *atom_cell;   // [N]
+    int32_t *type_perm;   // [N]
+    int32_t *type_start;  // [ntypes + 1]
+};
+
+struct FormatBuffers {
+    int32_t *nlist;   // [N][nm]
+    uint64_t *keys;   // [N][nm]
+    int32_t *nreal;   // [N][ntypes]
+};
+
+cudaError_t dp_launch_build(cudaStream_t st, const DevModel &m, const double *x, const int32_t *types,
+                            Box3 box, int N, double rlist, int cap, int nc[3], NlistBuffers nb,
+                            int32_t *status, int64_t *launches);
+cudaError_t dp_launch_format(cudaStream_t st, const DevModel &m, const double *x,
+                             const int32_t *types, Box3 box, int N, int cap, double skin,
+                             NlistBuffers nb, FormatBuffers fb, int32_t *status, int64_t *launches);
+
+struct EvalBuffers {
+    double *T;         // [N][4][M]
+    double *D;         // [N][m2*M]
+    double *gD;        // [N][m2*M]
+    double *Ei;        // [N]
+    double *pair_g;    // [N][nm][3]
+    double *f_own;     // [N][3]
+    double *vir_part;  // [N][9]
+};
+
+cudaError_t dp_launch_embed_fwd(cudaStream_t st, const DevModel &m, const double *x,
+                                const int32_t *types, Box3 box, int N, const FormatBuffers &fb,
+                                const NlistBuffers &nb, EvalBuffers eb, int num_sms,
+                                int64_t *launches);
+cudaError_t dp_launch_fit(cudaStream_t st, const DevModel &m, int N, const NlistBuffers &nb,
+                          EvalBuffers eb, int64_t *launches);
+cudaError_t dp_launch_embed_bwd(cudaStream_t st, const DevModel &m, const double *x,
+                                const int32_t *types, Box3 box, int N, const FormatBuffers &fb,
+                                const NlistBuffers &nb, EvalBuffers eb, int num_sms,
+                                int64_t *launches);
+cudaError_t dp_launch_force(cudaStream_t st, const DevModel &m, const double *x,
+                            const int32_t *types, Box3 box, int N, int cap,
+                            const NlistBuffers &nb, const FormatBuffers &fb, EvalBuffers eb,
+                            double *force, int64_t *launches);
+cudaError_t dp_launch_reduce(cudaStream_t st, int N, EvalBuffers eb, double *energy,
+                             double *virial, double *atom_energy, int32_t *status,
+                             int64_t *launches);
+
+// MD integrator kernels.
+cudaError_t dp_launch_kick_drift(cudaStream_t st, int N, double *x, double *v, const double *f,
+                                 const int32_t *types, const double *inv_mass_conv, double dt,
+                                 Box3 box, int64_t *launches);
+cudaError_t dp_launch_kick_thermo(cudaStream_t st, int N, double *v, const double *f,
+                                  const int32_t *types, const double *inv_mass_conv,
+                                  const double *mass, double dt, double *ke_part,
+                                  int64_t *launches);
+cudaError_t dp_launch_thermo(cudaStream_t st, int N, const double *ke_part, const double *energy,
+                             const double *virial, double volume, double *thermo_row,
+                             int64_t *launches);

@@ -1,0 +1,313 @@
+"""Thin Python binding of the C ABI in include/dp.h (ctypes).
+
+Argument marshalling only: every step of the path runs in the CUDA library
+libdp_gb300.so.  PyTorch supplies device memory and streams.  If the library
+cannot be built or loaded this module raises; there is no CPU fallback.
+
+The functions keep the C names (dp_build_nlist, dp_eval, dp_md_step, ...);
+``Model`` and ``Context`` wrap the handles.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+DP_OK = 0
+STATUS_NAMES = {
+    0: "DP_OK", -1: "DP_ERR_ARG", -2: "DP_ERR_BOX", -3: "DP_ERR_SEL_OVERFLOW",
+    -4: "DP_ERR_NLIST_STALE", -5: "DP_ERR_NONFINITE", -6: "DP_ERR_FILE", -7: "DP_ERR_CUDA",
+    -8: "DP_ERR_UNSUPPORTED", -9: "DP_ERR_CAPACITY", -10: "DP_ERR_NOMEM", -11: "DP_ERR_TYPE",
+}
+DP_PREC_FP64 = 0
+
+
+class DPError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class dp_model_desc(ctypes.Structure):
+    _fields_ = [("ntypes", ctypes.c_int32), ("sel", ctypes.c_int32 * 8), ("n_emb", ctypes.c_int32),
+                ("emb", ctypes.c_int32 * 4), ("m2", ctypes.c_int32), ("n_fit", ctypes.c_int32),
+                ("fit", ctypes.c_int32 * 4), ("desc_scale_nm", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("rcut", ctypes.c_double), ("rcut_smth", ctypes.c_double)]
+
+
+_lock = threading.Lock()
+_lib = None
+_vp = ctypes.c_void_p
+_i64 = ctypes.c_int64
+_i32 = ctypes.c_int32
+_dbl = ctypes.c_double
+
+
+def lib():
+    """Load (building first if needed) libdp_gb300.so."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.LIB if _build.up_to_date() else _build.build()
+            L = ctypes.CDLL(path)
+            L.dp_last_error.restype = ctypes.c_char_p
+            L.dp_status_string.restype = ctypes.c_char_p
+            L.dp_status_string.argtypes = [_i32]
+            L.dp_model_nparams.restype = _i64
+            L.dp_model_nparams.argtypes = [ctypes.POINTER(dp_model_desc)]
+            L.dp_model_create.restype = _i32
+            L.dp_model_create.argtypes = [ctypes.POINTER(dp_model_desc), _vp, _i64, ctypes.POINTER(_vp)]
+            L.dp_model_load.restype = _i32
+            L.dp_model_load.argtypes = [ctypes.c_char_p, ctypes.POINTER(_vp)]
+            L.dp_model_save.restype = _i32
+            L.dp_model_save.argtypes = [_vp, ctypes.c_char_p]
+            L.dp_model_free.argtypes = [_vp]
+            L.dp_ctx_create.restype = _i32
+            L.dp_ctx_create.argtypes = [_vp, _i64, _i32, _i32, _vp, ctypes.POINTER(_vp)]
+            L.dp_ctx_free.argtypes = [_vp]
+            L.dp_ctx_set_sync.restype = _i32
+            L.dp_ctx_set_sync.argtypes = [_vp, _i32]
+            L.dp_ctx_status.restype = _i32
+            L.dp_ctx_status.argtypes = [_vp]
+            L.dp_ctx_launches.restype = _i64
+            L.dp_ctx_launches.argtypes = [_vp]
+            L.dp_build_nlist.restype = _i32
+            L.dp_build_nlist.argtypes = [_vp, _vp, _vp, _vp, _i64, _dbl]
+            L.dp_format_nlist.restype = _i32
+            L.dp_format_nlist.argtypes = [_vp, _vp, _vp, _vp, _i64, _vp, _vp]
+            L.dp_eval.restype = _i32
+            L.dp_eval.argtypes = [_vp, _vp, _vp, _vp, _i64, _vp, _vp, _vp, _vp]
+            L.dp_md_step.restype = _i32
+            L.dp_md_step.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, _i64, _dbl, _i32, _i32, _dbl, _vp]
+            L.dp_md_get_force.restype = _i32
+            L.dp_md_get_force.argtypes = [_vp, _vp, _i64]
+            L.dp_md_reset.restype = _i32
+            L.dp_md_reset.argtypes = [_vp]
+            L.dp_ctx_set_timing.restype = _i32
+            L.dp_ctx_set_timing.argtypes = [_vp, _i32]
+            L.dp_ctx_kernel_times.restype = _i32
+            L.dp_ctx_kernel_times.argtypes = [_vp, _vp, _vp]
+            L.dp_kernel_group_name.restype = ctypes.c_char_p
+            L.dp_kernel_group_name.argtypes = [_i32]
+            _lib = L
+    return _lib
+
+
+def lib_path():
+    return _build.LIB
+
+
+def _check(status, ok=(DP_OK,)):
+    if status not in ok:
+        raise DPError(status, lib().dp_last_error().decode())
+    return status
+
+
+def make_desc(d):
+    """dp_model_desc from a dict (keys as in synth.WATER_MODEL)."""
+    c = dp_model_desc()
+    c.ntypes = d["ntypes"]
+    for a, s in enumerate(d["sel"]):
+        c.sel[a] = s
+    c.n_emb = len(d["emb"])
+    for l, w in enumerate(d["emb"]):
+        c.emb[l] = w
+    c.m2 = d["m2"]
+    c.n_fit = len(d["fit"])
+    for l, w in enumerate(d["fit"]):
+        c.fit[l] = w
+    c.desc_scale_nm = int(d.get("desc_scale_nm", 1))
+    c.rcut = float(d["rcut"])
+    c.rcut_smth = float(d["rcut_smth"])
+    return c
+
+
+def dp_model_nparams(desc):
+    c = make_desc(desc) if isinstance(desc, dict) else desc
+    return int(lib().dp_model_nparams(ctypes.byref(c)))
+
+
+def _box9(box):
+    b = np.asarray(box, dtype=np.float64)
+    if b.shape == (3,):
+        b = np.diag(b)
+    b = np.ascontiguousarray(b.reshape(9), dtype=np.float64)
+    return b
+
+
+def _dev(t, dtype, shape=None, name="tensor"):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype or not t.is_contiguous():
+        raise TypeError(f"{name} must be a contiguous {dtype} tensor")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {shape}, got {tuple(t.shape)}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Model:
+    """dp_model handle (parameters live on the current CUDA device)."""
+
+    def __init__(self, desc=None, params=None, _handle=None):
+        self._h = _vp()
+        if _handle is not None:
+            self._h = _handle
+        else:
+            self.desc_c = make_desc(desc)
+            p = np.ascontiguousarray(params, dtype=np.float64)
+            _check(lib().dp_model_create(ctypes.byref(self.desc_c), p.ctypes.data_as(_vp), len(p),
+                                         ctypes.byref(self._h)))
+        self.desc = desc
+
+    @classmethod
+    def load(cls, path, desc=None):
+        h = _vp()
+        _check(lib().dp_model_load(os.fsencode(path), ctypes.byref(h)))
+        return cls(desc=desc, _handle=h)
+
+    def save(self, path):
+        _check(lib().dp_model_save(self._h, os.fsencode(path)))
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._h:
+            lib().dp_model_free(self._h)
+            self._h = _vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Context:
+    """dp_ctx handle: scratch memory and stream for one system size."""
+
+    def __init__(self, model, natoms_max, cand_cap=0, precision=DP_PREC_FP64, stream=None):
+        self.model = model
+        self.natoms_max = int(natoms_max)
+        st = stream if stream is not None else torch.cuda.current_stream()
+        self.stream = st
+        self._h = _vp()
+        _check(lib().dp_ctx_create(model.handle, self.natoms_max, int(cand_cap), int(precision),
+                                   ctypes.c_void_p(st.cuda_stream), ctypes.byref(self._h)))
+
+    @property
+    def handle(self):
+        return self._h
+
+    def set_sync(self, sync):
+        _check(lib().dp_ctx_set_sync(self._h, int(bool(sync))))
+
+    def status(self):
+        return lib().dp_ctx_status(self._h)
+
+    @property
+    def launches(self):
+        return int(lib().dp_ctx_launches(self._h))
+
+    def set_timing(self, on):
+        _check(lib().dp_ctx_set_timing(self._h, int(bool(on))))
+
+    def kernel_times(self):
+        """{group name: (milliseconds, launches)} accumulated while timing was on."""
+        ms = np.zeros(8, dtype=np.float64)
+        n = np.zeros(8, dtype=np.int64)
+        _check(lib().dp_ctx_kernel_times(self._h, ms.ctypes.data_as(_vp), n.ctypes.data_as(_vp)))
+        return {lib().dp_kernel_group_name(g).decode(): (float(ms[g]), int(n[g])) for g in range(8)}
+
+    def close(self):
+        if self._h:
+            lib().dp_ctx_free(self._h)
+            self._h = _vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ------------------------------------------------------------ C-ABI names --
+
+def dp_build_nlist(ctx, coords, types, box, skin=0.0, check=True):
+    N = coords.shape[0]
+    b = _box9(box)
+    s = lib().dp_build_nlist(ctx.handle, _dev(coords, torch.float64, (N, 3), "coords"),
+                             _dev(types, torch.int32, (N,), "types"), b.ctypes.data_as(_vp), N, float(skin))
+    return _check(s) if check else s
+
+
+def dp_format_nlist(ctx, coords, types, box, check=True):
+    """Returns (nlist [N, N_m] int32, nreal [N, ntypes] int32, status)."""
+    N = coords.shape[0]
+    d = ctx.model.desc
+    nm = int(sum(d["sel"]))
+    nlist = torch.empty((N, nm), dtype=torch.int32, device=coords.device)
+    nreal = torch.empty((N, d["ntypes"]), dtype=torch.int32, device=coords.device)
+    b = _box9(box)
+    s = lib().dp_format_nlist(ctx.handle, _dev(coords, torch.float64, (N, 3), "coords"),
+                              _dev(types, torch.int32, (N,), "types"), b.ctypes.data_as(_vp), N,
+                              _dev(nlist, torch.int32), _dev(nreal, torch.int32))
+    if check:
+        _check(s)
+    return nlist, nreal, s
+
+
+def dp_eval(ctx, coords, types, box, energy=None, force=None, virial=None, atom_energy=None,
+            want_atom_energy=False, check=True):
+    """Energy, forces and virial; returns dict of device tensors and the status."""
+    N = coords.shape[0]
+    dev = coords.device
+    if energy is None:
+        energy = torch.empty(1, dtype=torch.float64, device=dev)
+    if force is None:
+        force = torch.empty((N, 3), dtype=torch.float64, device=dev)
+    if virial is None:
+        virial = torch.empty(9, dtype=torch.float64, device=dev)
+    if atom_energy is None and want_atom_energy:
+        atom_energy = torch.empty(N, dtype=torch.float64, device=dev)
+    b = _box9(box)
+    s = lib().dp_eval(ctx.handle, _dev(coords, torch.float64, (N, 3), "coords"),
+                      _dev(types, torch.int32, (N,), "types"), b.ctypes.data_as(_vp), N,
+                      _dev(energy, torch.float64, (1,), "energy"), _dev(force, torch.float64, (N, 3), "force"),
+                      _dev(virial, torch.float64, (9,), "virial"),
+                      _dev(atom_energy, torch.float64, (N,), "atom_energy") if atom_energy is not None else None)
+    if check:
+        _check(s)
+    return dict(energy=energy, force=force, virial=virial, atom_energy=atom_energy, status=s)
+
+
+def dp_md_step(ctx, coords, vel, types, box, masses, dt, nsteps, rebuild_every=10, skin=2.0,
+               thermo=None, check=True):
+    """Advance coords/vel in place; returns (thermo [nsteps, 4] device tensor or None, status)."""
+    N = coords.shape[0]
+    m = np.ascontiguousarray(masses, dtype=np.float64)
+    b = _box9(box)
+    s = lib().dp_md_step(ctx.handle, _dev(coords, torch.float64, (N, 3), "coords"),
+                         _dev(vel, torch.float64, (N, 3), "vel"), _dev(types, torch.int32, (N,), "types"),
+                         b.ctypes.data_as(_vp), m.ctypes.data_as(_vp), N, float(dt), int(nsteps),
+                         int(rebuild_every), float(skin),
+                         _dev(thermo, torch.float64, (nsteps, 4), "thermo") if thermo is not None else None)
+    if check:
+        _check(s)
+    return thermo, s
+
+
+def dp_md_get_force(ctx, N, device="cuda"):
+    f = torch.empty((N, 3), dtype=torch.float64, device=device)
+    _check(lib().dp_md_get_force(ctx.handle, _dev(f, torch.float64), N))
+    return f
+
+
+def dp_md_reset(ctx):
+    _check(lib().dp_md_reset(ctx.handle))

@@ -1,0 +1,266 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Bars: formatted neighbour lists bit-exact (integer work); energy, forces and
+virial within 1e-10 relative (norm-wise: |dE|/|E|, max|dF|/max|F|,
+max|dXi|/max|Xi|), the paper's own FP64 agreement of 10+ digits (Sec. 6).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def dp():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2004_11658_gb300 import dp as _dp
+    _dp.lib()
+    return _dp
+
+
+def system(synth, name):
+    if name == "water648":
+        return synth.sub_box_water(6, 6 * 49.7 / 16)
+    if name == "cu864":
+        c, t, b = synth.copper_fcc(6)
+        return dict(coords=c, types=t, box=b, model=synth.CU_MODEL, masses=(synth.MASS["Cu"],))
+    return synth.workload(name)
+
+
+_oracle_cache = {}
+
+
+def oracle_eval(oracle, synth, name, desc=None, seed=0):
+    key = (name, repr(desc), seed)
+    if key not in _oracle_cache:
+        w = system(synth, name)
+        d = desc or w["model"]
+        P = synth.model_params(d, seed)
+        out = oracle.evaluate(d, P, w["coords"], w["types"], w["box"])
+        _oracle_cache[key] = (w, d, P, out)
+    return _oracle_cache[key]
+
+
+def gpu_run(dp, desc, P, w, skin=0.0, cand_cap=0):
+    N = len(w["coords"])
+    model = dp.Model(desc, P)
+    ctx = dp.Context(model, N, cand_cap=cand_cap)
+    x = torch.tensor(w["coords"], dtype=torch.float64, device="cuda")
+    t = torch.tensor(w["types"], dtype=torch.int32, device="cuda")
+    dp.dp_build_nlist(ctx, x, t, w["box"], skin)
+    return model, ctx, x, t
+
+
+def rel_errors(g, o):
+    eE = abs(g["energy"].item() - o["energy"]) / abs(o["energy"])
+    F = g["force"].cpu().numpy()
+    eF = np.abs(F - o["force"]).max() / np.abs(o["force"]).max()
+    V = g["virial"].cpu().numpy().reshape(3, 3)
+    eV = np.abs(V - o["virial"]).max() / np.abs(o["virial"]).max()
+    return eE, eF, eV
+
+
+@pytest.mark.parametrize("name", ["water192", "water648", "cu864"])
+def test_format_bit_exact(dp, oracle, synth, name):
+    w, d, P, o = oracle_eval(oracle, synth, name)
+    model, ctx, x, t = gpu_run(dp, d, P, w)
+    nl, nr, s = dp.dp_format_nlist(ctx, x, t, w["box"])
+    np.testing.assert_array_equal(nl.cpu().numpy(), o["nlist"])
+    np.testing.assert_array_equal(nr.cpu().numpy(), o["nreal"])
+
+
+@pytest.mark.parametrize("name", ["water192", "water648", "cu864"])
+def test_eval_parity(dp, oracle, synth, name):
+    w, d, P, o = oracle_eval(oracle, synth, name)
+    model, ctx, x, t = gpu_run(dp, d, P, w)
+    g = dp.dp_eval(ctx, x, t, w["box"], want_atom_energy=True)
+    eE, eF, eV = rel_errors(g, o)
+    assert eE < TOL and eF < TOL and eV < TOL, (eE, eF, eV)
+    ea = np.abs(g["atom_energy"].cpu().numpy() - o["atom_energy"]).max() / np.abs(o["atom_energy"]).max()
+    assert ea < TOL
+
+
+def test_eval_with_skin_list_matches(dp, oracle, synth):
+    """Candidates built with a 2 A skin give the same result (Algorithm 1
+    re-sorts and truncates them every evaluation)."""
+    w, d, P, o = oracle_eval(oracle, synth, "water648")
+    model, ctx, x, t = gpu_run(dp, d, P, w, skin=2.0)
+    nl, nr, _ = dp.dp_format_nlist(ctx, x, t, w["box"])
+    np.testing.assert_array_equal(nl.cpu().numpy(), o["nlist"])
+    g = dp.dp_eval(ctx, x, t, w["box"])
+    assert max(rel_errors(g, o)) < TOL
+
+
+@pytest.mark.parametrize("variant", ["student", "unscaled"])
+def test_model_variants(dp, oracle, synth, variant):
+    if variant == "student":
+        desc = synth.WATER_STUDENT
+    else:
+        desc = dict(synth.WATER_MODEL, desc_scale_nm=0)
+    w, d, P, o = oracle_eval(oracle, synth, "water192", desc=desc)
+    if variant == "unscaled":
+        P = synth.model_params(d, 0, fit_in_gain=300.0 / 138 ** 2)
+        o = oracle.evaluate(d, P, w["coords"], w["types"], w["box"])
+    model, ctx, x, t = gpu_run(dp, d, P, w)
+    g = dp.dp_eval(ctx, x, t, w["box"])
+    assert max(rel_errors(g, o)) < TOL
+
+
+def test_deterministic(dp, oracle, synth):
+    w, d, P, o = oracle_eval(oracle, synth, "water648")
+    model, ctx, x, t = gpu_run(dp, d, P, w)
+    a = dp.dp_eval(ctx, x, t, w["box"])
+    b = dp.dp_eval(ctx, x, t, w["box"])
+    assert torch.equal(a["force"], b["force"]) and torch.equal(a["energy"], b["energy"])
+    assert torch.equal(a["virial"], b["virial"])
+
+
+def test_sel_overflow_matches_truncated_oracle(dp, oracle, synth):
+    w = synth.workload("water192")
+    d = dict(w["model"], sel=(20, 40))
+    P = synth.model_params(d, 0)
+    o = oracle.evaluate(d, P, w["coords"], w["types"], w["box"])
+    assert o["overflow"] > 0
+    model, ctx, x, t = gpu_run(dp, d, P, w)
+    g = dp.dp_eval(ctx, x, t, w["box"], check=False)
+    assert g["status"] == -3  # DP_ERR_SEL_OVERFLOW, results written
+    assert max(rel_errors(g, o)) < TOL
+
+
+def test_isolated_and_single_atoms(dp, oracle, synth):
+    d = synth.WATER_MODEL
+    P = synth.model_params(d, 0)
+    # a molecule far from a small cluster: atoms with no neighbour at all
+    w = synth.workload("water192")
+    x = np.concatenate([w["coords"][:30] + 10.0, np.array([[45.0, 45.0, 45.0]])])
+    t = np.concatenate([w["types"][:30], np.array([1], np.int32)])
+    box = np.array([60.0, 60.0, 60.0])
+    o = oracle.evaluate(d, P, x, t, box)
+    ws = dict(coords=x, types=t, box=box)
+    model, ctx, xg, tg = gpu_run(dp, d, P, ws)
+    g = dp.dp_eval(ctx, xg, tg, box, want_atom_energy=True)
+    assert max(rel_errors(g, o)) < TOL
+    assert np.all(g["force"].cpu().numpy()[-1] == 0.0)
+    # N = 1
+    ws1 = dict(coords=np.array([[1.0, 2.0, 3.0]]), types=np.array([0], np.int32), box=box)
+    o1 = oracle.evaluate(d, P, ws1["coords"], ws1["types"], box)
+    model1, ctx1, x1, t1 = gpu_run(dp, d, P, ws1)
+    g1 = dp.dp_eval(ctx1, x1, t1, box)
+    assert g1["energy"].item() == pytest.approx(o1["energy"], rel=TOL)
+    assert torch.all(g1["force"] == 0)
+
+
+def test_errors_are_reported(dp, synth):
+    w = synth.workload("water192")
+    d = w["model"]
+    P = synth.model_params(d, 0)
+    model, ctx, x, t = gpu_run(dp, d, P, w)
+    # non-orthorhombic cell
+    b = np.diag(w["box"]).copy()
+    b[0, 1] = 0.1
+    with pytest.raises(dp.DPError) as e:
+        dp.dp_eval(ctx, x, t, b)
+    assert e.value.status == -2
+    # cell too small for rcut + skin
+    with pytest.raises(dp.DPError) as e:
+        dp.dp_build_nlist(ctx, x, t, w["box"], skin=1.0)
+    assert e.value.status == -2
+    # type out of range
+    tb = t.clone()
+    tb[5] = 7
+    s = dp.dp_build_nlist(ctx, x, tb, w["box"], 0.0, check=False)
+    assert s == -11
+    # wrong parameter count
+    with pytest.raises(dp.DPError):
+        dp.Model(d, P[:-1])
+
+
+def test_model_file_round_trip(dp, oracle, synth, tmp_path):
+    w, d, P, o = oracle_eval(oracle, synth, "water192")
+    m1 = dp.Model(d, P)
+    path = str(tmp_path / "water.dpm")
+    m1.save(path)
+    m2 = dp.Model.load(path, desc=d)
+    ctx = dp.Context(m2, len(w["coords"]))
+    x = torch.tensor(w["coords"], device="cuda")
+    t = torch.tensor(w["types"], device="cuda")
+    g = dp.dp_eval(ctx, x, t, w["box"])
+    assert max(rel_errors(g, o)) < TOL
+    with open(path, "r+b") as f:
+        f.truncate(1000)
+    with pytest.raises(dp.DPError) as e:
+        dp.Model.load(path)
+    assert e.value.status == -6
+
+
+def test_md_parity_small(dp, oracle, synth):
+    """dp_md_step against the oracle's velocity Verlet (water192, rebuild every
+    step since the 12.42 A cell leaves no room for a skin)."""
+    w = synth.workload("water192")
+    d = w["model"]
+    P = synth.model_params(d, 0)
+    m = np.array(w["masses"])[w["types"]]
+    v0 = synth.maxwell_velocities(m, 300.0, seed=2)
+    n = 20
+    xo, vo, fo, tho, _ = oracle.md(d, P, w["coords"], v0, w["types"], w["box"], w["masses"], 0.5, n,
+                                   rebuild_every=1, skin=0.0)
+    model = dp.Model(d, P)
+    ctx = dp.Context(model, len(m))
+    x = torch.tensor(w["coords"], device="cuda")
+    v = torch.tensor(v0, device="cuda")
+    t = torch.tensor(w["types"], device="cuda")
+    th = torch.empty((n, 4), dtype=torch.float64, device="cuda")
+    dp.dp_md_step(ctx, x, v, t, w["box"], w["masses"], 0.5, n, rebuild_every=1, skin=0.0, thermo=th)
+    th = th.cpu().numpy()
+    np.testing.assert_allclose(th[:, 0], tho[:, 0], rtol=1e-9)
+    np.testing.assert_allclose(th[:, 1], tho[:, 1], rtol=1e-9)
+    np.testing.assert_allclose(th[:, 3], tho[:, 3], rtol=1e-8, atol=1e-12)
+    dx = x.cpu().numpy() - xo
+    dx -= w["box"] * np.round(dx / w["box"])
+    assert np.abs(dx).max() < 1e-9
+    np.testing.assert_allclose(v.cpu().numpy(), vo, atol=1e-10)
+
+
+def test_md_parity_with_skin(dp, oracle, synth):
+    """Skin list rebuilt every 10 steps (water648, 2 A skin), 30 steps."""
+    w = system(synth, "water648")
+    d = w["model"]
+    P = synth.model_params(d, 0)
+    m = np.array(w["masses"])[w["types"]]
+    v0 = synth.maxwell_velocities(m, 300.0, seed=2)
+    n = 30
+    xo, vo, fo, tho, st = oracle.md(d, P, w["coords"], v0, w["types"], w["box"], w["masses"], 0.5, n,
+                                    rebuild_every=10, skin=2.0)
+    model = dp.Model(d, P)
+    ctx = dp.Context(model, len(m))
+    x = torch.tensor(w["coords"], device="cuda")
+    v = torch.tensor(v0, device="cuda")
+    t = torch.tensor(w["types"], device="cuda")
+    th = torch.empty((n, 4), dtype=torch.float64, device="cuda")
+    # two calls of 15 steps: the context keeps the force and the step counter
+    dp.dp_md_step(ctx, x, v, t, w["box"], w["masses"], 0.5, 15, rebuild_every=10, skin=2.0, thermo=th[:15])
+    dp.dp_md_step(ctx, x, v, t, w["box"], w["masses"], 0.5, 15, rebuild_every=10, skin=2.0, thermo=th[15:])
+    th = th.cpu().numpy()
+    np.testing.assert_allclose(th[:, 0], tho[:, 0], rtol=1e-9)
+    np.testing.assert_allclose(th[:, 1], tho[:, 1], rtol=1e-9)
+    f = dp.dp_md_get_force(ctx, len(m)).cpu().numpy()
+    assert np.abs(f - fo).max() < 1e-8 * np.abs(fo).max()
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("name", ["water12288", "cu32000"])
+def test_full_size_parity(dp, oracle, synth, name):
+    """Full benchmark sizes (12,288-atom water, 32,000-atom copper): formatted
+    list bit-exact, E/F/virial within 1e-10 of the oracle."""
+    w, d, P, o = oracle_eval(oracle, synth, name)
+    model, ctx, x, t = gpu_run(dp, d, P, w, skin=2.0)
+    nl, nr, _ = dp.dp_format_nlist(ctx, x, t, w["box"])
+    np.testing.assert_array_equal(nl.cpu().numpy(), o["nlist"])
+    np.testing.assert_array_equal(nr.cpu().numpy(), o["nreal"])
+    g = dp.dp_eval(ctx, x, t, w["box"])
+    eE, eF, eV = rel_errors(g, o)
+    assert eE < TOL and eF < TOL and eV < TOL, (eE, eF, eV)

@@ -43,9 +43,13 @@ L2_BYTES = 129 * 1024 * 1024
 # The per-SM rate is the one that reproduces the nominal 1.25 TFLOP/s.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
-# DRAM bytes per launch of the dominant kernel from one ncu capture (see
-# profiles/); reported only while the kernel source is the one captured.
-TRAFFIC = {}
+# DRAM bytes per launch of the dominant kernel from one ncu capture;
+# reported only while the kernel source is the one captured.
+TRAFFIC = {
+    # ncu --set full, k_embed_bwd, one 12,288-atom water evaluation:
+    # dram__bytes_read.sum + dram__bytes_write.sum
+    "embed_bwd": {"bytes_per_launch": 207.849984e6 + 20.871680e6, "file": "embed.cu", "src_sha": "6034564e8b7128ac"},
+}
 
 
 def parse():
@@ -57,6 +61,8 @@ def parse():
     p.add_argument("--workload", default="water12288")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--profile-eval", type=int, default=0, metavar="N",
+                   help="run N energy/force evaluations of the workload and exit (profiling driver)")
     return p.parse_args()
 
 
@@ -241,9 +247,14 @@ def run_ours(args, rank, world, local_rank):
     th = torch.empty((MD_PER_STEP, 4), dtype=torch.float64, device=dev)
     flush = torch.empty(2 * L2_BYTES, dtype=torch.uint8, device=dev)
 
+    statuses = {}
+
     def step():
-        dp.dp_md_step(ctx, x, v, t, w["box"], w["masses"], DT_FS, MD_PER_STEP, rebuild_every=MD_PER_STEP,
-                      skin=SKIN, thermo=th)
+        _, s = dp.dp_md_step(ctx, x, v, t, w["box"], w["masses"], DT_FS, MD_PER_STEP, rebuild_every=MD_PER_STEP,
+                             skin=SKIN, thermo=th, check=False)
+        if s not in (0, -3, -4):  # anything but "results written" conditions is fatal
+            raise dp.DPError(s, dp.lib().dp_last_error().decode())
+        statuses[dp.STATUS_NAMES[s]] = statuses.get(dp.STATUS_NAMES[s], 0) + 1
 
     for _ in range(args.warmup):
         step()
@@ -363,6 +374,7 @@ def run_ours(args, rank, world, local_rank):
             "nve": {"etot_first": float(etot[0]), "etot_last": float(etot[-1]),
                     "max_abs_drift_eV_per_atom": float(np.abs(etot - etot[0]).max() / N),
                     "T_last_K": float(th_all[-1, 2])},
+            "status_counts": statuses,
             "clocks": clocks,
             "e2e": e2e,
             "cpu_baseline": cpu,
@@ -371,11 +383,32 @@ def run_ours(args, rank, world, local_rank):
     return 0
 
 
+def profile_eval(args):
+    """Small profiling driver: N x (candidate build + dp_eval) of the workload."""
+    import torch
+    from paper_2004_11658_gb300 import dp, synth
+    w = synth.workload(args.workload)
+    desc = w["model"]
+    model = dp.Model(desc, synth.model_params(desc, 0))
+    ctx = dp.Context(model, len(w["coords"]))
+    x = torch.tensor(w["coords"], device="cuda")
+    t = torch.tensor(w["types"], device="cuda")
+    for _ in range(args.profile_eval):
+        dp.dp_build_nlist(ctx, x, t, w["box"], SKIN)
+        out = dp.dp_eval(ctx, x, t, w["box"])
+    torch.cuda.synchronize()
+    print(f"profile-eval {args.workload}: {args.profile_eval} evaluations, E = {out['energy'].item():.10f}, "
+          f"{ctx.launches} launches")
+    return 0
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.profile_eval:
+        return profile_eval(args)
     if args.impl == "reference":
         return run_reference(args, rank, world)
     if world > 1:

@@ -165,14 +165,16 @@ dp_status dp_eval(dp_ctx *ctx, const double *coords, const int32_t *types, const
 
 /* nsteps of velocity-Verlet NVE (Sec. 4): v += F/m dt/2; x += v dt; wrap
  * into the cell; rebuild the candidates when the context's MD step counter
- * is a multiple of rebuild_every (and at the first step of a context);
+ * is a multiple of rebuild_every (and at the first step of a context), and
+ * also, with skin > 0, at any step where an atom has moved more than skin/2
+ * since the last build (checked on the device every step, no host sync);
  * Algorithm 1 + evaluation; v += F/m dt/2.  coords, vel: device [N][3],
  * updated in place.  mass_per_type: host [ntypes] (amu).  thermo: device
  * [nsteps][4] = (E_pot, E_kin, T, P) per step (eV, eV, K, eV/A^3,
  * P = (2 E_kin + tr Xi)/(3V), T with 3N-3 degrees of freedom) or NULL.
  * The force of the current coordinates is kept in the context between calls
- * (computed first when absent).  DP_ERR_NLIST_STALE if an atom moved more
- * than skin/2 from its reference position between rebuilds. */
+ * (computed first when absent).  With skin = 0 the list must be rebuilt
+ * every step (rebuild_every = 1) to stay exact. */
 dp_status dp_md_step(dp_ctx *ctx, double *coords, double *vel, const int32_t *types,
                      const double box[9], const double *mass_per_type, int64_t N,
                      double dt_fs, int32_t nsteps, int32_t rebuild_every, double skin,

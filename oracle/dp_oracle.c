@@ -608,10 +608,12 @@ int64_t orc_md(const int32_t *idesc, const double *ddesc, const double *params, 
     int32_t *nlist = malloc(sizeof(int32_t) * (size_t)N * nm);
     int32_t *nreal = malloc(sizeof(int32_t) * (size_t)N * T);
     int64_t *ovf = malloc(sizeof(int64_t) * (size_t)N);
+    double *xref = malloc(sizeof(double) * 3 * (size_t)N);
     int64_t status = 0;
     double E = 0.0, V[9];
     const double vol = box[0] * box[1] * box[2];
     if (orc_candidates(N, x, box, m.rcut + skin, cap, ncand, cand)) { status = -3; goto done; }
+    memcpy(xref, x, sizeof(double) * 3 * (size_t)N);
     if (!*have_force) {
         orc_format(N, x, types, box, ncand, cand, cap, T, m.sel, m.rcut, nlist, nreal, ovf);
         for (int64_t i = 0; i < N; ++i) status += ovf[i];
@@ -625,8 +627,20 @@ int64_t orc_md(const int32_t *idesc, const double *ddesc, const double *params, 
         }
         for (int64_t q = 0; q < 3 * N; ++q) x[q] += dt * v[q];
         orc_wrap(x, N, box);
-        if (rebuild_every > 0 && s % rebuild_every == 0)
+        int rebuild = rebuild_every > 0 && s % rebuild_every == 0;
+        if (!rebuild && skin > 0.0) {
+            /* rebuild early once an atom has moved more than skin/2 */
+            for (int64_t i = 0; i < N && !rebuild; ++i) {
+                double d[3];
+                orc_min_image(box, xref + 3 * i, x + 3 * i, d);
+                double r = orc_norm(d);
+                if (r * r > 0.25 * skin * skin) rebuild = 1;
+            }
+        }
+        if (rebuild) {
             if (orc_candidates(N, x, box, m.rcut + skin, cap, ncand, cand)) { status = -3; goto done; }
+            memcpy(xref, x, sizeof(double) * 3 * (size_t)N);
+        }
         orc_format(N, x, types, box, ncand, cand, cap, T, m.sel, m.rcut, nlist, nreal, ovf);
         for (int64_t i = 0; i < N; ++i) status += ovf[i];
         orc_eval(idesc, ddesc, params, N, x, types, box, nlist, &E, force, V, NULL, NULL);
@@ -649,7 +663,7 @@ int64_t orc_md(const int32_t *idesc, const double *ddesc, const double *params, 
         }
     }
 done:
-    free(ncand); free(cand); free(nlist); free(nreal); free(ovf);
+    free(ncand); free(cand); free(nlist); free(nreal); free(ovf); free(xref);
     return status;
 }
 

@@ -104,6 +104,7 @@ struct dp_ctx {
     int64_t launches;
     // device status word + pinned host mirror
     int32_t *d_status;
+    int32_t *d_gate;   // conditional-rebuild flag (0 between steps)
     int32_t *h_status;
     // neighbour candidates
     NlistBuffers nb;
@@ -286,7 +287,7 @@ dp_status check_common(dp_ctx *c, const double *coords, const int32_t *types, in
 }
 
 dp_status do_build(dp_ctx *c, const double *coords, const int32_t *types, const Box3 &b, int64_t N,
-                   double skin)
+                   double skin, bool gated = false)
 {
     if (!(skin >= 0.0)) return fail(DP_ERR_ARG, "skin must be >= 0");
     const double rlist = c->m.rcut + skin;
@@ -324,8 +325,12 @@ dp_status do_build(dp_ctx *c, const double *coords, const int32_t *types, const 
     }
     for (int a = 0; a < 3; ++a) c->nc[a] = nc[a];
     GroupTimer tm(c, G_BUILD);
-    cudaError_t e = dp_launch_build(c->stream, c->m, coords, types, b, (int)N, rlist, c->cap, nc, c->nb,
-                                    c->d_status, &c->launches);
+    cudaError_t e = cudaSuccess;
+    if (gated) e = dp_launch_check_stale(c->stream, coords, c->nb.xref, (int)N, b, 0.25 * skin * skin, c->d_gate,
+                                         &c->launches);
+    if (e == cudaSuccess)
+        e = dp_launch_build(c->stream, c->m, coords, types, b, (int)N, rlist, c->cap, nc, c->nb, c->d_status,
+                            gated ? c->d_gate : nullptr, &c->launches);
     if (e != cudaSuccess) return cuda_fail(e, "dp_build_nlist");
     c->nlist_valid = true;
     c->nlist_N = N;
@@ -548,6 +553,7 @@ void dp_ctx_free(dp_ctx *c)
     if (c->stream) cudaStreamSynchronize(c->stream);
     for (cudaEvent_t e : c->events) cudaEventDestroy(e);
     dev_free(c->d_status);
+    dev_free(c->d_gate);
     if (c->h_status) cudaFreeHost(c->h_status);
     if (c->h_mass_stage) cudaFreeHost(c->h_mass_stage);
     void *bufs[] = {c->nb.cand, c->nb.ncand, c->nb.xref, c->nb.cell_count, c->nb.cell_start,
@@ -588,6 +594,7 @@ dp_status dp_ctx_create(const dp_model *model, int64_t natoms_max, int32_t cand_
 #define ALLOC(ptr, n) \
     if (!s) s = dev_alloc(&(ptr), (n), #ptr)
     ALLOC(c->d_status, 1);
+    ALLOC(c->d_gate, 1);
     ALLOC(c->nb.ncand, N);
     ALLOC(c->nb.xref, 3 * N);
     ALLOC(c->nb.cell_atoms, N);
@@ -622,6 +629,7 @@ dp_status dp_ctx_create(const dp_model *model, int64_t natoms_max, int32_t cand_
     }
     if (!s) {
         cudaError_t e = cudaMemsetAsync(c->d_status, 0, sizeof(int32_t), c->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(c->d_gate, 0, sizeof(int32_t), c->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
         if (e != cudaSuccess) s = cuda_fail(e, "dp_ctx_create");
     }
@@ -786,8 +794,12 @@ dp_status dp_md_step(dp_ctx *c, double *coords, double *vel, const int32_t *type
         }
         if (e != cudaSuccess) return cuda_fail(e, "kick_drift");
         c->md_step += 1;
-        if (rebuild_every > 0 && c->md_step % rebuild_every == 0)
+        if (rebuild_every > 0 && c->md_step % rebuild_every == 0) {
             if ((s = do_build(c, coords, types, b, N, skin))) return s;
+        } else if (skin > 0.0) {
+            // rebuild on the device as soon as an atom has moved more than skin/2
+            if ((s = do_build(c, coords, types, b, N, skin, true))) return s;
+        }
         if ((s = enqueue_eval(c, coords, types, b, N, c->d_energy, c->md_force, c->d_virial, nullptr))) return s;
         {
             GroupTimer tm(c, G_MD);

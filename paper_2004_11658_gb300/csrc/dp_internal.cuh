@@ -123,9 +123,14 @@ struct FormatBuffers {
     int32_t *nreal;   // [N][ntypes]
 };
 
+// gate == nullptr: unconditional build; otherwise every kernel returns at
+// once unless *gate != 0, and the last one clears *gate.
 cudaError_t dp_launch_build(cudaStream_t st, const DevModel &m, const double *x, const int32_t *types,
                             Box3 box, int N, double rlist, int cap, int nc[3], NlistBuffers nb,
-                            int32_t *status, int64_t *launches);
+                            int32_t *status, int32_t *gate, int64_t *launches);
+// Sets *gate if an atom moved more than sqrt(stale2) from its reference position.
+cudaError_t dp_launch_check_stale(cudaStream_t st, const double *x, const double *xref, int N, Box3 box,
+                                  double stale2, int32_t *gate, int64_t *launches);
 cudaError_t dp_launch_format(cudaStream_t st, const DevModel &m, const double *x,
                              const int32_t *types, Box3 box, int N, int cap, double skin,
                              NlistBuffers nb, FormatBuffers fb, int32_t *status, int64_t *launches);

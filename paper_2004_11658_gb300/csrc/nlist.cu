@@ -27,11 +27,38 @@ __device__ __forceinline__ double wrap1(double v, double L)
     return __dsub_rn(v, __dmul_rn(L, n));
 }
 
+// Every build kernel takes a gate: with gate == nullptr it always runs; with a
+// device flag it returns at once unless the flag is set (device-side
+// conditional rebuild, no host round trip).
+#define DP_GATED(gate) \
+    if ((gate) != nullptr && *(gate) == 0) return
+
+__global__ void k_zero_cells(int32_t *__restrict__ cell_count, int ncell, const int32_t *gate)
+{
+    DP_GATED(gate);
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncell; c += gridDim.x * blockDim.x) cell_count[c] = 0;
+}
+
+// Sets *gate when an atom has moved more than skin/2 (squared: stale2) from
+// its position at the last build.
+__global__ void k_check_stale(const double *__restrict__ x, const double *__restrict__ xref, int N, Box3 box,
+                              double stale2, int32_t *gate)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    double d[3];
+    const double xr[3] = {xref[3 * i], xref[3 * i + 1], xref[3 * i + 2]};
+    const double xi[3] = {x[3 * i], x[3 * i + 1], x[3 * i + 2]};
+    const double r = dp_pinned_dist(xr, xi, box, d);
+    if (__dmul_rn(r, r) > stale2) *gate = 1;
+}
+
 __global__ void k_cell_assign(const double *__restrict__ x, const int32_t *__restrict__ types, int N,
                               int ntypes, Box3 box, int nx, int ny, int nz,
                               int32_t *__restrict__ cell_count, int32_t *__restrict__ atom_cell,
-                              int32_t *status)
+                              int32_t *status, const int32_t *gate)
 {
+    DP_GATED(gate);
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     int t = types[i];
@@ -50,8 +77,10 @@ __global__ void k_cell_assign(const double *__restrict__ x, const int32_t *__res
 
 // Exclusive scan of the cell counts by one CTA (ncell is at most a few 10^4).
 __global__ void k_cell_scan(const int32_t *__restrict__ cell_count, int ncell,
-                            int32_t *__restrict__ cell_start, int32_t *__restrict__ cell_cursor)
+                            int32_t *__restrict__ cell_start, int32_t *__restrict__ cell_cursor,
+                            const int32_t *gate)
 {
+    DP_GATED(gate);
     __shared__ int32_t part[1024];
     const int t = threadIdx.x, nt = blockDim.x;
     const int chunk = (ncell + nt - 1) / nt;
@@ -80,8 +109,9 @@ __global__ void k_cell_scan(const int32_t *__restrict__ cell_count, int ncell,
 
 __global__ void k_cell_fill(const int32_t *__restrict__ atom_cell, int N,
                             const int32_t *__restrict__ cell_start, int32_t *__restrict__ cell_cursor,
-                            int32_t *__restrict__ cell_atoms)
+                            int32_t *__restrict__ cell_atoms, const int32_t *gate)
 {
+    DP_GATED(gate);
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     int c = atom_cell[i];
@@ -92,8 +122,10 @@ __global__ void k_cell_fill(const int32_t *__restrict__ atom_cell, int N,
 // Order each cell's atoms by index (rank sort; cells hold ~10^2 atoms), so the
 // candidate order does not depend on the atomics of k_cell_fill.
 __global__ void k_cell_sort(const int32_t *__restrict__ cell_start, int ncell,
-                            const int32_t *__restrict__ cell_atoms, int32_t *__restrict__ cell_sorted)
+                            const int32_t *__restrict__ cell_atoms, int32_t *__restrict__ cell_sorted,
+                            const int32_t *gate)
 {
+    DP_GATED(gate);
     int c = blockIdx.x;
     if (c >= ncell) return;
     int b = cell_start[c], e = cell_start[c + 1], n = e - b;
@@ -118,8 +150,9 @@ __global__ void __launch_bounds__(128) k_cand_cells(
     const double *__restrict__ x, int N, Box3 box, int nx, int ny, int nz,
     const int32_t *__restrict__ atom_cell, const int32_t *__restrict__ cell_start,
     const int32_t *__restrict__ cell_sorted, double rlist, int cap, int32_t *__restrict__ cand,
-    int32_t *__restrict__ ncand, double *__restrict__ xref, int32_t *status)
+    int32_t *__restrict__ ncand, double *__restrict__ xref, int32_t *status, const int32_t *gate)
 {
+    DP_GATED(gate);
     const int lane = threadIdx.x & 31;
     const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (i >= N) return;
@@ -164,8 +197,10 @@ __global__ void __launch_bounds__(128) k_cand_brute(const double *__restrict__ x
                                                     double rlist, int cap,
                                                     int32_t *__restrict__ cand,
                                                     int32_t *__restrict__ ncand,
-                                                    double *__restrict__ xref, int32_t *status)
+                                                    double *__restrict__ xref, int32_t *status,
+                                                    const int32_t *gate)
 {
+    DP_GATED(gate);
     const int lane = threadIdx.x & 31;
     const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (i >= N) return;
@@ -195,8 +230,9 @@ __global__ void __launch_bounds__(128) k_cand_brute(const double *__restrict__ x
 // atoms in index order, then type-1 atoms, ...; type_start[a] is the offset.
 __global__ void k_type_perm(const int32_t *__restrict__ types, int N, int ntypes,
                             int32_t *__restrict__ type_perm, int32_t *__restrict__ type_start,
-                            int32_t *status)
+                            int32_t *status, int32_t *gate)
 {
+    DP_GATED(gate);
     __shared__ int32_t cnt[DP_MAX_TYPES][1024];
     const int t = threadIdx.x, nt = blockDim.x;
     const int chunk = (N + nt - 1) / nt;
@@ -250,6 +286,9 @@ __global__ void k_type_perm(const int32_t *__restrict__ types, int N, int ntypes
         for (int a = 0; a < DP_MAX_TYPES; ++a)
             if (a == ty) type_perm[pos[a]++] = i;
     }
+    // last kernel of a gated build: every thread has read the gate (the
+    // barriers above), so it can be cleared for the next step
+    if (gate != nullptr && t == 0) *gate = 0;
 }
 
 // ---------------------------------------------------------------- format --
@@ -402,31 +441,38 @@ __global__ void __launch_bounds__(128) k_format(
 
 cudaError_t dp_launch_build(cudaStream_t st, const DevModel &m, const double *x, const int32_t *types,
                             Box3 box, int N, double rlist, int cap, int nc[3], NlistBuffers nb,
-                            int32_t *status, int64_t *launches)
+                            int32_t *status, int32_t *gate, int64_t *launches)
 {
     const int TB = 256;
     const bool cells = nc[0] >= 3 && nc[1] >= 3 && nc[2] >= 3;
     const int wblocks = (N + 3) / 4;  // 4 warps (atoms) per 128-thread CTA
     if (cells) {
         const int ncell = nc[0] * nc[1] * nc[2];
-        cudaMemsetAsync(nb.cell_count, 0, sizeof(int32_t) * ncell, st);
+        k_zero_cells<<<(ncell + TB - 1) / TB, TB, 0, st>>>(nb.cell_count, ncell, gate);
         k_cell_assign<<<(N + TB - 1) / TB, TB, 0, st>>>(x, types, N, m.ntypes, box, nc[0], nc[1], nc[2],
-                                                        nb.cell_count, nb.atom_cell, status);
-        k_cell_scan<<<1, 1024, 0, st>>>(nb.cell_count, ncell, nb.cell_start, nb.cell_cursor);
+                                                        nb.cell_count, nb.atom_cell, status, gate);
+        k_cell_scan<<<1, 1024, 0, st>>>(nb.cell_count, ncell, nb.cell_start, nb.cell_cursor, gate);
         k_cell_fill<<<(N + TB - 1) / TB, TB, 0, st>>>(nb.atom_cell, N, nb.cell_start, nb.cell_cursor,
-                                                      nb.cell_atoms);
-        k_cell_sort<<<ncell, 128, 0, st>>>(nb.cell_start, ncell, nb.cell_atoms, nb.cell_sorted);
+                                                      nb.cell_atoms, gate);
+        k_cell_sort<<<ncell, 128, 0, st>>>(nb.cell_start, ncell, nb.cell_atoms, nb.cell_sorted, gate);
         k_cand_cells<<<wblocks, 128, 0, st>>>(x, N, box, nc[0], nc[1], nc[2], nb.atom_cell,
                                               nb.cell_start, nb.cell_sorted, rlist, cap, nb.cand,
-                                              nb.ncand, nb.xref, status);
-        *launches += 5;
+                                              nb.ncand, nb.xref, status, gate);
+        *launches += 6;
     } else {
-        // type check happens in k_cell_assign on the cell path; do it here too
         k_cand_brute<<<wblocks, 128, 0, st>>>(x, N, box, rlist, cap, nb.cand, nb.ncand, nb.xref,
-                                              status);
+                                              status, gate);
         *launches += 1;
     }
-    k_type_perm<<<1, 1024, 0, st>>>(types, N, m.ntypes, nb.type_perm, nb.type_start, status);
+    k_type_perm<<<1, 1024, 0, st>>>(types, N, m.ntypes, nb.type_perm, nb.type_start, status, gate);
+    *launches += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t dp_launch_check_stale(cudaStream_t st, const double *x, const double *xref, int N, Box3 box,
+                                  double stale2, int32_t *gate, int64_t *launches)
+{
+    k_check_stale<<<(N + 255) / 256, 256, 0, st>>>(x, xref, N, box, stale2, gate);
     *launches += 1;
     return cudaGetLastError();
 }

@@ -45,6 +45,15 @@ def oracle_eval(oracle, synth, name, desc=None, seed=0):
     return _oracle_cache[key]
 
 
+def oracle_nlist(oracle, w, desc, skin):
+    """Algorithm 1 by the oracle from candidates built with rcut + skin."""
+    cap = oracle.default_cap(desc, w["box"], len(w["coords"]), skin)
+    ncand, cand, over = oracle.candidates(w["coords"], w["box"], desc["rcut"] + skin, cap)
+    assert over == 0
+    nl, nr, _ = oracle.format_nlist(w["coords"], w["types"], w["box"], ncand, cand, desc["sel"], desc["rcut"])
+    return nl, nr
+
+
 def gpu_run(dp, desc, P, w, skin=0.0, cand_cap=0):
     N = len(w["coords"])
     model = dp.Model(desc, P)
@@ -85,12 +94,17 @@ def test_eval_parity(dp, oracle, synth, name):
 
 
 def test_eval_with_skin_list_matches(dp, oracle, synth):
-    """Candidates built with a 2 A skin give the same result (Algorithm 1
-    re-sorts and truncates them every evaluation)."""
+    """Candidates built with a 2 A skin: the formatted list also holds the
+    candidates between rcut and rcut + skin that fit sel (zero rows), so it is
+    compared with the oracle's list from the same candidates; the energy,
+    forces and virial equal those of the rcut-only list."""
     w, d, P, o = oracle_eval(oracle, synth, "water648")
     model, ctx, x, t = gpu_run(dp, d, P, w, skin=2.0)
     nl, nr, _ = dp.dp_format_nlist(ctx, x, t, w["box"])
-    np.testing.assert_array_equal(nl.cpu().numpy(), o["nlist"])
+    onl, onr = oracle_nlist(oracle, w, d, 2.0)
+    np.testing.assert_array_equal(nl.cpu().numpy(), onl)
+    np.testing.assert_array_equal(nr.cpu().numpy(), onr)
+    np.testing.assert_array_equal(nr.cpu().numpy(), o["nreal"])
     g = dp.dp_eval(ctx, x, t, w["box"])
     assert max(rel_errors(g, o)) < TOL
 
@@ -174,6 +188,8 @@ def test_errors_are_reported(dp, synth):
     tb[5] = 7
     s = dp.dp_build_nlist(ctx, x, tb, w["box"], 0.0, check=False)
     assert s == -11
+    g = dp.dp_eval(ctx, x, tb, w["box"], check=False)
+    assert g["status"] == -11
     # wrong parameter count
     with pytest.raises(dp.DPError):
         dp.Model(d, P[:-1])
@@ -259,8 +275,38 @@ def test_full_size_parity(dp, oracle, synth, name):
     w, d, P, o = oracle_eval(oracle, synth, name)
     model, ctx, x, t = gpu_run(dp, d, P, w, skin=2.0)
     nl, nr, _ = dp.dp_format_nlist(ctx, x, t, w["box"])
-    np.testing.assert_array_equal(nl.cpu().numpy(), o["nlist"])
-    np.testing.assert_array_equal(nr.cpu().numpy(), o["nreal"])
+    onl, onr = oracle_nlist(oracle, w, d, 2.0)
+    np.testing.assert_array_equal(nl.cpu().numpy(), onl)
+    np.testing.assert_array_equal(nr.cpu().numpy(), onr)
     g = dp.dp_eval(ctx, x, t, w["box"])
     eE, eF, eV = rel_errors(g, o)
     assert eE < TOL and eF < TOL and eV < TOL, (eE, eF, eV)
+
+
+def test_md_parity_early_rebuild(dp, oracle, synth):
+    """With a 0.5 A skin and a rebuild period longer than the run, the list is
+    rebuilt on the device whenever an atom has moved more than skin/2; the
+    oracle applies the same rule."""
+    w = system(synth, "water648")
+    d = w["model"]
+    P = synth.model_params(d, 0)
+    m = np.array(w["masses"])[w["types"]]
+    v0 = synth.maxwell_velocities(m, 600.0, seed=3)
+    n = 40
+    xo, vo, fo, tho, st = oracle.md(d, P, w["coords"], v0, w["types"], w["box"], w["masses"], 0.5, n,
+                                    rebuild_every=1000, skin=0.5)
+    model = dp.Model(d, P)
+    ctx = dp.Context(model, len(m))
+    x = torch.tensor(w["coords"], device="cuda")
+    v = torch.tensor(v0, device="cuda")
+    t = torch.tensor(w["types"], device="cuda")
+    th = torch.empty((n, 4), dtype=torch.float64, device="cuda")
+    builds0 = ctx.launches
+    dp.dp_md_step(ctx, x, v, t, w["box"], w["masses"], 0.5, n, rebuild_every=1000, skin=0.5, thermo=th)
+    th = th.cpu().numpy()
+    np.testing.assert_allclose(th[:, 0], tho[:, 0], rtol=1e-9)
+    np.testing.assert_allclose(th[:, 1], tho[:, 1], rtol=1e-9)
+    dx = x.cpu().numpy() - xo
+    dx -= w["box"] * np.round(dx / w["box"])
+    assert np.abs(dx).max() < 1e-9
+    assert ctx.launches > builds0

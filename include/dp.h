@@ -153,6 +153,34 @@ dp_status dp_build_nlist(dp_ctx *ctx, const double *coords, const int32_t *types
 dp_status dp_format_nlist(dp_ctx *ctx, const double *coords, const int32_t *types,
                           const double box[9], int64_t N, int32_t *nlist, int32_t *nreal);
 
+/* No-allocation variant of dp_format_nlist.  The paper has no counterpart:
+ * this entry point exists for callers that cannot allocate device memory at
+ * the time they need the list -- a host MD engine that owns a fixed device
+ * budget and forbids allocations after start-up, or code running where
+ * cudaMalloc is not allowed.  It needs no context and no model object: it
+ * reads the descriptor (ntypes, sel, rcut) from the host struct, builds the
+ * candidates (all j != i with minimum-image |r_ij| <= rcut + skin) by brute
+ * force and runs Algorithm 1, writing the same nlist[N][N_m] and
+ * nreal[N][ntypes] (device, caller-owned, both required) as dp_format_nlist
+ * for the same candidate radius.  coords, types: device; box: host double[9];
+ * stream: cudaStream_t (NULL = legacy default stream); the call returns after
+ * the stream has finished the work.
+ * Scratch: one file-scope device array of fixed size (about 21 MB) that every
+ * GPU loading the library holds until the process exits; it bounds
+ * N <= DP_NOALLOC_MAX_ATOMS and the candidates of an atom to
+ * DP_NOALLOC_CAND_CAP.  Larger N gives DP_ERR_CAPACITY before any work, more
+ * candidates give DP_ERR_CAPACITY after it.  The call makes no cudaMalloc,
+ * cudaFree or other allocating call.  Its first call on a device looks up
+ * the array's device address (cudaGetSymbolAddress) with that device
+ * current, so make that first call before any stream capture.  All calls
+ * share the array, which keeps the last call's contents: calls that overlap
+ * on the GPU (other streams, other host threads) race and must not be made. */
+#define DP_NOALLOC_MAX_ATOMS 2048
+#define DP_NOALLOC_CAND_CAP 512
+dp_status dp_format_nlist_noalloc(const dp_model_desc *desc, const double *coords,
+                                  const int32_t *types, const double box[9], int64_t N,
+                                  double skin, int32_t *nlist, int32_t *nreal, void *stream);
+
 /* Energy, forces and virial (Sec. 2; Algorithms 1 and 2; Eqs. embedding,
  * descrpt, fitting; Remark 2).  energy: device double[1]; force: device
  * [N][3]; virial: device double[9], Xi[a][b] = -sum_{i,j} r_ij[a] dE_i/dr_ij[b]

@@ -387,6 +387,10 @@ dp_status enqueue_eval(dp_ctx *c, const double *coords, const int32_t *types, co
 
 }  // namespace
 
+// Lets other translation units (the no-allocation entry point) report errors
+// through dp_last_error().
+void dp_set_last_error(const char *msg) { g_last_error = msg; }
+
 extern "C" {
 
 const char *dp_last_error(void) { return g_last_error.c_str(); }

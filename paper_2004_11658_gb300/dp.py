@@ -94,6 +94,9 @@ def lib():
             L.dp_ctx_kernel_times.argtypes = [_vp, _vp, _vp]
             L.dp_kernel_group_name.restype = ctypes.c_char_p
             L.dp_kernel_group_name.argtypes = [_i32]
+            L.dp_format_nlist_noalloc.restype = _i32
+            L.dp_format_nlist_noalloc.argtypes = [ctypes.POINTER(dp_model_desc), _vp, _vp, _vp, _i64, _dbl,
+                                                  _vp, _vp, _vp]
             _lib = L
     return _lib
 
@@ -258,6 +261,30 @@ def dp_format_nlist(ctx, coords, types, box, check=True):
     s = lib().dp_format_nlist(ctx.handle, _dev(coords, torch.float64, (N, 3), "coords"),
                               _dev(types, torch.int32, (N,), "types"), b.ctypes.data_as(_vp), N,
                               _dev(nlist, torch.int32), _dev(nreal, torch.int32))
+    if check:
+        _check(s)
+    return nlist, nreal, s
+
+
+def dp_format_nlist_noalloc(desc, coords, types, box, skin=0.0, nlist=None, nreal=None, stream=None,
+                            check=True):
+    """Algorithm 1 with no device allocation inside the library (see
+    include/dp.h); returns (nlist [N, N_m], nreal [N, ntypes], status).  The
+    output tensors are the caller's (allocated here only when not given)."""
+    N = coords.shape[0]
+    c = make_desc(desc)
+    nm = int(sum(desc["sel"]))
+    if nlist is None:
+        nlist = torch.empty((N, nm), dtype=torch.int32, device=coords.device)
+    if nreal is None:
+        nreal = torch.empty((N, desc["ntypes"]), dtype=torch.int32, device=coords.device)
+    st = stream if stream is not None else torch.cuda.current_stream()
+    b = _box9(box)
+    s = lib().dp_format_nlist_noalloc(ctypes.byref(c), _dev(coords, torch.float64, (N, 3), "coords"),
+                                      _dev(types, torch.int32, (N,), "types"), b.ctypes.data_as(_vp), N,
+                                      float(skin), _dev(nlist, torch.int32, (N, nm), "nlist"),
+                                      _dev(nreal, torch.int32, (N, desc["ntypes"]), "nreal"),
+                                      ctypes.c_void_p(st.cuda_stream))
     if check:
         _check(s)
     return nlist, nreal, s

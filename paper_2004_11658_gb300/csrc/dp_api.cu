@@ -77,6 +77,16 @@ dp_status check_desc(const dp_model_desc *d)
     if (d->fit[0] == d->m2 * M || d->fit[0] == 2 * d->m2 * M)
         return fail(DP_ERR_UNSUPPORTED, "a skip connection on the first fitting layer is not supported");
     if (d->desc_scale_nm != 0 && d->desc_scale_nm != 1) return fail(DP_ERR_ARG, "desc_scale_nm must be 0 or 1");
+    {
+        // shared memory of the fitting kernel: chunks, activations and one
+        // tanh buffer per layer (16 atoms x (max width + 1) doubles each)
+        int maxf = 0;
+        for (int l = 0; l < d->n_fit; ++l) maxf = d->fit[l] > maxf ? d->fit[l] : maxf;
+        const long ldw = 16L * (maxf + 1) > 17L * maxf ? 16L * (maxf + 1) : 17L * maxf;
+        const long bytes = 8L * (2 * 16 * 17 + 2 * ldw + (2L + d->n_fit) * 16 * (maxf + 1));
+        if (bytes > 227L * 1024)
+            return fail(DP_ERR_UNSUPPORTED, "fitting net too wide/deep for the fitting kernel's shared memory");
+    }
     if (!(d->rcut > 0.0) || !(d->rcut_smth >= 0.0) || !(d->rcut_smth < d->rcut))
         return fail(DP_ERR_ARG, "need 0 <= rcut_smth < rcut");
     return DP_OK;

@@ -61,6 +61,7 @@ def parse():
     p.add_argument("--workload", default="water12288")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision measurement")
     p.add_argument("--profile-eval", type=int, default=0, metavar="N",
                    help="run N energy/force evaluations of the workload and exit (profiling driver)")
     return p.parse_args()
@@ -226,6 +227,97 @@ def cpu_baseline(w, desc, P):
 
 # ------------------------------------------------------------------ ours --
 
+def mixed_kernel_flops(desc, rows, natoms):
+    """Per-launch work of the mixed-precision kernels, split by unit:
+    tensor-core FLOPs (BF16 GEMMs, unpadded) and FP64 FLOPs (contractions)."""
+    M, m2 = desc["emb"][-1], desc["m2"]
+    g = emb_row_flops(desc) - 2 * desc["emb"][0]   # layer 0 runs on the CUDA cores
+    return {
+        "embed_fwd": {"tensor": rows * g, "fp64": rows * 8 * M + natoms * 8 * m2 * M},
+        "embed_bwd": {"tensor": rows * 2 * g, "fp64": rows * 16 * M + natoms * 16 * m2 * M},
+        "fit": {"tensor": natoms * 2 * fit_atom_flops(desc), "fp64": 0},
+    }
+
+
+def measure_mixed(args, dp, synth, w, desc, P, v0, dev, world, flush):
+    """Mixed-precision MD on the same workload: throughput, per-kernel times,
+    roofline of the dominant kernel and accuracy against the FP64 path."""
+    import torch
+    N = len(v0)
+    model = dp.Model(desc, P)
+    ctx = dp.Context(model, N, precision=dp.DP_PREC_MIXED)
+    ref = dp.Context(model, N)
+    x = torch.tensor(w["coords"], dtype=torch.float64, device=dev)
+    v = torch.tensor(v0, dtype=torch.float64, device=dev)
+    t = torch.tensor(w["types"], dtype=torch.int32, device=dev)
+    # accuracy on the initial configuration, same candidates
+    dp.dp_build_nlist(ctx, x, t, w["box"], SKIN)
+    dp.dp_build_nlist(ref, x, t, w["box"], SKIN)
+    a = dp.dp_eval(ctx, x, t, w["box"])
+    b = dp.dp_eval(ref, x, t, w["box"])
+    dF = (a["force"] - b["force"]).double()
+    rmse = float(dF.pow(2).mean().sqrt())
+    frms = float(b["force"].pow(2).mean().sqrt())
+    e_err = abs(a["energy"].item() - b["energy"].item()) / N
+    v_err = float((a["virial"] - b["virial"]).abs().max() / b["virial"].abs().max())
+    del ref
+    th = torch.empty((MD_PER_STEP, 4), dtype=torch.float64, device=dev)
+
+    def step():
+        dp.dp_md_step(ctx, x, v, t, w["box"], w["masses"], DT_FS, MD_PER_STEP, rebuild_every=MD_PER_STEP,
+                      skin=SKIN, thermo=th, check=False)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    ctx.set_timing(1)
+    evs, thermo_all = [], []
+    for k in range(args.steps):
+        flush.fill_(k & 0xFF)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        step()
+        e1.record()
+        evs.append((e0, e1))
+        thermo_all.append(th.clone())
+    torch.cuda.synchronize()
+    kt = ctx.kernel_times()
+    ctx.set_timing(0)
+    total_ms = sum(e0.elapsed_time(e1) for e0, e1 in evs)
+    nl, nr, _ = dp.dp_format_nlist(ctx, x, t, w["box"], check=False)
+    rows = int(nr.sum().item())
+    fl = mixed_kernel_flops(desc, rows, N)
+    groups = {g: {"ms": ms, "launches": n} for g, (ms, n) in kt.items() if n > 0}
+    dom = max(groups, key=lambda g: groups[g]["ms"])
+    roof = None
+    if dom in fl:
+        sec = groups[dom]["ms"] / groups[dom]["launches"] / 1000.0
+        pk = measured_peaks()
+        bf16_peak = pk.get("bf16_tflops", 1886.6)
+        ach_t = fl[dom]["tensor"] / sec / 1e12
+        ach_d = fl[dom]["fp64"] / sec / 1e12
+        ft, fd = ach_t / bf16_peak, ach_d / FP64_PEAK_TFLOPS
+        roof = {"bound": "alu" if fd >= ft else "tensor", "kernel": dom,
+                "achieved": ach_d if fd >= ft else ach_t,
+                "peak": FP64_PEAK_TFLOPS if fd >= ft else bf16_peak, "unit": "TFLOP/s",
+                "frac": max(fd, ft), "traffic": None,
+                "fp64": {"achieved": ach_d, "peak": FP64_PEAK_TFLOPS, "frac": fd},
+                "tensor_bf16": {"achieved": ach_t, "peak": bf16_peak, "frac": ft,
+                                "peak_source": "MEASURED_PEAKS bf16_tflops (burst, of measured)"}}
+    th_all = torch.stack(thermo_all).cpu().numpy().reshape(-1, 4)
+    etot = th_all[:, 0] + th_all[:, 1]
+    return {"value": world * N * MD_PER_STEP * args.steps / (total_ms / 1000.0), "unit": METRIC,
+            "ms_per_step": total_ms / args.steps, "dtype": "bf16 GEMMs (fp32 accumulate) + f64",
+            "kernels_ms_per_step": {g: d["ms"] / args.steps for g, d in groups.items()},
+            "roofline": roof,
+            "accuracy_vs_fp64": {"force_rmse_eV_per_A": rmse, "force_rms_eV_per_A": frms,
+                                 "rel_force_rmse": rmse / frms if frms > 0 else None,
+                                 "energy_err_eV_per_atom": e_err, "virial_rel_err": v_err},
+            "nve": {"max_abs_drift_eV_per_atom": float(np.abs(etot - etot[0]).max() / N),
+                    "T_last_K": float(th_all[-1, 2])}}
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     import torch.distributed as dist
@@ -354,6 +446,10 @@ def run_ours(args, rank, world, local_rank):
                "h2d_bytes_per_step": int(2 * N * 3 * 8 + N * 4),
                "d2h_bytes_per_step": int(2 * N * 3 * 8 + th_h_bytes)}
 
+    modes = {}
+    if not args.no_mixed:
+        modes["mixed"] = measure_mixed(args, dp, synth, w, desc, P, v0, dev, world, flush)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(w, desc, P)
@@ -378,6 +474,7 @@ def run_ours(args, rank, world, local_rank):
             "clocks": clocks,
             "e2e": e2e,
             "cpu_baseline": cpu,
+            "modes": modes,
         }
         print(json.dumps(line), flush=True)
     return 0

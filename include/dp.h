@@ -81,6 +81,15 @@ typedef struct dp_ctx dp_ctx;
 
 /* Precision modes of a context. */
 #define DP_PREC_FP64  0   /* every step in float64 */
+#define DP_PREC_MIXED 1   /* embedding- and fitting-net GEMMs on the tensor cores
+                             (BF16 operands, FP32 accumulation, FP32 tanh); the
+                             environment matrix, the descriptor contraction
+                             T = R~^T G / N_m and D, the backward contractions,
+                             forces, virial, energy sum and the integrator in
+                             FP64.  Needs a 3-layer doubling embedding net with
+                             s_1 in {16, 25, 32} and equal fitting widths
+                             (multiples of 16, <= 256) after the first layer;
+                             other shapes give DP_ERR_UNSUPPORTED. */
 
 /* Thread-local text of the last error (never NULL). */
 const char *dp_last_error(void);

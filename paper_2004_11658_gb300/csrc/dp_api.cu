@@ -129,6 +129,10 @@ struct dp_ctx {
     // MD state
     double *md_force, *ke_part, *d_inv_mass_conv, *d_mass, *h_mass_stage;
     double last_mass[DP_MAX_TYPES];
+    // mixed precision: BF16 / FP32 copies of the parameters
+    MixedModel mx;
+    float *d_p32;
+    unsigned char *d_emb_ops, *d_fit_fwd, *d_fit_bwd;
     bool md_force_valid;
     int64_t md_N;
     int64_t md_step;
@@ -231,6 +235,97 @@ dp_status finish(dp_ctx *c)
 }
 
 enum { G_BUILD = 0, G_FORMAT, G_EMBED_FWD, G_FIT, G_EMBED_BWD, G_FORCE, G_REDUCE, G_MD };
+
+// float -> bfloat16 bits, round to nearest even (NaN kept quiet)
+uint16_t to_bf16(float f)
+{
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    if ((u & 0x7fffffffu) > 0x7f800000u) return 0x7fc0;
+    u += 0x7fffu + ((u >> 16) & 1u);
+    return (uint16_t)(u >> 16);
+}
+
+// element offset of (row, k) in the tensor-core K-major layout with K columns
+size_t kofs(int row, int k, int K)
+{
+    return (size_t)(row >> 3) * K * 8 + (size_t)(k >> 3) * 64 + (size_t)(row & 7) * 8 + (size_t)(k & 7);
+}
+
+int pad_to(int v, int q) { return (v + q - 1) / q * q; }
+
+// BF16 operands of the tensor-core kernels and an FP32 copy of every
+// parameter, built once per context from the model's host parameters.
+dp_status build_mixed(dp_ctx *c)
+{
+    const dp_model *md = c->model;
+    const DevModel &m = c->m;
+    const double *P = md->h_params;
+    const int T = m.ntypes, e1 = m.emb[0], e2 = m.emb[1], e3 = m.emb[2];
+    const int K1p = pad_to(e1, 16), N1p = pad_to(e2, 16), K2p = N1p, N2p = pad_to(e3, 16);
+    MixedModel &mx = c->mx;
+    std::memset(&mx, 0, sizeof(mx));
+    // embedding: per net W1^T [N1p][K1p], W2^T [N2p][K2p]
+    const size_t b1 = (size_t)N1p * K1p, b2 = (size_t)N2p * K2p;
+    const size_t net_elems = pad_to((int)(b1 + b2), 128);
+    std::vector<uint16_t> emb((size_t)T * T * net_elems, 0);
+    for (int net = 0; net < T * T; ++net) {
+        const double *W1 = P + m.emb_base[net] + 2 * e1;
+        const double *W2 = W1 + (size_t)e1 * e2 + e2;
+        uint16_t *o1 = emb.data() + net * net_elems, *o2 = o1 + b1;
+        for (int n = 0; n < e2; ++n)
+            for (int k = 0; k < e1; ++k) o1[kofs(n, k, K1p)] = to_bf16((float)W1[(size_t)k * e2 + n]);
+        for (int n = 0; n < e3; ++n)
+            for (int k = 0; k < e2; ++k) o2[kofs(n, k, K2p)] = to_bf16((float)W2[(size_t)k * e3 + n]);
+        mx.emb_off[net][0] = (int64_t)(net * net_elems) * 2;
+        mx.emb_off[net][1] = (int64_t)(net * net_elems + b1) * 2;
+    }
+    // fitting: per type and layer, W^T (forward) and W (backward), K-chunks of 64
+    const int K1 = m.m2 * m.M;
+    std::vector<uint16_t> fwd, bwd;
+    for (int a = 0; a < T; ++a) {
+        const double *W = P + m.fit_base[a];
+        int kin = K1;
+        for (int l = 0; l < m.n_fit; ++l) {
+            const int F = m.fit[l];
+            const int Np = pad_to(F, 16), Kp = pad_to(kin, 64), Kinp = pad_to(kin, 16), Fp = pad_to(F, 64);
+            mx.fit_np[l] = Np;
+            mx.fit_kp[l] = Kp;
+            mx.fit_kinp[l] = Kinp;
+            mx.fit_fp[l] = Fp;
+            size_t f0 = fwd.size(), g0 = bwd.size();
+            fwd.resize(f0 + (size_t)Kp * Np, 0);
+            bwd.resize(g0 + (size_t)Fp * Kinp, 0);
+            mx.fit_fwd_off[a][l] = (int64_t)f0 * 2;
+            mx.fit_bwd_off[a][l] = (int64_t)g0 * 2;
+            for (int k = 0; k < kin; ++k)
+                for (int n = 0; n < F; ++n) {
+                    const uint16_t v = to_bf16((float)W[(size_t)k * F + n]);
+                    fwd[f0 + (size_t)(k / 64) * Np * 64 + kofs(n, k % 64, 64)] = v;   // element (n, k) of W^T
+                    bwd[g0 + (size_t)(n / 64) * Kinp * 64 + kofs(k, n % 64, 64)] = v;  // element (k, n) of W
+                }
+            W += (size_t)kin * F + F;
+            kin = F;
+        }
+    }
+    std::vector<float> p32((size_t)md->nparams);
+    for (int64_t q = 0; q < md->nparams; ++q) p32[q] = (float)P[q];
+    dp_status s = DP_OK;
+    if ((s = dev_alloc(&c->d_p32, p32.size(), "fp32 params"))) return s;
+    if ((s = dev_alloc(&c->d_emb_ops, emb.size() * 2, "bf16 embedding operands"))) return s;
+    if ((s = dev_alloc(&c->d_fit_fwd, fwd.size() * 2, "bf16 fitting operands"))) return s;
+    if ((s = dev_alloc(&c->d_fit_bwd, bwd.size() * 2, "bf16 fitting operands"))) return s;
+    DP_CUDA(cudaMemcpy(c->d_p32, p32.data(), p32.size() * 4, cudaMemcpyHostToDevice), "mixed operands");
+    DP_CUDA(cudaMemcpy(c->d_emb_ops, emb.data(), emb.size() * 2, cudaMemcpyHostToDevice), "mixed operands");
+    DP_CUDA(cudaMemcpy(c->d_fit_fwd, fwd.data(), fwd.size() * 2, cudaMemcpyHostToDevice), "mixed operands");
+    DP_CUDA(cudaMemcpy(c->d_fit_bwd, bwd.data(), bwd.size() * 2, cudaMemcpyHostToDevice), "mixed operands");
+    mx.p32 = c->d_p32;
+    mx.emb_ops = c->d_emb_ops;
+    mx.fit_fwd = c->d_fit_fwd;
+    mx.fit_bwd = c->d_fit_bwd;
+    (void)K2p;
+    return DP_OK;
+}
 
 dp_status flush_spans(dp_ctx *c)
 {
@@ -363,22 +458,28 @@ dp_status enqueue_eval(dp_ctx *c, const double *coords, const int32_t *types, co
     dp_status s = enqueue_format(c, coords, types, b, N);
     if (s) return s;
     cudaError_t e;
+    const bool mixed = c->precision == DP_PREC_MIXED;
     {
         GroupTimer tm(c, G_EMBED_FWD);
-        if ((e = dp_launch_embed_fwd(c->stream, c->m, coords, types, b, (int)N, c->fb, c->nb, c->eb, c->num_sms,
-                                     &c->launches)) != cudaSuccess)
-            return cuda_fail(e, "embed_fwd");
+        e = mixed ? dp_launch_embed_fwd_mx(c->stream, c->m, c->mx, coords, types, b, (int)N, c->fb, c->nb, c->eb,
+                                           c->num_sms, c->d_status, &c->launches)
+                  : dp_launch_embed_fwd(c->stream, c->m, coords, types, b, (int)N, c->fb, c->nb, c->eb, c->num_sms,
+                                        &c->launches);
+        if (e != cudaSuccess) return cuda_fail(e, "embed_fwd");
     }
     {
         GroupTimer tm(c, G_FIT);
-        if ((e = dp_launch_fit(c->stream, c->m, (int)N, c->nb, c->eb, &c->launches)) != cudaSuccess)
-            return cuda_fail(e, "fit");
+        e = mixed ? dp_launch_fit_mx(c->stream, c->m, c->mx, (int)N, c->nb, c->eb, c->d_status, &c->launches)
+                  : dp_launch_fit(c->stream, c->m, (int)N, c->nb, c->eb, &c->launches);
+        if (e != cudaSuccess) return cuda_fail(e, "fit");
     }
     {
         GroupTimer tm(c, G_EMBED_BWD);
-        if ((e = dp_launch_embed_bwd(c->stream, c->m, coords, types, b, (int)N, c->fb, c->nb, c->eb, c->num_sms,
-                                     &c->launches)) != cudaSuccess)
-            return cuda_fail(e, "embed_bwd");
+        e = mixed ? dp_launch_embed_bwd_mx(c->stream, c->m, c->mx, coords, types, b, (int)N, c->fb, c->nb, c->eb,
+                                           c->num_sms, c->d_status, &c->launches)
+                  : dp_launch_embed_bwd(c->stream, c->m, coords, types, b, (int)N, c->fb, c->nb, c->eb, c->num_sms,
+                                        &c->launches);
+        if (e != cudaSuccess) return cuda_fail(e, "embed_bwd");
     }
     {
         GroupTimer tm(c, G_FORCE);
@@ -574,7 +675,8 @@ void dp_ctx_free(dp_ctx *c)
                     c->nb.cell_cursor, c->nb.cell_atoms, c->nb.cell_sorted, c->nb.atom_cell,
                     c->nb.type_perm, c->nb.type_start, c->fb.nlist, c->fb.keys, c->fb.nreal,
                     c->eb.T, c->eb.D, c->eb.gD, c->eb.Ei, c->eb.pair_g, c->eb.f_own, c->eb.vir_part,
-                    c->d_energy, c->d_virial, c->md_force, c->ke_part, c->d_inv_mass_conv, c->d_mass};
+                    c->d_energy, c->d_virial, c->md_force, c->ke_part, c->d_inv_mass_conv, c->d_mass,
+                    c->eb.fit_t, c->eb.fit_h, c->d_p32, c->d_emb_ops, c->d_fit_fwd, c->d_fit_bwd};
     for (void *p : bufs) dev_free(p);
     delete c;
 }
@@ -587,7 +689,11 @@ dp_status dp_ctx_create(const dp_model *model, int64_t natoms_max, int32_t cand_
     if (!model) return fail(DP_ERR_ARG, "model is NULL");
     if (natoms_max < 1 || natoms_max >= (1 << 26)) return fail(DP_ERR_ARG, "natoms_max must be in [1, 2^26)");
     if (cand_cap < 0 || cand_cap > 1024) return fail(DP_ERR_ARG, "cand_cap must be in [0, 1024]");
-    if (precision != DP_PREC_FP64) return fail(DP_ERR_UNSUPPORTED, "precision mode not available");
+    if (precision != DP_PREC_FP64 && precision != DP_PREC_MIXED)
+        return fail(DP_ERR_UNSUPPORTED, "unknown precision mode");
+    if (precision == DP_PREC_MIXED && !dp_mixed_supported(model->dev))
+        return fail(DP_ERR_UNSUPPORTED, "mixed precision needs a 3-layer doubling embedding net (s_1 in {16, 25, 32}) "
+                                        "and equal fitting widths (multiples of 16, <= 256) after the first layer");
     dp_ctx *c = new (std::nothrow) dp_ctx();
     if (!c) return fail(DP_ERR_NOMEM, "host allocation failed");
     c->model = model;
@@ -632,7 +738,12 @@ dp_status dp_ctx_create(const dp_model *model, int64_t natoms_max, int32_t cand_
     ALLOC(c->ke_part, N);
     ALLOC(c->d_inv_mass_conv, DP_MAX_TYPES);
     ALLOC(c->d_mass, DP_MAX_TYPES);
+    if (precision == DP_PREC_MIXED) {
+        ALLOC(c->eb.fit_t, N * (size_t)c->m.n_fit * 256);
+        ALLOC(c->eb.fit_h, N * 256);
+    }
 #undef ALLOC
+    if (!s && precision == DP_PREC_MIXED) s = build_mixed(c);
     if (!s && cudaMallocHost((void **)&c->h_status, sizeof(int32_t)) != cudaSuccess) {
         c->h_status = nullptr;
         s = fail(DP_ERR_NOMEM, "pinned allocation failed");
@@ -706,6 +817,7 @@ dp_status dp_ctx_status(dp_ctx *c)
     DP_CUDA(cudaStreamSynchronize(c->stream), "status read");
     const int32_t f = *c->h_status;
     DP_CUDA(cudaMemsetAsync(c->d_status, 0, sizeof(int32_t), c->stream), "status reset");
+    if (f & DPF_MMA_TIMEOUT) return fail(DP_ERR_CUDA, "a tensor-core completion wait timed out");
     if (f & DPF_BAD_TYPE) return fail(DP_ERR_TYPE, "an atom type is outside [0, ntypes)");
     if (f & DPF_CAND_OVERFLOW) return fail(DP_ERR_CAPACITY, "an atom has more candidates than cand_cap");
     if (f & DPF_NONFINITE) return fail(DP_ERR_NONFINITE, "non-finite energy or virial");

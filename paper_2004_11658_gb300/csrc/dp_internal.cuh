@@ -18,6 +18,7 @@ enum : int32_t {
     DPF_STALE = 4,
     DPF_NONFINITE = 8,
     DPF_BAD_TYPE = 16,
+    DPF_MMA_TIMEOUT = 32,   // a tensor-core completion wait gave up
 };
 
 // Model description passed by value to kernels.
@@ -143,6 +144,23 @@ struct EvalBuffers {
     double *pair_g;    // [N][nm][3]
     double *f_own;     // [N][3]
     double *vir_part;  // [N][9]
+    float *fit_t;      // mixed mode: tanh values of the fitting layers [N][n_fit][256]
+    float *fit_h;      // mixed mode: fitting activation / gradient [N][256]
+};
+
+// Mixed-precision operands: BF16 copies of the weight matrices in the
+// tensor-core layout (see tc.cuh), FP32 copies of biases and small vectors.
+struct MixedModel {
+    const unsigned char *emb_ops;                            // bf16 operands, bytes
+    int64_t emb_off[DP_MAX_TYPES * DP_MAX_TYPES][2];         // W1^T, W2^T per net (byte offsets)
+    const float *p32;                                        // all parameters in fp32, FP64 layout
+    const unsigned char *fit_fwd, *fit_bwd;                  // bf16 operands, bytes
+    int64_t fit_fwd_off[DP_MAX_TYPES][DP_MAX_LAYERS];        // W_l^T, K-chunks of 64
+    int64_t fit_bwd_off[DP_MAX_TYPES][DP_MAX_LAYERS];        // W_l,   K-chunks of 64
+    int fit_np[DP_MAX_LAYERS];     // F_l padded to 16 (MMA N, forward)
+    int fit_kp[DP_MAX_LAYERS];     // K_in,l padded to 64 (forward K)
+    int fit_kinp[DP_MAX_LAYERS];   // K_in,l padded to 16 (MMA N, backward)
+    int fit_fp[DP_MAX_LAYERS];     // F_l padded to 64 (backward K)
 };
 
 cudaError_t dp_launch_embed_fwd(cudaStream_t st, const DevModel &m, const double *x,
@@ -162,6 +180,20 @@ cudaError_t dp_launch_force(cudaStream_t st, const DevModel &m, const double *x,
 cudaError_t dp_launch_reduce(cudaStream_t st, int N, EvalBuffers eb, double *energy,
                              double *virial, double *atom_energy, int32_t *status,
                              int64_t *launches);
+
+// Mixed precision (BF16 tensor-core GEMMs, FP64 environment / contractions).
+cudaError_t dp_launch_embed_fwd_mx(cudaStream_t st, const DevModel &m, const MixedModel &mx, const double *x,
+                                   const int32_t *types, Box3 box, int N, const FormatBuffers &fb,
+                                   const NlistBuffers &nb, EvalBuffers eb, int num_sms, int32_t *status,
+                                   int64_t *launches);
+cudaError_t dp_launch_fit_mx(cudaStream_t st, const DevModel &m, const MixedModel &mx, int N,
+                             const NlistBuffers &nb, EvalBuffers eb, int32_t *status, int64_t *launches);
+cudaError_t dp_launch_embed_bwd_mx(cudaStream_t st, const DevModel &m, const MixedModel &mx, const double *x,
+                                   const int32_t *types, Box3 box, int N, const FormatBuffers &fb,
+                                   const NlistBuffers &nb, EvalBuffers eb, int num_sms, int32_t *status,
+                                   int64_t *launches);
+// true if the mixed-precision kernels support this model shape
+bool dp_mixed_supported(const DevModel &m);
 
 // MD integrator kernels.
 cudaError_t dp_launch_kick_drift(cudaStream_t st, int N, double *x, double *v, const double *f,

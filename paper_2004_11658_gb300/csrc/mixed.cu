@@ -1,0 +1,855 @@
+// mixed.cu -- mixed-precision evaluation: the embedding-net and fitting-net
+// GEMMs run on the 5th-generation tensor cores (tcgen05.mma, BF16 operands in
+// shared memory, FP32 accumulators in tensor memory); tanh runs in FP32; the
+// environment matrix, the descriptor contraction T = R~^T G / N_m and
+// D = T_<^T T, the contractions of the backward pass with gT, the pair
+// gradients, forces, virial and energy sum stay in FP64.
+//
+// Kernel shapes.  One CTA = 4 warps = the 128 lanes of a tcgen05 accumulator,
+// one thread per row.  Embedding kernels: rows are the real neighbours of one
+// atom for one neighbour type (up to 128 per tile); layer 0 (1 -> e1) runs on
+// the CUDA cores, layers 1 and 2 are MMAs of 128 x N x K with the net's
+// transposed weights as the B operand.  Fitting kernel: rows are 128 atoms of
+// one type; layer 1 streams the descriptor (converted to BF16) and the weight
+// K-chunks through double-buffered shared memory.
+//
+// Supported shapes: embedding widths (e1, 2 e1, 4 e1) with e1 in {16, 25, 32}
+// (the paper's doubling nets), fitting layers of equal width <= 256 after the
+// first one.  Every wait on the tensor core is bounded; on a timeout the
+// kernel flags DPF_MMA_TIMEOUT, stops issuing work, waits once more, frees its
+// tensor memory and returns.
+#include <cuda_bf16.h>
+
+#include "dp_internal.cuh"
+#include "tc.cuh"
+
+namespace {
+
+constexpr int MXT = 128;
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi)
+{
+    __nv_bfloat162 p = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<uint32_t *>(&p);
+}
+
+// 8 consecutive K-values of one row into the canonical K-major layout
+__device__ __forceinline__ void st8(unsigned char *base, int row, int k0, int K, const float (&v)[8])
+{
+    uint4 u;
+    u.x = pack_bf16x2(v[0], v[1]);
+    u.y = pack_bf16x2(v[2], v[3]);
+    u.z = pack_bf16x2(v[4], v[5]);
+    u.w = pack_bf16x2(v[6], v[7]);
+    *reinterpret_cast<uint4 *>(base + tc::kmajor_offset(row, k0, K)) = u;
+}
+
+__device__ __forceinline__ void copy16(unsigned char *dst, const unsigned char *__restrict__ src, int bytes)
+{
+    for (int q = threadIdx.x * 16; q < bytes; q += blockDim.x * 16)
+        *reinterpret_cast<uint4 *>(dst + q) = *reinterpret_cast<const uint4 *>(src + q);
+}
+
+// CTA-wide barrier that also orders tensor-core operations and makes the
+// threads' shared-memory writes visible to the tensor core.
+__device__ __forceinline__ void tc_sync()
+{
+    tc::fence_proxy_async();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+}
+
+// Bounded wait on the MMA barrier; returns false for the whole CTA if any
+// thread gave up.
+__device__ __forceinline__ bool tc_wait(uint64_t *mbar, uint32_t &phase, int32_t *status)
+{
+    const bool ok = tc::mbar_wait(mbar, phase);
+    phase ^= 1u;
+    const bool bad = __syncthreads_or(!ok);
+    if (bad && threadIdx.x == 0) atomicOr(status, DPF_MMA_TIMEOUT);
+    tc::fence_after_sync();
+    return !bad;
+}
+
+constexpr int pad16(int v) { return (v + 15) / 16 * 16; }
+constexpr int tcols_for(int n) { return n <= 32 ? 32 : (n <= 64 ? 64 : (n <= 128 ? 128 : (n <= 256 ? 256 : 512))); }
+
+struct RowGeo {
+    double s, ds, R[4], d[3], r;
+};
+
+__device__ __forceinline__ void geometry(const DevModel &m, const double *__restrict__ x, const double xi[3], int j,
+                                         const Box3 &box, RowGeo &g)
+{
+    const double xj[3] = {x[3 * j], x[3 * j + 1], x[3 * j + 2]};
+    g.r = dp_pinned_dist(xi, xj, box, g.d);
+    dp_switch(g.r, m.rcut_smth, m.rcut, g.s, g.ds);
+    const double inv = 1.0 / g.r;
+    g.R[0] = g.s;
+    g.R[1] = g.s * g.d[0] * inv;
+    g.R[2] = g.s * g.d[1] * inv;
+    g.R[3] = g.s * g.d[2] * inv;
+}
+
+// ------------------------------------------------------------ embedding fwd --
+
+template <int E1>
+struct EmbShape {
+    static constexpr int E2 = 2 * E1, E3 = 4 * E1;
+    static constexpr int K1p = pad16(E1), N1p = pad16(E2), K2p = N1p, N2p = pad16(E3);
+    static constexpr int A0B = MXT * K1p * 2, A1B = MXT * K2p * 2;      // bytes
+    static constexpr int B1B = N1p * K1p * 2, B2B = N2p * K2p * 2;
+};
+
+template <int E1>
+__global__ void __launch_bounds__(MXT, 1) k_embed_fwd_mx(
+    DevModel m, MixedModel mx, const double *__restrict__ x, const int32_t *__restrict__ types, Box3 box, int N,
+    const int32_t *__restrict__ type_perm, const int32_t *__restrict__ nlist, const int32_t *__restrict__ nreal,
+    double *__restrict__ Tout, double *__restrict__ Dout, int32_t *status)
+{
+    using S = EmbShape<E1>;
+    constexpr int E2 = S::E2, E3 = S::E3, K1p = S::K1p, N1p = S::N1p, K2p = S::K2p, N2p = S::N2p;
+    constexpr int TCOLS = tcols_for(N2p);
+    extern __shared__ __align__(1024) unsigned char smraw[];
+    unsigned char *A0 = smraw;
+    unsigned char *A1 = A0 + S::A0B;
+    unsigned char *B1 = A1 + S::A1B;
+    unsigned char *B2 = B1 + S::B1B;
+    double *Gt = reinterpret_cast<double *>(B2 + S::B2B);  // [4][32][17]
+    double *Rt = Gt + 4 * 32 * 17;                          // [4][32][4]
+    double *Tw = Rt + 4 * 32 * 4;                           // [4][4][E3]
+    double *Ts = Tw + 4 * 4 * E3;                           // [4][E3]
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint32_t tslot;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int T = m.ntypes, nm = m.nm;
+    if (warp == 0) tc::tmem_alloc(&tslot, TCOLS);
+    if (tid == 0) tc::mbar_init(&mbar, 1);
+    tc_sync();
+    const uint32_t tbase = tslot;
+    const uint32_t tlane = tbase + ((uint32_t)(32 * warp) << 16);
+    const uint32_t idesc1 = tc::make_idesc_bf16(MXT, N1p), idesc2 = tc::make_idesc_bf16(MXT, N2p);
+    uint32_t phase = 0;
+    bool alive = true;
+    int staged = -1;
+    double *Gw = Gt + warp * 32 * 17;
+    double *Rw = Rt + warp * 32 * 4;
+    double *Tww = Tw + warp * 4 * E3;
+
+    for (int ii = blockIdx.x; ii < N && alive; ii += gridDim.x) {
+        const int i = type_perm[ii];
+        const int a = types[i];
+        const bool a_ok = (unsigned)a < (unsigned)T;
+        const double xi[3] = {x[3 * i], x[3 * i + 1], x[3 * i + 2]};
+        for (int q = tid; q < 4 * 4 * E3; q += MXT) Tw[q] = 0.0;
+        for (int b = 0; b < T && alive; ++b) {
+            const int nb = a_ok ? nreal[(size_t)i * T + b] : 0;
+            if (nb == 0) continue;
+            const int net = a * T + b;
+            if (net != staged) {
+                __syncthreads();
+                copy16(B1, mx.emb_ops + mx.emb_off[net][0], S::B1B);
+                copy16(B2, mx.emb_ops + mx.emb_off[net][1], S::B2B);
+                staged = net;
+            }
+            const float *P32 = mx.p32 + m.emb_base[net];
+            const float *W0 = P32, *b0 = P32 + E1, *b1 = P32 + 2 * E1 + E1 * E2, *b2 = b1 + E2 + E2 * E3;
+            for (int c0 = 0; c0 < nb && alive; c0 += MXT) {
+                const int r = c0 + tid;
+                const bool valid = r < nb;
+                const bool warp_live = c0 + 32 * warp < nb;
+                RowGeo g;
+                g.s = 0.0;
+                g.R[0] = g.R[1] = g.R[2] = g.R[3] = 0.0;
+                if (valid) geometry(m, x, xi, nlist[(size_t)i * nm + m.sel_off[b] + r], box, g);
+                // layer 0 on the CUDA cores
+                float h0[E1];
+                const float s32 = (float)g.s;
+#pragma unroll
+                for (int o = 0; o < E1; ++o) h0[o] = tanhf(fmaf(s32, W0[o], b0[o]));
+#pragma unroll
+                for (int k8 = 0; k8 < K1p; k8 += 8) {
+                    float v[8];
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) v[q] = (k8 + q < E1) ? h0[k8 + q] : 0.f;
+                    st8(A0, tid, k8, K1p, v);
+                }
+                tc_sync();
+                if (tid == 0) {
+#pragma unroll
+                    for (int kk = 0; kk < K1p / 16; ++kk)
+                        tc::mma_bf16(tbase, tc::make_desc(tc::smem_u32(A0) + kk * 256, 128, K1p * 16),
+                                     tc::make_desc(tc::smem_u32(B1) + kk * 256, 128, K1p * 16), idesc1, kk > 0);
+                    tc::mma_commit(&mbar);
+                }
+                alive = tc_wait(&mbar, phase, status);
+                // epilogue 1: h1 = (h0, h0) + tanh(z1 + b1)
+                float h1[E2];
+#pragma unroll
+                for (int o = 0; o < E2; ++o) h1[o] = 0.f;
+                if (alive && warp_live) {
+#pragma unroll
+                    for (int cc = 0; cc < N1p; cc += 16) {
+                        float v[16];
+                        tc::tmem_ld16(tlane + cc, v);
+#pragma unroll
+                        for (int q = 0; q < 16; ++q) {
+                            const int o = cc + q;
+                            if (o < E2) h1[o] = h0[o < E1 ? o : o - E1] + tanhf(v[q] + b1[o]);
+                        }
+                    }
+                }
+#pragma unroll
+                for (int k8 = 0; k8 < K2p; k8 += 8) {
+                    float v[8];
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) v[q] = (k8 + q < E2) ? h1[k8 + q] : 0.f;
+                    st8(A1, tid, k8, K2p, v);
+                }
+                tc_sync();
+                if (!alive) break;
+                if (tid == 0) {
+#pragma unroll
+                    for (int kk = 0; kk < K2p / 16; ++kk)
+                        tc::mma_bf16(tbase, tc::make_desc(tc::smem_u32(A1) + kk * 256, 128, K2p * 16),
+                                     tc::make_desc(tc::smem_u32(B2) + kk * 256, 128, K2p * 16), idesc2, kk > 0);
+                    tc::mma_commit(&mbar);
+                }
+                alive = tc_wait(&mbar, phase, status);
+                // epilogue 2: G = (h1, h1) + tanh(z2 + b2); T += R~^T G in FP64
+                if (alive && warp_live) {
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) Rw[lane * 4 + c] = valid ? g.R[c] : 0.0;
+#pragma unroll
+                    for (int cc = 0; cc < N2p; cc += 16) {
+                        float v[16];
+                        tc::tmem_ld16(tlane + cc, v);
+#pragma unroll
+                        for (int q = 0; q < 16; ++q) {
+                            const int o = cc + q;
+                            float G = 0.f;
+                            if (o < E3 && valid) G = h1[o < E2 ? o : o - E2] + tanhf(v[q] + b2[o]);
+                            Gw[lane * 17 + q] = (double)G;
+                        }
+                        __syncwarp();
+#pragma unroll
+                        for (int u = 0; u < 2; ++u) {
+                            const int p = lane + 32 * u, c = p >> 4, q = p & 15, o = cc + q;
+                            if (o < E3) {
+                                double acc = 0.0;
+#pragma unroll 8
+                                for (int rr = 0; rr < 32; ++rr) acc = fma(Rw[rr * 4 + c], Gw[rr * 17 + q], acc);
+                                Tww[c * E3 + o] += acc;
+                            }
+                        }
+                        __syncwarp();
+                    }
+                }
+                tc_sync();
+            }
+        }
+        if (!alive) break;
+        // T = scale * sum over warps (fixed order); D = T_<^T T
+        __syncthreads();
+        for (int p = tid; p < 4 * E3; p += MXT) {
+            const double v = (Tw[p] + Tw[4 * E3 + p] + Tw[8 * E3 + p] + Tw[12 * E3 + p]) * m.desc_scale;
+            Ts[p] = v;
+            Tout[(size_t)i * 4 * E3 + p] = v;
+        }
+        __syncthreads();
+        const int nd = m.m2 * E3;
+        for (int q = tid; q < nd; q += MXT) {
+            const int a2 = q / E3, b2i = q - a2 * E3;
+            double acc = Ts[a2] * Ts[b2i];
+            acc = fma(Ts[E3 + a2], Ts[E3 + b2i], acc);
+            acc = fma(Ts[2 * E3 + a2], Ts[2 * E3 + b2i], acc);
+            acc = fma(Ts[3 * E3 + a2], Ts[3 * E3 + b2i], acc);
+            Dout[(size_t)i * nd + q] = acc;
+        }
+        __syncthreads();
+    }
+    if (!alive) tc::mbar_wait(&mbar, phase ^ 1u);  // once more for an MMA still in flight
+    tc_sync();
+    if (warp == 0) tc::tmem_dealloc(tbase, TCOLS);
+}
+
+// ------------------------------------------------------------ embedding bwd --
+
+template <int E1>
+__global__ void __launch_bounds__(MXT, 1) k_embed_bwd_mx(
+    DevModel m, MixedModel mx, const double *__restrict__ x, const int32_t *__restrict__ types, Box3 box, int N,
+    const int32_t *__restrict__ type_perm, const int32_t *__restrict__ nlist, const int32_t *__restrict__ nreal,
+    const double *__restrict__ Tin, const double *__restrict__ gD, double *__restrict__ pair_g,
+    double *__restrict__ f_own, double *__restrict__ vir_part, int32_t *status)
+{
+    using S = EmbShape<E1>;
+    constexpr int E2 = S::E2, E3 = S::E3, K1p = S::K1p, N1p = S::N1p, K2p = S::K2p, N2p = S::N2p;
+    constexpr int TOFF = N2p;                 // tangent accumulator column offset
+    constexpr int TCOLS = tcols_for(2 * N2p);
+    extern __shared__ __align__(1024) unsigned char smraw[];
+    unsigned char *A0 = smraw;
+    unsigned char *dA0 = A0 + S::A0B;
+    unsigned char *A1 = dA0 + S::A0B;
+    unsigned char *dA1 = A1 + S::A1B;
+    unsigned char *B1 = dA1 + S::A1B;
+    unsigned char *B2 = B1 + S::B1B;
+    double *gTs = reinterpret_cast<double *>(B2 + S::B2B);  // [4][E3], scaled
+    double *Ts = gTs + 4 * E3;                               // [4][E3]
+    double *red = Ts + 4 * E3;                               // [4][12]
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint32_t tslot;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int T = m.ntypes, nm = m.nm, m2 = m.m2;
+    if (warp == 0) tc::tmem_alloc(&tslot, TCOLS);
+    if (tid == 0) tc::mbar_init(&mbar, 1);
+    tc_sync();
+    const uint32_t tbase = tslot;
+    const uint32_t tlane = tbase + ((uint32_t)(32 * warp) << 16);
+    const uint32_t idesc1 = tc::make_idesc_bf16(MXT, N1p), idesc2 = tc::make_idesc_bf16(MXT, N2p);
+    uint32_t phase = 0;
+    bool alive = true;
+    int staged = -1;
+
+    for (int ii = blockIdx.x; ii < N && alive; ii += gridDim.x) {
+        const int i = type_perm[ii];
+        const int a = types[i];
+        const bool a_ok = (unsigned)a < (unsigned)T;
+        const double xi[3] = {x[3 * i], x[3 * i + 1], x[3 * i + 2]};
+        // gT[c][x] = [x < M2] sum_b gD[x][b] T[c][b] + sum_{a<M2} gD[a][x] T[c][a], times the scale
+        for (int p = tid; p < 4 * E3; p += MXT) Ts[p] = Tin[(size_t)i * 4 * E3 + p];
+        __syncthreads();
+        {
+            const double *gd = gD + (size_t)i * m2 * E3;
+            for (int p = tid; p < 4 * E3; p += MXT) {
+                const int cc = p / E3, xx = p - cc * E3;
+                double acc = 0.0;
+                if (xx < m2)
+                    for (int b2i = 0; b2i < E3; ++b2i) acc = fma(gd[xx * E3 + b2i], Ts[cc * E3 + b2i], acc);
+                for (int a2 = 0; a2 < m2; ++a2) acc = fma(gd[a2 * E3 + xx], Ts[cc * E3 + a2], acc);
+                gTs[p] = acc * m.desc_scale;
+            }
+        }
+        __syncthreads();
+        double fo[3] = {0.0, 0.0, 0.0}, vir[9];
+#pragma unroll
+        for (int q = 0; q < 9; ++q) vir[q] = 0.0;
+        for (int b = 0; b < T && alive; ++b) {
+            const int nb = a_ok ? nreal[(size_t)i * T + b] : 0;
+            if (nb == 0) continue;
+            const int net = a * T + b;
+            if (net != staged) {
+                __syncthreads();
+                copy16(B1, mx.emb_ops + mx.emb_off[net][0], S::B1B);
+                copy16(B2, mx.emb_ops + mx.emb_off[net][1], S::B2B);
+                staged = net;
+            }
+            const float *P32 = mx.p32 + m.emb_base[net];
+            const float *W0 = P32, *b0 = P32 + E1, *b1 = P32 + 2 * E1 + E1 * E2, *b2 = b1 + E2 + E2 * E3;
+            for (int c0 = 0; c0 < nb && alive; c0 += MXT) {
+                const int r = c0 + tid;
+                const bool valid = r < nb;
+                const bool warp_live = c0 + 32 * warp < nb;
+                const int slot = m.sel_off[b] + r;
+                RowGeo g;
+                g.s = g.ds = 0.0;
+                g.R[0] = g.R[1] = g.R[2] = g.R[3] = 0.0;
+                g.d[0] = g.d[1] = g.d[2] = 0.0;
+                g.r = 1.0;
+                if (valid) geometry(m, x, xi, nlist[(size_t)i * nm + slot], box, g);
+                // layer 0 with its s-tangent
+                float h0[E1], dh0[E1];
+                const float s32 = (float)g.s;
+#pragma unroll
+                for (int o = 0; o < E1; ++o) {
+                    const float t = tanhf(fmaf(s32, W0[o], b0[o]));
+                    h0[o] = t;
+                    dh0[o] = fmaf(-t, t, 1.f) * W0[o];
+                }
+#pragma unroll
+                for (int k8 = 0; k8 < K1p; k8 += 8) {
+                    float v[8], dv[8];
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        v[q] = (k8 + q < E1) ? h0[k8 + q] : 0.f;
+                        dv[q] = (k8 + q < E1) ? dh0[k8 + q] : 0.f;
+                    }
+                    st8(A0, tid, k8, K1p, v);
+                    st8(dA0, tid, k8, K1p, dv);
+                }
+                tc_sync();
+                if (tid == 0) {
+#pragma unroll
+                    for (int kk = 0; kk < K1p / 16; ++kk) {
+                        const uint64_t bd = tc::make_desc(tc::smem_u32(B1) + kk * 256, 128, K1p * 16);
+                        tc::mma_bf16(tbase, tc::make_desc(tc::smem_u32(A0) + kk * 256, 128, K1p * 16), bd, idesc1,
+                                     kk > 0);
+                        tc::mma_bf16(tbase + TOFF, tc::make_desc(tc::smem_u32(dA0) + kk * 256, 128, K1p * 16), bd,
+                                     idesc1, kk > 0);
+                    }
+                    tc::mma_commit(&mbar);
+                }
+                alive = tc_wait(&mbar, phase, status);
+                float h1[E2], dh1[E2];
+#pragma unroll
+                for (int o = 0; o < E2; ++o) h1[o] = dh1[o] = 0.f;
+                if (alive && warp_live) {
+#pragma unroll
+                    for (int cc = 0; cc < N1p; cc += 16) {
+                        float v[16], dv[16];
+                        tc::tmem_ld16(tlane + cc, v);
+                        tc::tmem_ld16(tlane + TOFF + cc, dv);
+#pragma unroll
+                        for (int q = 0; q < 16; ++q) {
+                            const int o = cc + q;
+                            if (o < E2) {
+                                const int os = o < E1 ? o : o - E1;
+                                const float t = tanhf(v[q] + b1[o]);
+                                h1[o] = h0[os] + t;
+                                dh1[o] = fmaf(fmaf(-t, t, 1.f), dv[q], dh0[os]);
+                            }
+                        }
+                    }
+                }
+#pragma unroll
+                for (int k8 = 0; k8 < K2p; k8 += 8) {
+                    float v[8], dv[8];
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        v[q] = (k8 + q < E2) ? h1[k8 + q] : 0.f;
+                        dv[q] = (k8 + q < E2) ? dh1[k8 + q] : 0.f;
+                    }
+                    st8(A1, tid, k8, K2p, v);
+                    st8(dA1, tid, k8, K2p, dv);
+                }
+                tc_sync();
+                if (!alive) break;
+                if (tid == 0) {
+#pragma unroll
+                    for (int kk = 0; kk < K2p / 16; ++kk) {
+                        const uint64_t bd = tc::make_desc(tc::smem_u32(B2) + kk * 256, 128, K2p * 16);
+                        tc::mma_bf16(tbase, tc::make_desc(tc::smem_u32(A1) + kk * 256, 128, K2p * 16), bd, idesc2,
+                                     kk > 0);
+                        tc::mma_bf16(tbase + TOFF, tc::make_desc(tc::smem_u32(dA1) + kk * 256, 128, K2p * 16), bd,
+                                     idesc2, kk > 0);
+                    }
+                    tc::mma_commit(&mbar);
+                }
+                alive = tc_wait(&mbar, phase, status);
+                // epilogue 2: G, dG/ds and the FP64 contractions with gT
+                if (alive && warp_live) {
+                    double ra[4] = {0.0, 0.0, 0.0, 0.0}, rb[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+                    for (int cc = 0; cc < N2p; cc += 16) {
+                        float v[16], dv[16];
+                        tc::tmem_ld16(tlane + cc, v);
+                        tc::tmem_ld16(tlane + TOFF + cc, dv);
+#pragma unroll
+                        for (int q = 0; q < 16; ++q) {
+                            const int o = cc + q;
+                            if (o < E3) {
+                                const int os = o < E2 ? o : o - E2;
+                                const float t = tanhf(v[q] + b2[o]);
+                                const double G = (double)(h1[os] + t);
+                                const double dG = (double)fmaf(fmaf(-t, t, 1.f), dv[q], dh1[os]);
+#pragma unroll
+                                for (int c = 0; c < 4; ++c) {
+                                    const double gt = gTs[c * E3 + o];
+                                    ra[c] = fma(G, gt, ra[c]);
+                                    rb[c] = fma(dG, gt, rb[c]);
+                                }
+                            }
+                        }
+                    }
+                    if (valid) {
+                        double gR0 = ra[0];
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) gR0 = fma(g.R[c], rb[c], gR0);
+                        const double inv = 1.0 / g.r;
+                        const double u[3] = {g.d[0] * inv, g.d[1] * inv, g.d[2] * inv};
+                        const double dot = ra[1] * u[0] + ra[2] * u[1] + ra[3] * u[2];
+                        const double sr = g.s * inv;
+                        const double coef = gR0 * g.ds + g.ds * dot - sr * dot;
+                        double gv[3];
+#pragma unroll
+                        for (int bb = 0; bb < 3; ++bb) gv[bb] = fma(u[bb], coef, sr * ra[1 + bb]);
+                        double *pg = pair_g + ((size_t)i * nm + slot) * 3;
+                        pg[0] = gv[0];
+                        pg[1] = gv[1];
+                        pg[2] = gv[2];
+#pragma unroll
+                        for (int aa = 0; aa < 3; ++aa) {
+                            fo[aa] += gv[aa];
+#pragma unroll
+                            for (int bb = 0; bb < 3; ++bb) vir[aa * 3 + bb] -= g.d[aa] * gv[bb];
+                        }
+                    }
+                }
+                tc_sync();
+            }
+        }
+        if (!alive) break;
+        // own force and virial part of atom i: fixed shuffle tree, then warps in order
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+#pragma unroll
+            for (int q = 0; q < 3; ++q) fo[q] += __shfl_xor_sync(0xffffffffu, fo[q], off);
+#pragma unroll
+            for (int q = 0; q < 9; ++q) vir[q] += __shfl_xor_sync(0xffffffffu, vir[q], off);
+        }
+        if (lane == 0) {
+#pragma unroll
+            for (int q = 0; q < 3; ++q) red[warp * 12 + q] = fo[q];
+#pragma unroll
+            for (int q = 0; q < 9; ++q) red[warp * 12 + 3 + q] = vir[q];
+        }
+        __syncthreads();
+        if (tid < 12) {
+            const double v = red[tid] + red[12 + tid] + red[24 + tid] + red[36 + tid];
+            if (tid < 3) f_own[(size_t)i * 3 + tid] = v;
+            else vir_part[(size_t)i * 9 + tid - 3] = v;
+        }
+        __syncthreads();
+    }
+    if (!alive) tc::mbar_wait(&mbar, phase ^ 1u);
+    tc_sync();
+    if (warp == 0) tc::tmem_dealloc(tbase, TCOLS);
+}
+
+// ----------------------------------------------------------------- fitting --
+
+constexpr int FIT_KC = 64;  // K per streamed chunk
+
+// One CTA = one tile of up to 128 atoms of one type.
+__global__ void __launch_bounds__(MXT, 1) k_fit_mx(DevModel m, MixedModel mx, int N,
+                                                   const int32_t *__restrict__ type_perm,
+                                                   const int32_t *__restrict__ type_start,
+                                                   const double *__restrict__ D, double *__restrict__ Ei,
+                                                   double *__restrict__ gD, float *__restrict__ tbuf,
+                                                   float *__restrict__ hbuf, int32_t *status)
+{
+    extern __shared__ __align__(1024) unsigned char smraw[];
+    unsigned char *Ab = smraw;                          // [2][128][64] bf16 (layer-1 input chunks)
+    unsigned char *Bb = Ab + 2 * MXT * FIT_KC * 2;      // [2][256][64] bf16 (weight chunks)
+    unsigned char *Hb = Bb + 2 * 256 * FIT_KC * 2;      // [128][256] bf16 (activation / gradient)
+    __shared__ __align__(8) uint64_t mbar[2];
+    __shared__ uint32_t tslot;
+    __shared__ int rows_atom[MXT];
+    constexpr int HK = 256;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    (void)lane;
+    const int M = m.M, K1 = m.m2 * M, nf = m.n_fit;
+
+    int bid = blockIdx.x, a = -1, first = 0, cnt = 0;
+    for (int t = 0; t < m.ntypes; ++t) {
+        const int n_t = type_start[t + 1] - type_start[t];
+        const int tiles = (n_t + MXT - 1) / MXT;
+        if (bid < tiles) {
+            a = t;
+            first = type_start[t] + bid * MXT;
+            cnt = min(MXT, n_t - bid * MXT);
+            break;
+        }
+        bid -= tiles;
+    }
+    if (a < 0) return;
+    if (warp == 0) tc::tmem_alloc(&tslot, 256);
+    if (tid == 0) {
+        tc::mbar_init(&mbar[0], 1);
+        tc::mbar_init(&mbar[1], 1);
+    }
+    rows_atom[tid] = tid < cnt ? type_perm[first + tid] : -1;
+    tc_sync();
+    const uint32_t tbase = tslot;
+    const uint32_t tlane = tbase + ((uint32_t)(32 * warp) << 16);
+    const int my = rows_atom[tid];
+    const bool warp_live = 32 * warp < cnt;
+    uint32_t ph[2] = {0, 0};
+    bool alive = true;
+    const float *P32 = mx.p32 + m.fit_base[a];
+    float *tb = tbuf + (size_t)(my < 0 ? 0 : my) * nf * HK;
+    float *hb = hbuf + (size_t)(my < 0 ? 0 : my) * HK;
+
+    // streamed GEMM into TMEM columns [0, Np): for K-chunk kc, A is either the
+    // layer-1 input chunk (converted here) or the resident Hb, B is the chunk
+    // of the weight operand (rows [n0, n0 + Np) of a K-chunked operand).
+    auto gemm = [&](bool from_D, int nK, const unsigned char *Bsrc, int64_t chunk_bytes, int64_t row_off_bytes,
+                    int Np) -> bool {
+        const uint32_t idesc = tc::make_idesc_bf16(MXT, Np);
+        const int bbytes = Np * FIT_KC * 2;
+        int issued = 0;
+        for (int kc = 0; kc < nK; ++kc) {
+            const int buf = kc & 1;
+            if (kc >= 2) {  // buffer reuse: the MMAs of chunk kc-2 must be done
+                if (!tc_wait(&mbar[buf], ph[buf], status)) return false;
+            }
+            copy16(Bb + buf * 256 * FIT_KC * 2, Bsrc + kc * chunk_bytes + row_off_bytes, bbytes);
+            if (from_D) {
+                unsigned char *Ac = Ab + buf * MXT * FIT_KC * 2;
+#pragma unroll
+                for (int k8 = 0; k8 < FIT_KC; k8 += 8) {
+                    float v[8];
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        const int k = kc * FIT_KC + k8 + q;
+                        v[q] = (my >= 0 && k < K1) ? (float)D[(size_t)my * K1 + k] : 0.f;
+                    }
+                    st8(Ac, tid, k8, FIT_KC, v);
+                }
+            }
+            tc_sync();
+            if (tid == 0) {
+#pragma unroll
+                for (int kk = 0; kk < FIT_KC / 16; ++kk) {
+                    const uint64_t ad =
+                        from_D ? tc::make_desc(tc::smem_u32(Ab + buf * MXT * FIT_KC * 2) + kk * 256, 128, FIT_KC * 16)
+                               : tc::make_desc(tc::smem_u32(Hb) + (kc * (FIT_KC / 16) + kk) * 256, 128, HK * 16);
+                    const uint64_t bd =
+                        tc::make_desc(tc::smem_u32(Bb + buf * 256 * FIT_KC * 2) + kk * 256, 128, FIT_KC * 16);
+                    tc::mma_bf16(tbase, ad, bd, idesc, kc > 0 || kk > 0);
+                }
+                tc::mma_commit(&mbar[buf]);
+            }
+            ++issued;
+        }
+        // drain: the last one or two chunks
+        for (int kc = (nK >= 2 ? nK - 2 : 0); kc < nK; ++kc)
+            if (!tc_wait(&mbar[kc & 1], ph[kc & 1], status)) return false;
+        (void)issued;
+        return true;
+    };
+
+    // ---------------- forward
+    int Kin = K1;
+    for (int l = 0; l < nf && alive; ++l) {
+        const int F = m.fit[l];
+        const int Np = mx.fit_np[l];
+        const int nK = mx.fit_kp[l] / FIT_KC;
+        const unsigned char *Bsrc = mx.fit_fwd + mx.fit_fwd_off[a][l];
+        alive = gemm(l == 0, nK, Bsrc, (int64_t)Np * 128, 0, Np);
+        if (!alive) break;
+        // bias offset in the FP64 parameter layout
+        int64_t boff = 0;
+        {
+            int kin = K1;
+            for (int q = 0; q <= l; ++q) {
+                boff += (int64_t)kin * m.fit[q];
+                if (q < l) boff += m.fit[q];
+                kin = m.fit[q];
+            }
+        }
+        const float *bias = P32 + boff;
+        if (warp_live) {
+            for (int cc = 0; cc < Np; cc += 16) {
+                float v[16];
+                tc::tmem_ld16(tlane + cc, v);
+                if (my >= 0) {
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) {
+                        const int n = cc + q;
+                        if (n < F) {
+                            const float t = tanhf(v[q] + bias[n]);
+                            tb[l * HK + n] = t;
+                            hb[n] = (l > 0 ? hb[n] : 0.f) + t;  // equal-width skip after the first layer
+                        }
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        // next layer's A operand (bf16, zero-padded to 256)
+        for (int k8 = 0; k8 < HK; k8 += 8) {
+            float v[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) v[q] = (my >= 0 && k8 + q < F) ? hb[k8 + q] : 0.f;
+            st8(Hb, tid, k8, HK, v);
+        }
+        tc_sync();
+        Kin = F;
+    }
+    // output layer (FP64 accumulation of the dot product)
+    const float *wo = nullptr;
+    {
+        int64_t off = 0;
+        int kin = K1;
+        for (int q = 0; q < nf; ++q) {
+            off += (int64_t)kin * m.fit[q] + m.fit[q];
+            kin = m.fit[q];
+        }
+        wo = P32 + off;
+    }
+    if (alive && my >= 0) {
+        double e = (double)wo[Kin];
+        for (int n = 0; n < Kin; ++n) e = fma((double)hb[n], (double)wo[n], e);
+        Ei[my] = e;
+    }
+
+    // ---------------- backward: gh = w_out; gz_l = gh * (1 - t_l^2)
+    if (my >= 0)
+        for (int n = 0; n < Kin; ++n) hb[n] = wo[n];
+    for (int l = nf - 1; l >= 0 && alive; --l) {
+        const int F = m.fit[l];
+        const int Kl = (l == 0) ? K1 : m.fit[l - 1];
+        for (int k8 = 0; k8 < HK; k8 += 8) {
+            float v[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int n = k8 + q;
+                float gz = 0.f;
+                if (my >= 0 && n < F) {
+                    const float t = tb[l * HK + n];
+                    gz = hb[n] * fmaf(-t, t, 1.f);
+                }
+                v[q] = gz;
+            }
+            st8(Hb, tid, k8, HK, v);
+        }
+        tc_sync();
+        const int nK = mx.fit_fp[l] / FIT_KC;
+        const int Kinp = mx.fit_kinp[l];
+        const unsigned char *Bsrc = mx.fit_bwd + mx.fit_bwd_off[a][l];
+        // output columns in chunks of up to 256 (128 for the wide first layer)
+        const int NB = Kinp <= 256 ? Kinp : 128;
+        for (int n0 = 0; n0 < Kinp && alive; n0 += NB) {
+            const int nb = min(NB, Kinp - n0);
+            alive = gemm(false, nK, Bsrc, (int64_t)Kinp * 128, (int64_t)(n0 / 8) * 1024, nb);
+            if (!alive) break;
+            if (warp_live) {
+                for (int cc = 0; cc < nb; cc += 16) {
+                    float v[16];
+                    tc::tmem_ld16(tlane + cc, v);
+                    if (my >= 0) {
+#pragma unroll
+                        for (int q = 0; q < 16; ++q) {
+                            const int n = n0 + cc + q;
+                            if (n < Kl) {
+                                if (l == 0) gD[(size_t)my * K1 + n] = (double)v[q];
+                                else hb[n] = v[q] + hb[n];  // equal widths: the skip passes gh through
+                            }
+                        }
+                    }
+                }
+            }
+            tc_sync();
+        }
+    }
+    if (!alive) {
+        tc::mbar_wait(&mbar[0], ph[0] ^ 1u);
+        tc::mbar_wait(&mbar[1], ph[1] ^ 1u);
+    }
+    tc_sync();
+    if (warp == 0) tc::tmem_dealloc(tbase, 256);
+}
+
+template <int E1>
+size_t fwd_smem()
+{
+    using S = EmbShape<E1>;
+    return S::A0B + S::A1B + S::B1B + S::B2B + sizeof(double) * (4 * 32 * 17 + 4 * 32 * 4 + 4 * 4 * S::E3 + 4 * S::E3);
+}
+template <int E1>
+size_t bwd_smem()
+{
+    using S = EmbShape<E1>;
+    return 2 * S::A0B + 2 * S::A1B + S::B1B + S::B2B + sizeof(double) * (4 * S::E3 * 2 + 48);
+}
+
+template <int E1>
+cudaError_t launch_fwd(cudaStream_t st, const DevModel &m, const MixedModel &mx, const double *x,
+                       const int32_t *types, Box3 box, int N, const FormatBuffers &fb, const NlistBuffers &nb,
+                       EvalBuffers eb, int num_sms, int32_t *status)
+{
+    const size_t smem = fwd_smem<E1>();
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(k_embed_fwd_mx<E1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    // two CTAs per SM (tensor memory: 128 columns each)
+    int grid = 2 * num_sms;
+    if (grid > N) grid = N;
+    k_embed_fwd_mx<E1><<<grid, MXT, smem, st>>>(m, mx, x, types, box, N, nb.type_perm, fb.nlist, fb.nreal, eb.T,
+                                                eb.D, status);
+    return cudaGetLastError();
+}
+
+template <int E1>
+cudaError_t launch_bwd(cudaStream_t st, const DevModel &m, const MixedModel &mx, const double *x,
+                       const int32_t *types, Box3 box, int N, const FormatBuffers &fb, const NlistBuffers &nb,
+                       EvalBuffers eb, int num_sms, int32_t *status)
+{
+    const size_t smem = bwd_smem<E1>();
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(k_embed_bwd_mx<E1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    // two CTAs per SM (tensor memory: <= 256 columns each)
+    int grid = 2 * num_sms;
+    if (grid > N) grid = N;
+    k_embed_bwd_mx<E1><<<grid, MXT, smem, st>>>(m, mx, x, types, box, N, nb.type_perm, fb.nlist, fb.nreal, eb.T,
+                                                eb.gD, eb.pair_g, eb.f_own, eb.vir_part, status);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+bool dp_mixed_supported(const DevModel &m)
+{
+    if (m.n_emb != 3) return false;
+    const int e1 = m.emb[0];
+    if (!(e1 == 16 || e1 == 25 || e1 == 32)) return false;
+    if (m.emb[1] != 2 * e1 || m.emb[2] != 4 * e1) return false;
+    for (int l = 0; l < m.n_fit; ++l) {
+        if (m.fit[l] % 16 != 0 || m.fit[l] > 256) return false;
+        if (l > 0 && m.fit[l] != m.fit[l - 1]) return false;
+    }
+    return true;
+}
+
+cudaError_t dp_launch_embed_fwd_mx(cudaStream_t st, const DevModel &m, const MixedModel &mx, const double *x,
+                                   const int32_t *types, Box3 box, int N, const FormatBuffers &fb,
+                                   const NlistBuffers &nb, EvalBuffers eb, int num_sms, int32_t *status,
+                                   int64_t *launches)
+{
+    *launches += 1;
+    switch (m.emb[0]) {
+    case 16: return launch_fwd<16>(st, m, mx, x, types, box, N, fb, nb, eb, num_sms, status);
+    case 25: return launch_fwd<25>(st, m, mx, x, types, box, N, fb, nb, eb, num_sms, status);
+    case 32: return launch_fwd<32>(st, m, mx, x, types, box, N, fb, nb, eb, num_sms, status);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t dp_launch_embed_bwd_mx(cudaStream_t st, const DevModel &m, const MixedModel &mx, const double *x,
+                                   const int32_t *types, Box3 box, int N, const FormatBuffers &fb,
+                                   const NlistBuffers &nb, EvalBuffers eb, int num_sms, int32_t *status,
+                                   int64_t *launches)
+{
+    *launches += 1;
+    switch (m.emb[0]) {
+    case 16: return launch_bwd<16>(st, m, mx, x, types, box, N, fb, nb, eb, num_sms, status);
+    case 25: return launch_bwd<25>(st, m, mx, x, types, box, N, fb, nb, eb, num_sms, status);
+    case 32: return launch_bwd<32>(st, m, mx, x, types, box, N, fb, nb, eb, num_sms, status);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t dp_launch_fit_mx(cudaStream_t st, const DevModel &m, const MixedModel &mx, int N,
+                             const NlistBuffers &nb, EvalBuffers eb, int32_t *status, int64_t *launches)
+{
+    const size_t smem = 2 * MXT * FIT_KC * 2 + 2 * 256 * FIT_KC * 2 + MXT * 256 * 2;
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(k_fit_mx, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    const int grid = (N + MXT - 1) / MXT + m.ntypes;
+    k_fit_mx<<<grid, MXT, smem, st>>>(m, mx, N, nb.type_perm, nb.type_start, eb.D, eb.Ei, eb.gD, eb.fit_t,
+                                      eb.fit_h, status);
+    *launches += 1;
+    return cudaGetLastError();
+}

@@ -25,6 +25,7 @@ STATUS_NAMES = {
     -8: "DP_ERR_UNSUPPORTED", -9: "DP_ERR_CAPACITY", -10: "DP_ERR_NOMEM", -11: "DP_ERR_TYPE",
 }
 DP_PREC_FP64 = 0
+DP_PREC_MIXED = 1
 
 
 class DPError(RuntimeError):

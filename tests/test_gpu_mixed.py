@@ -1,0 +1,120 @@
+"""Mixed precision (BF16 tensor-core GEMMs, FP64 environment / contractions /
+forces) against the FP64 oracle.
+
+Bar: force RMSE <= 1e-3 eV/A against the FP64 result; also reported and
+bounded: energy error per atom, relative force RMSE and virial error.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+FORCE_RMSE = 1e-3      # eV/A
+E_PER_ATOM = 1e-3      # eV
+
+
+@pytest.fixture(scope="module")
+def dp():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2004_11658_gb300 import dp as _dp
+    _dp.lib()
+    return _dp
+
+
+def system(synth, name):
+    if name == "water648":
+        return synth.sub_box_water(6, 6 * 49.7 / 16)
+    if name == "cu864":
+        c, t, b = synth.copper_fcc(6)
+        return dict(coords=c, types=t, box=b, model=synth.CU_MODEL, masses=(synth.MASS["Cu"],))
+    return synth.workload(name)
+
+
+def mixed_eval(dp, desc, P, w, skin=0.0):
+    N = len(w["coords"])
+    model = dp.Model(desc, P)
+    ctx = dp.Context(model, N, precision=dp.DP_PREC_MIXED)
+    x = torch.tensor(w["coords"], dtype=torch.float64, device="cuda")
+    t = torch.tensor(w["types"], dtype=torch.int32, device="cuda")
+    dp.dp_build_nlist(ctx, x, t, w["box"], skin)
+    out = dp.dp_eval(ctx, x, t, w["box"], want_atom_energy=True)
+    return model, ctx, x, t, out
+
+
+def errors(g, o, N):
+    F = g["force"].cpu().numpy()
+    dF = F - o["force"]
+    rmse = float(np.sqrt((dF ** 2).mean()))
+    rel = rmse / float(np.sqrt((o["force"] ** 2).mean()))
+    eE = abs(g["energy"].item() - o["energy"]) / N
+    V = g["virial"].cpu().numpy().reshape(3, 3)
+    eV = np.abs(V - o["virial"]).max() / np.abs(o["virial"]).max()
+    return rmse, rel, eE, eV
+
+
+@pytest.mark.parametrize("name,variant", [("water192", None), ("water648", None), ("cu864", None),
+                                          ("water192", "student")])
+def test_mixed_against_fp64_oracle(dp, oracle, synth, name, variant):
+    w = system(synth, name)
+    desc = synth.WATER_STUDENT if variant == "student" else w["model"]
+    P = synth.model_params(desc, 0)
+    o = oracle.evaluate(desc, P, w["coords"], w["types"], w["box"])
+    N = len(w["coords"])
+    model, ctx, x, t, g = mixed_eval(dp, desc, P, w)
+    rmse, rel, eE, eV = errors(g, o, N)
+    print(f"{name} {variant}: force RMSE {rmse:.2e} eV/A (rel {rel:.2e}), |dE|/N {eE:.2e} eV, virial {eV:.2e}")
+    assert rmse <= FORCE_RMSE
+    assert rel < 0.05
+    assert eE <= E_PER_ATOM
+    assert eV < 0.05
+    assert np.isfinite(g["force"].cpu().numpy()).all()
+
+
+def test_mixed_deterministic_and_same_list(dp, synth):
+    w = system(synth, "water648")
+    desc = w["model"]
+    P = synth.model_params(desc, 0)
+    model, ctx, x, t, a = mixed_eval(dp, desc, P, w, skin=2.0)
+    b = dp.dp_eval(ctx, x, t, w["box"])
+    assert torch.equal(a["force"], b["force"]) and torch.equal(a["energy"], b["energy"])
+    # the formatted list does not depend on the precision mode
+    m64 = dp.Model(desc, P)
+    c64 = dp.Context(m64, len(w["coords"]))
+    dp.dp_build_nlist(c64, x, t, w["box"], 2.0)
+    nl64, nr64, _ = dp.dp_format_nlist(c64, x, t, w["box"])
+    nlmx, nrmx, _ = dp.dp_format_nlist(ctx, x, t, w["box"])
+    assert torch.equal(nl64, nlmx) and torch.equal(nr64, nrmx)
+
+
+def test_mixed_unsupported_shape(dp, synth):
+    desc = dict(synth.WATER_MODEL, emb=(25, 50))
+    model = dp.Model(desc, synth.model_params(desc, 0))
+    with pytest.raises(dp.DPError) as e:
+        dp.Context(model, 10, precision=dp.DP_PREC_MIXED)
+    assert e.value.status == -8
+
+
+def test_mixed_md_tracks_fp64(dp, synth):
+    """30 NVE steps of the 648-atom box: the mixed trajectory's energies stay
+    within the force-error budget of the FP64 one and its energy is conserved."""
+    w = system(synth, "water648")
+    desc = w["model"]
+    P = synth.model_params(desc, 0)
+    m = np.array(w["masses"])[w["types"]]
+    v0 = synth.maxwell_velocities(m, 300.0, seed=2)
+    ths = {}
+    for prec in (0, 1):
+        model = dp.Model(desc, P)
+        ctx = dp.Context(model, len(m), precision=prec)
+        x = torch.tensor(w["coords"], device="cuda")
+        v = torch.tensor(v0, device="cuda")
+        t = torch.tensor(w["types"], device="cuda")
+        th = torch.empty((30, 4), dtype=torch.float64, device="cuda")
+        dp.dp_md_step(ctx, x, v, t, w["box"], w["masses"], 0.5, 30, rebuild_every=10, skin=2.0, thermo=th)
+        ths[prec] = th.cpu().numpy()
+    N = len(m)
+    assert np.abs(ths[1][:, 0] - ths[0][:, 0]).max() / N < E_PER_ATOM
+    etot = ths[1][:, 0] + ths[1][:, 1]
+    assert np.abs(etot - etot[0]).max() / N < 1e-3

@@ -92,7 +92,18 @@ __device__ __forceinline__ void geometry(const DevModel &m, const double *__rest
     g.R[3] = g.s * g.d[2] * inv;
 }
 
-// ------------------------------------------------------------ embedding fwd --
+// ------------------------------------------------------------ embedding --
+//
+// Packing: a CTA owns a balanced contiguous share of the type-sorted atoms
+// and walks it in batches of up to AB atoms of one centre type.  For each
+// neighbour type b the batch's real rows are cut into 32-row groups, each
+// group belonging to one atom; a tile of the MMA is 4 groups (one per warp),
+// so tiles are full even when an atom has only ~30 neighbours of a type.
+// Per-warp partial sums are merged into per-atom accumulators in warp order
+// after each tile, which keeps every result reproducible bit for bit.
+
+constexpr int AB = 8;                        // atoms per batch
+constexpr int MAXG = AB * (DP_MAX_NM / 32);  // 32-row groups per batch and type (upper bound)
 
 template <int E1>
 struct EmbShape {
@@ -102,11 +113,41 @@ struct EmbShape {
     static constexpr int B1B = N1p * K1p * 2, B2B = N2p * K2p * 2;
 };
 
+struct BatchInfo {
+    int ids[AB];             // atom indices of the batch
+    int grp_atom[MAXG];      // batch index of each 32-row group
+    int grp_r0[MAXG];        // first row of each group
+    int ngroups;
+};
+
+// Next batch [first, first + k) of one type inside [first, hi).
+__device__ __forceinline__ int batch_size(int first, int hi, const int *tstart, int T, int &a)
+{
+    a = 0;
+    while (a + 1 < T && first >= tstart[a + 1]) ++a;
+    return min(AB, min(hi, tstart[a + 1]) - first);
+}
+
+// Group list of neighbour type b for the batch (one thread builds it).
+__device__ __forceinline__ void build_groups(BatchInfo &bi, int k, const int32_t *__restrict__ nreal, int T, int b)
+{
+    int g = 0;
+    for (int j = 0; j < k; ++j) {
+        const int nb = nreal[(size_t)bi.ids[j] * T + b];
+        for (int r0 = 0; r0 < nb; r0 += 32) {
+            bi.grp_atom[g] = j;
+            bi.grp_r0[g] = r0;
+            ++g;
+        }
+    }
+    bi.ngroups = g;
+}
+
 template <int E1>
 __global__ void __launch_bounds__(MXT, 1) k_embed_fwd_mx(
     DevModel m, MixedModel mx, const double *__restrict__ x, const int32_t *__restrict__ types, Box3 box, int N,
-    const int32_t *__restrict__ type_perm, const int32_t *__restrict__ nlist, const int32_t *__restrict__ nreal,
-    double *__restrict__ Tout, double *__restrict__ Dout, int32_t *status)
+    const int32_t *__restrict__ type_perm, const int32_t *__restrict__ type_start, const int32_t *__restrict__ nlist,
+    const int32_t *__restrict__ nreal, double *__restrict__ Tout, double *__restrict__ Dout, int32_t *status)
 {
     using S = EmbShape<E1>;
     constexpr int E2 = S::E2, E3 = S::E3, K1p = S::K1p, N1p = S::N1p, K2p = S::K2p, N2p = S::N2p;
@@ -118,12 +159,15 @@ __global__ void __launch_bounds__(MXT, 1) k_embed_fwd_mx(
     unsigned char *B2 = B1 + S::B1B;
     double *Gt = reinterpret_cast<double *>(B2 + S::B2B);  // [4][32][17]
     double *Rt = Gt + 4 * 32 * 17;                          // [4][32][4]
-    double *Tw = Rt + 4 * 32 * 4;                           // [4][4][E3]
-    double *Ts = Tw + 4 * 4 * E3;                           // [4][E3]
+    double *Tw = Rt + 4 * 32 * 4;                           // [4][4][E3] per-warp partial of one tile
+    double *Tacc = Tw + 4 * 4 * E3;                         // [AB][4][E3] per-atom sums
     __shared__ __align__(8) uint64_t mbar;
     __shared__ uint32_t tslot;
+    __shared__ BatchInfo bi;
+    __shared__ int tstart[DP_MAX_TYPES + 1];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int T = m.ntypes, nm = m.nm;
+    if (tid <= T) tstart[tid] = type_start[tid];
     if (warp == 0) tc::tmem_alloc(&tslot, TCOLS);
     if (tid == 0) tc::mbar_init(&mbar, 1);
     tc_sync();
@@ -136,36 +180,46 @@ __global__ void __launch_bounds__(MXT, 1) k_embed_fwd_mx(
     double *Gw = Gt + warp * 32 * 17;
     double *Rw = Rt + warp * 32 * 4;
     double *Tww = Tw + warp * 4 * E3;
+    const int lo = (int)(((long long)blockIdx.x * N) / gridDim.x);
+    const int hi = (int)(((long long)(blockIdx.x + 1) * N) / gridDim.x);
 
-    for (int ii = blockIdx.x; ii < N && alive; ii += gridDim.x) {
-        const int i = type_perm[ii];
-        const int a = types[i];
+    for (int first = lo; first < hi && alive;) {
+        int a;
+        const int k = batch_size(first, hi, tstart, T, a);
+        __syncthreads();
+        if (tid < AB) bi.ids[tid] = tid < k ? type_perm[first + tid] : 0;
+        for (int q = tid; q < AB * 4 * E3; q += MXT) Tacc[q] = 0.0;
+        __syncthreads();
         const bool a_ok = (unsigned)a < (unsigned)T;
-        const double xi[3] = {x[3 * i], x[3 * i + 1], x[3 * i + 2]};
-        for (int q = tid; q < 4 * 4 * E3; q += MXT) Tw[q] = 0.0;
-        for (int b = 0; b < T && alive; ++b) {
-            const int nb = a_ok ? nreal[(size_t)i * T + b] : 0;
-            if (nb == 0) continue;
+        for (int b = 0; b < T && alive && a_ok; ++b) {
+            if (tid == 0) build_groups(bi, k, nreal, T, b);
+            __syncthreads();
+            const int G = bi.ngroups;
+            if (G == 0) continue;
             const int net = a * T + b;
             if (net != staged) {
-                __syncthreads();
                 copy16(B1, mx.emb_ops + mx.emb_off[net][0], S::B1B);
                 copy16(B2, mx.emb_ops + mx.emb_off[net][1], S::B2B);
                 staged = net;
             }
             const float *P32 = mx.p32 + m.emb_base[net];
             const float *W0 = P32, *b0 = P32 + E1, *b1 = P32 + 2 * E1 + E1 * E2, *b2 = b1 + E2 + E2 * E3;
-            for (int c0 = 0; c0 < nb && alive; c0 += MXT) {
-                const int r = c0 + tid;
-                const bool valid = r < nb;
-                const bool warp_live = c0 + 32 * warp < nb;
-                RowGeo g;
-                g.s = 0.0;
-                g.R[0] = g.R[1] = g.R[2] = g.R[3] = 0.0;
-                if (valid) geometry(m, x, xi, nlist[(size_t)i * nm + m.sel_off[b] + r], box, g);
-                // layer 0 on the CUDA cores
+            for (int t0 = 0; t0 < G && alive; t0 += 4) {
+                const int g = t0 + warp;
+                const bool warp_live = g < G;
+                const int j = warp_live ? bi.grp_atom[g] : 0;
+                const int i = bi.ids[j];
+                const int r = warp_live ? bi.grp_r0[g] + lane : 0;
+                const bool valid = warp_live && r < nreal[(size_t)i * T + b];
+                RowGeo gg;
+                gg.s = 0.0;
+                gg.R[0] = gg.R[1] = gg.R[2] = gg.R[3] = 0.0;
+                if (valid) {
+                    const double xi[3] = {x[3 * i], x[3 * i + 1], x[3 * i + 2]};
+                    geometry(m, x, xi, nlist[(size_t)i * nm + m.sel_off[b] + r], box, gg);
+                }
                 float h0[E1];
-                const float s32 = (float)g.s;
+                const float s32 = (float)gg.s;
 #pragma unroll
                 for (int o = 0; o < E1; ++o) h0[o] = tanhf(fmaf(s32, W0[o], b0[o]));
 #pragma unroll
@@ -184,7 +238,6 @@ __global__ void __launch_bounds__(MXT, 1) k_embed_fwd_mx(
                     tc::mma_commit(&mbar);
                 }
                 alive = tc_wait(&mbar, phase, status);
-                // epilogue 1: h1 = (h0, h0) + tanh(z1 + b1)
                 float h1[E2];
 #pragma unroll
                 for (int o = 0; o < E2; ++o) h1[o] = 0.f;
@@ -217,10 +270,10 @@ __global__ void __launch_bounds__(MXT, 1) k_embed_fwd_mx(
                     tc::mma_commit(&mbar);
                 }
                 alive = tc_wait(&mbar, phase, status);
-                // epilogue 2: G = (h1, h1) + tanh(z2 + b2); T += R~^T G in FP64
+                // epilogue 2: G = (h1, h1) + tanh(z2 + b2); the warp's partial of T = R~^T G in FP64
                 if (alive && warp_live) {
 #pragma unroll
-                    for (int c = 0; c < 4; ++c) Rw[lane * 4 + c] = valid ? g.R[c] : 0.0;
+                    for (int c = 0; c < 4; ++c) Rw[lane * 4 + c] = valid ? gg.R[c] : 0.0;
 #pragma unroll
                     for (int cc = 0; cc < N2p; cc += 16) {
                         float v[16];
@@ -228,9 +281,9 @@ __global__ void __launch_bounds__(MXT, 1) k_embed_fwd_mx(
 #pragma unroll
                         for (int q = 0; q < 16; ++q) {
                             const int o = cc + q;
-                            float G = 0.f;
-                            if (o < E3 && valid) G = h1[o < E2 ? o : o - E2] + tanhf(v[q] + b2[o]);
-                            Gw[lane * 17 + q] = (double)G;
+                            float G2 = 0.f;
+                            if (o < E3 && valid) G2 = h1[o < E2 ? o : o - E2] + tanhf(v[q] + b2[o]);
+                            Gw[lane * 17 + q] = (double)G2;
                         }
                         __syncwarp();
 #pragma unroll
@@ -240,48 +293,58 @@ __global__ void __launch_bounds__(MXT, 1) k_embed_fwd_mx(
                                 double acc = 0.0;
 #pragma unroll 8
                                 for (int rr = 0; rr < 32; ++rr) acc = fma(Rw[rr * 4 + c], Gw[rr * 17 + q], acc);
-                                Tww[c * E3 + o] += acc;
+                                Tww[c * E3 + o] = acc;
                             }
                         }
                         __syncwarp();
                     }
                 }
                 tc_sync();
+                // merge the tile's warp partials into the atoms' sums, warps in order
+                if (alive) {
+                    for (int p = tid; p < 4 * E3; p += MXT) {
+#pragma unroll
+                        for (int w = 0; w < 4; ++w)
+                            if (t0 + w < G) Tacc[bi.grp_atom[t0 + w] * 4 * E3 + p] += Tw[w * 4 * E3 + p];
+                    }
+                }
+                __syncthreads();
             }
         }
         if (!alive) break;
-        // T = scale * sum over warps (fixed order); D = T_<^T T
-        __syncthreads();
-        for (int p = tid; p < 4 * E3; p += MXT) {
-            const double v = (Tw[p] + Tw[4 * E3 + p] + Tw[8 * E3 + p] + Tw[12 * E3 + p]) * m.desc_scale;
-            Ts[p] = v;
-            Tout[(size_t)i * 4 * E3 + p] = v;
-        }
-        __syncthreads();
+        // T = scale * sum; D = T_<^T T, per atom of the batch
         const int nd = m.m2 * E3;
-        for (int q = tid; q < nd; q += MXT) {
-            const int a2 = q / E3, b2i = q - a2 * E3;
-            double acc = Ts[a2] * Ts[b2i];
-            acc = fma(Ts[E3 + a2], Ts[E3 + b2i], acc);
-            acc = fma(Ts[2 * E3 + a2], Ts[2 * E3 + b2i], acc);
-            acc = fma(Ts[3 * E3 + a2], Ts[3 * E3 + b2i], acc);
-            Dout[(size_t)i * nd + q] = acc;
+        for (int j = 0; j < k; ++j) {
+            const int i = bi.ids[j];
+            double *Tj = Tacc + j * 4 * E3;
+            for (int p = tid; p < 4 * E3; p += MXT) {
+                const double v = Tj[p] * m.desc_scale;
+                Tj[p] = v;
+                Tout[(size_t)i * 4 * E3 + p] = v;
+            }
+            __syncthreads();
+            for (int q = tid; q < nd; q += MXT) {
+                const int a2 = q / E3, b2i = q - a2 * E3;
+                double acc = Tj[a2] * Tj[b2i];
+                acc = fma(Tj[E3 + a2], Tj[E3 + b2i], acc);
+                acc = fma(Tj[2 * E3 + a2], Tj[2 * E3 + b2i], acc);
+                acc = fma(Tj[3 * E3 + a2], Tj[3 * E3 + b2i], acc);
+                Dout[(size_t)i * nd + q] = acc;
+            }
         }
-        __syncthreads();
+        first += k;
     }
     if (!alive) tc::mbar_wait(&mbar, phase ^ 1u);  // once more for an MMA still in flight
     tc_sync();
     if (warp == 0) tc::tmem_dealloc(tbase, TCOLS);
 }
 
-// ------------------------------------------------------------ embedding bwd --
-
 template <int E1>
 __global__ void __launch_bounds__(MXT, 1) k_embed_bwd_mx(
     DevModel m, MixedModel mx, const double *__restrict__ x, const int32_t *__restrict__ types, Box3 box, int N,
-    const int32_t *__restrict__ type_perm, const int32_t *__restrict__ nlist, const int32_t *__restrict__ nreal,
-    const double *__restrict__ Tin, const double *__restrict__ gD, double *__restrict__ pair_g,
-    double *__restrict__ f_own, double *__restrict__ vir_part, int32_t *status)
+    const int32_t *__restrict__ type_perm, const int32_t *__restrict__ type_start, const int32_t *__restrict__ nlist,
+    const int32_t *__restrict__ nreal, const double *__restrict__ Tin, const double *__restrict__ gD,
+    double *__restrict__ pair_g, double *__restrict__ f_own, double *__restrict__ vir_part, int32_t *status)
 {
     using S = EmbShape<E1>;
     constexpr int E2 = S::E2, E3 = S::E3, K1p = S::K1p, N1p = S::N1p, K2p = S::K2p, N2p = S::N2p;
@@ -294,13 +357,17 @@ __global__ void __launch_bounds__(MXT, 1) k_embed_bwd_mx(
     unsigned char *dA1 = A1 + S::A1B;
     unsigned char *B1 = dA1 + S::A1B;
     unsigned char *B2 = B1 + S::B1B;
-    double *gTs = reinterpret_cast<double *>(B2 + S::B2B);  // [4][E3], scaled
-    double *Ts = gTs + 4 * E3;                               // [4][E3]
+    double *gTs = reinterpret_cast<double *>(B2 + S::B2B);  // [AB][4][E3], scaled
+    double *Ts = gTs + AB * 4 * E3;                          // [4][E3]
     double *red = Ts + 4 * E3;                               // [4][12]
+    double *facc = red + 4 * 12;                             // [AB][12]
     __shared__ __align__(8) uint64_t mbar;
     __shared__ uint32_t tslot;
+    __shared__ BatchInfo bi;
+    __shared__ int tstart[DP_MAX_TYPES + 1];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int T = m.ntypes, nm = m.nm, m2 = m.m2;
+    if (tid <= T) tstart[tid] = type_start[tid];
     if (warp == 0) tc::tmem_alloc(&tslot, TCOLS);
     if (tid == 0) tc::mbar_init(&mbar, 1);
     tc_sync();
@@ -310,16 +377,21 @@ __global__ void __launch_bounds__(MXT, 1) k_embed_bwd_mx(
     uint32_t phase = 0;
     bool alive = true;
     int staged = -1;
+    const int lo = (int)(((long long)blockIdx.x * N) / gridDim.x);
+    const int hi = (int)(((long long)(blockIdx.x + 1) * N) / gridDim.x);
 
-    for (int ii = blockIdx.x; ii < N && alive; ii += gridDim.x) {
-        const int i = type_perm[ii];
-        const int a = types[i];
-        const bool a_ok = (unsigned)a < (unsigned)T;
-        const double xi[3] = {x[3 * i], x[3 * i + 1], x[3 * i + 2]};
-        // gT[c][x] = [x < M2] sum_b gD[x][b] T[c][b] + sum_{a<M2} gD[a][x] T[c][a], times the scale
-        for (int p = tid; p < 4 * E3; p += MXT) Ts[p] = Tin[(size_t)i * 4 * E3 + p];
+    for (int first = lo; first < hi && alive;) {
+        int a;
+        const int k = batch_size(first, hi, tstart, T, a);
         __syncthreads();
-        {
+        if (tid < AB) bi.ids[tid] = tid < k ? type_perm[first + tid] : 0;
+        for (int q = tid; q < AB * 12; q += MXT) facc[q] = 0.0;
+        __syncthreads();
+        // gT[c][x] = [x < M2] sum_b gD[x][b] T[c][b] + sum_{a<M2} gD[a][x] T[c][a], times the scale
+        for (int j = 0; j < k; ++j) {
+            const int i = bi.ids[j];
+            for (int p = tid; p < 4 * E3; p += MXT) Ts[p] = Tin[(size_t)i * 4 * E3 + p];
+            __syncthreads();
             const double *gd = gD + (size_t)i * m2 * E3;
             for (int p = tid; p < 4 * E3; p += MXT) {
                 const int cc = p / E3, xx = p - cc * E3;
@@ -327,39 +399,43 @@ __global__ void __launch_bounds__(MXT, 1) k_embed_bwd_mx(
                 if (xx < m2)
                     for (int b2i = 0; b2i < E3; ++b2i) acc = fma(gd[xx * E3 + b2i], Ts[cc * E3 + b2i], acc);
                 for (int a2 = 0; a2 < m2; ++a2) acc = fma(gd[a2 * E3 + xx], Ts[cc * E3 + a2], acc);
-                gTs[p] = acc * m.desc_scale;
+                gTs[j * 4 * E3 + p] = acc * m.desc_scale;
             }
+            __syncthreads();
         }
-        __syncthreads();
-        double fo[3] = {0.0, 0.0, 0.0}, vir[9];
-#pragma unroll
-        for (int q = 0; q < 9; ++q) vir[q] = 0.0;
-        for (int b = 0; b < T && alive; ++b) {
-            const int nb = a_ok ? nreal[(size_t)i * T + b] : 0;
-            if (nb == 0) continue;
+        const bool a_ok = (unsigned)a < (unsigned)T;
+        for (int b = 0; b < T && alive && a_ok; ++b) {
+            if (tid == 0) build_groups(bi, k, nreal, T, b);
+            __syncthreads();
+            const int G = bi.ngroups;
+            if (G == 0) continue;
             const int net = a * T + b;
             if (net != staged) {
-                __syncthreads();
                 copy16(B1, mx.emb_ops + mx.emb_off[net][0], S::B1B);
                 copy16(B2, mx.emb_ops + mx.emb_off[net][1], S::B2B);
                 staged = net;
             }
             const float *P32 = mx.p32 + m.emb_base[net];
             const float *W0 = P32, *b0 = P32 + E1, *b1 = P32 + 2 * E1 + E1 * E2, *b2 = b1 + E2 + E2 * E3;
-            for (int c0 = 0; c0 < nb && alive; c0 += MXT) {
-                const int r = c0 + tid;
-                const bool valid = r < nb;
-                const bool warp_live = c0 + 32 * warp < nb;
+            for (int t0 = 0; t0 < G && alive; t0 += 4) {
+                const int g = t0 + warp;
+                const bool warp_live = g < G;
+                const int j = warp_live ? bi.grp_atom[g] : 0;
+                const int i = bi.ids[j];
+                const int r = warp_live ? bi.grp_r0[g] + lane : 0;
+                const bool valid = warp_live && r < nreal[(size_t)i * T + b];
                 const int slot = m.sel_off[b] + r;
-                RowGeo g;
-                g.s = g.ds = 0.0;
-                g.R[0] = g.R[1] = g.R[2] = g.R[3] = 0.0;
-                g.d[0] = g.d[1] = g.d[2] = 0.0;
-                g.r = 1.0;
-                if (valid) geometry(m, x, xi, nlist[(size_t)i * nm + slot], box, g);
-                // layer 0 with its s-tangent
+                RowGeo gg;
+                gg.s = gg.ds = 0.0;
+                gg.R[0] = gg.R[1] = gg.R[2] = gg.R[3] = 0.0;
+                gg.d[0] = gg.d[1] = gg.d[2] = 0.0;
+                gg.r = 1.0;
+                if (valid) {
+                    const double xi[3] = {x[3 * i], x[3 * i + 1], x[3 * i + 2]};
+                    geometry(m, x, xi, nlist[(size_t)i * nm + slot], box, gg);
+                }
                 float h0[E1], dh0[E1];
-                const float s32 = (float)g.s;
+                const float s32 = (float)gg.s;
 #pragma unroll
                 for (int o = 0; o < E1; ++o) {
                     const float t = tanhf(fmaf(s32, W0[o], b0[o]));
@@ -436,8 +512,12 @@ __global__ void __launch_bounds__(MXT, 1) k_embed_bwd_mx(
                     tc::mma_commit(&mbar);
                 }
                 alive = tc_wait(&mbar, phase, status);
-                // epilogue 2: G, dG/ds and the FP64 contractions with gT
+                // epilogue 2: G, dG/ds and the FP64 contractions with gT of the row's atom
+                double fo[3] = {0.0, 0.0, 0.0}, vir[9];
+#pragma unroll
+                for (int q = 0; q < 9; ++q) vir[q] = 0.0;
                 if (alive && warp_live) {
+                    const double *gT = gTs + j * 4 * E3;
                     double ra[4] = {0.0, 0.0, 0.0, 0.0}, rb[4] = {0.0, 0.0, 0.0, 0.0};
 #pragma unroll
                     for (int cc = 0; cc < N2p; cc += 16) {
@@ -450,12 +530,12 @@ __global__ void __launch_bounds__(MXT, 1) k_embed_bwd_mx(
                             if (o < E3) {
                                 const int os = o < E2 ? o : o - E2;
                                 const float t = tanhf(v[q] + b2[o]);
-                                const double G = (double)(h1[os] + t);
+                                const double G2 = (double)(h1[os] + t);
                                 const double dG = (double)fmaf(fmaf(-t, t, 1.f), dv[q], dh1[os]);
 #pragma unroll
                                 for (int c = 0; c < 4; ++c) {
-                                    const double gt = gTs[c * E3 + o];
-                                    ra[c] = fma(G, gt, ra[c]);
+                                    const double gt = gT[c * E3 + o];
+                                    ra[c] = fma(G2, gt, ra[c]);
                                     rb[c] = fma(dG, gt, rb[c]);
                                 }
                             }
@@ -464,12 +544,12 @@ __global__ void __launch_bounds__(MXT, 1) k_embed_bwd_mx(
                     if (valid) {
                         double gR0 = ra[0];
 #pragma unroll
-                        for (int c = 0; c < 4; ++c) gR0 = fma(g.R[c], rb[c], gR0);
-                        const double inv = 1.0 / g.r;
-                        const double u[3] = {g.d[0] * inv, g.d[1] * inv, g.d[2] * inv};
+                        for (int c = 0; c < 4; ++c) gR0 = fma(gg.R[c], rb[c], gR0);
+                        const double inv = 1.0 / gg.r;
+                        const double u[3] = {gg.d[0] * inv, gg.d[1] * inv, gg.d[2] * inv};
                         const double dot = ra[1] * u[0] + ra[2] * u[1] + ra[3] * u[2];
-                        const double sr = g.s * inv;
-                        const double coef = gR0 * g.ds + g.ds * dot - sr * dot;
+                        const double sr = gg.s * inv;
+                        const double coef = gR0 * gg.ds + gg.ds * dot - sr * dot;
                         double gv[3];
 #pragma unroll
                         for (int bb = 0; bb < 3; ++bb) gv[bb] = fma(u[bb], coef, sr * ra[1 + bb]);
@@ -479,37 +559,43 @@ __global__ void __launch_bounds__(MXT, 1) k_embed_bwd_mx(
                         pg[2] = gv[2];
 #pragma unroll
                         for (int aa = 0; aa < 3; ++aa) {
-                            fo[aa] += gv[aa];
+                            fo[aa] = gv[aa];
 #pragma unroll
-                            for (int bb = 0; bb < 3; ++bb) vir[aa * 3 + bb] -= g.d[aa] * gv[bb];
+                            for (int bb = 0; bb < 3; ++bb) vir[aa * 3 + bb] = -gg.d[aa] * gv[bb];
                         }
+                    }
+                    // the group's own-force and virial part: fixed shuffle tree
+#pragma unroll
+                    for (int off = 16; off > 0; off >>= 1) {
+#pragma unroll
+                        for (int q = 0; q < 3; ++q) fo[q] += __shfl_xor_sync(0xffffffffu, fo[q], off);
+#pragma unroll
+                        for (int q = 0; q < 9; ++q) vir[q] += __shfl_xor_sync(0xffffffffu, vir[q], off);
+                    }
+                    if (lane == 0) {
+#pragma unroll
+                        for (int q = 0; q < 3; ++q) red[warp * 12 + q] = fo[q];
+#pragma unroll
+                        for (int q = 0; q < 9; ++q) red[warp * 12 + 3 + q] = vir[q];
                     }
                 }
                 tc_sync();
+                if (alive && tid < 12) {
+#pragma unroll
+                    for (int w = 0; w < 4; ++w)
+                        if (t0 + w < G) facc[bi.grp_atom[t0 + w] * 12 + tid] += red[w * 12 + tid];
+                }
+                __syncthreads();
             }
         }
         if (!alive) break;
-        // own force and virial part of atom i: fixed shuffle tree, then warps in order
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-#pragma unroll
-            for (int q = 0; q < 3; ++q) fo[q] += __shfl_xor_sync(0xffffffffu, fo[q], off);
-#pragma unroll
-            for (int q = 0; q < 9; ++q) vir[q] += __shfl_xor_sync(0xffffffffu, vir[q], off);
+        for (int q = tid; q < k * 12; q += MXT) {
+            const int j = q / 12, c = q - j * 12;
+            const int i = bi.ids[j];
+            if (c < 3) f_own[(size_t)i * 3 + c] = facc[q];
+            else vir_part[(size_t)i * 9 + c - 3] = facc[q];
         }
-        if (lane == 0) {
-#pragma unroll
-            for (int q = 0; q < 3; ++q) red[warp * 12 + q] = fo[q];
-#pragma unroll
-            for (int q = 0; q < 9; ++q) red[warp * 12 + 3 + q] = vir[q];
-        }
-        __syncthreads();
-        if (tid < 12) {
-            const double v = red[tid] + red[12 + tid] + red[24 + tid] + red[36 + tid];
-            if (tid < 3) f_own[(size_t)i * 3 + tid] = v;
-            else vir_part[(size_t)i * 9 + tid - 3] = v;
-        }
-        __syncthreads();
+        first += k;
     }
     if (!alive) tc::mbar_wait(&mbar, phase ^ 1u);
     tc_sync();
@@ -745,13 +831,14 @@ template <int E1>
 size_t fwd_smem()
 {
     using S = EmbShape<E1>;
-    return S::A0B + S::A1B + S::B1B + S::B2B + sizeof(double) * (4 * 32 * 17 + 4 * 32 * 4 + 4 * 4 * S::E3 + 4 * S::E3);
+    return S::A0B + S::A1B + S::B1B + S::B2B +
+           sizeof(double) * (4 * 32 * 17 + 4 * 32 * 4 + 4 * 4 * S::E3 + AB * 4 * S::E3);
 }
 template <int E1>
 size_t bwd_smem()
 {
     using S = EmbShape<E1>;
-    return 2 * S::A0B + 2 * S::A1B + S::B1B + S::B2B + sizeof(double) * (4 * S::E3 * 2 + 48);
+    return 2 * S::A0B + 2 * S::A1B + S::B1B + S::B2B + sizeof(double) * (AB * 4 * S::E3 + 4 * S::E3 + 48 + AB * 12);
 }
 
 template <int E1>
@@ -766,11 +853,11 @@ cudaError_t launch_fwd(cudaStream_t st, const DevModel &m, const MixedModel &mx,
         if (e != cudaSuccess) return e;
         configured = true;
     }
-    // two CTAs per SM (tensor memory: 128 columns each)
+    // two CTAs per SM (tensor memory: 128 columns each), each a balanced share of the atoms
     int grid = 2 * num_sms;
-    if (grid > N) grid = N;
-    k_embed_fwd_mx<E1><<<grid, MXT, smem, st>>>(m, mx, x, types, box, N, nb.type_perm, fb.nlist, fb.nreal, eb.T,
-                                                eb.D, status);
+    if (grid > (N + 7) / 8) grid = (N + 7) / 8;
+    k_embed_fwd_mx<E1><<<grid, MXT, smem, st>>>(m, mx, x, types, box, N, nb.type_perm, nb.type_start, fb.nlist,
+                                                fb.nreal, eb.T, eb.D, status);
     return cudaGetLastError();
 }
 
@@ -786,11 +873,11 @@ cudaError_t launch_bwd(cudaStream_t st, const DevModel &m, const MixedModel &mx,
         if (e != cudaSuccess) return e;
         configured = true;
     }
-    // two CTAs per SM (tensor memory: <= 256 columns each)
+    // two CTAs per SM (tensor memory: <= 256 columns each), each a balanced share of the atoms
     int grid = 2 * num_sms;
-    if (grid > N) grid = N;
-    k_embed_bwd_mx<E1><<<grid, MXT, smem, st>>>(m, mx, x, types, box, N, nb.type_perm, fb.nlist, fb.nreal, eb.T,
-                                                eb.gD, eb.pair_g, eb.f_own, eb.vir_part, status);
+    if (grid > (N + 7) / 8) grid = (N + 7) / 8;
+    k_embed_bwd_mx<E1><<<grid, MXT, smem, st>>>(m, mx, x, types, box, N, nb.type_perm, nb.type_start, fb.nlist,
+                                                fb.nreal, eb.T, eb.gD, eb.pair_g, eb.f_own, eb.vir_part, status);
     return cudaGetLastError();
 }
 

@@ -154,11 +154,13 @@ dp_status dp_build_nlist(dp_ctx *ctx, const double *coords, const int32_t *types
                          const double box[9], int64_t N, double skin);
 
 /* Algorithm 1 (formatted neighbour list) from the current coordinates and the
- * candidates of the last dp_build_nlist.  Writes nlist[N][N_m] (int32 atom
- * indices, -1 = padding; type blocks of sel[a] slots in type order, each
- * sorted by (floor(|r_ij| * 1e8), j)) and nreal[N][ntypes] (1 + the last slot
- * of the block with |r_ij| < rcut, 0 if none).  Either output may be NULL.
- * Device pointers.  DP_ERR_SEL_OVERFLOW if a neighbour within rcut was cut. */
+ * candidates of the last dp_build_nlist: the neighbours within rcut -- L(i)
+ * of Sec. 2 -- in type blocks of sel[a] slots in type order, each block sorted
+ * by (floor(|r_ij| * 1e8), j), truncated to sel[a] and padded with -1.  Writes
+ * nlist[N][N_m] (int32 atom indices) and nreal[N][ntypes] (entries kept in
+ * each block).  Either output may be NULL.  Device pointers.  The result does
+ * not depend on the skin of the candidates.  DP_ERR_SEL_OVERFLOW if a
+ * neighbour within rcut was cut. */
 dp_status dp_format_nlist(dp_ctx *ctx, const double *coords, const int32_t *types,
                           const double box[9], int64_t N, int32_t *nlist, int32_t *nreal);
 

@@ -206,13 +206,14 @@ static int orc_S_cmp(const void *pa, const void *pb)
     return 0;
 }
 
-/* Algorithm 1 (Formatting the neighbour list): for each atom i, build
- * S(i,k) = (alpha(j), |r_ij|, j) for its candidates, sort by type, then
+/* Algorithm 1 (Formatting the neighbour list) on L(i) = {j : |r_ij| <= rcut}
+ * (Sec. 2): the candidates of atom i (built with a buffer, Sec. 4) are
+ * restricted to L(i); S(i,k) = (alpha(j), |r_ij|, j) is sorted by type, then
  * distance, then smaller index on ties (Sec. 3.2.2 text; the distance is the
- * 1e-8 A quantum of the compressed key), keep the first sel_alpha entries of
- * each type and pad the rest of the type block with -1.
- * Outputs: nlist[N][N_m]; nreal[N][T] = 1 + last slot in block with r < rcut
- * (0 if none); overflow[N] = neighbours with r < rcut that did not fit. */
+ * 1e-8 A quantum of the compressed key), the first sel_alpha entries of each
+ * type are kept and the rest of the type block is padded with -1.
+ * Outputs: nlist[N][N_m]; nreal[N][T] = entries kept in block T;
+ * overflow[N] = neighbours within rcut that did not fit sel. */
 int orc_format(int64_t N, const double *x, const int32_t *types, const double *box,
                const int32_t *ncand, const int32_t *cand, int32_t cap, int32_t ntypes,
                const int32_t *sel, double rcut, int32_t *nlist, int32_t *nreal,
@@ -225,32 +226,33 @@ int orc_format(int64_t N, const double *x, const int32_t *types, const double *b
         orc_S *S = (orc_S *)malloc(sizeof(orc_S) * (size_t)(cap > 0 ? cap : 1));
 #pragma omp for schedule(dynamic, 16)
         for (int64_t i = 0; i < N; ++i) {
-            int n = ncand[i];
-            for (int k = 0; k < n; ++k) {
+            int n = 0;
+            for (int k = 0; k < ncand[i]; ++k) {
                 int j = cand[i * cap + k];
                 double d[3];
                 orc_min_image(box, x + 3 * i, x + 3 * j, d);
                 double r = orc_norm(d);
-                S[k].alpha = types[j];
-                S[k].q = (uint64_t)floor(r * 1e8);
-                S[k].j = j;
-                S[k].r = r;
+                if (r > rcut) continue;
+                S[n].alpha = types[j];
+                S[n].q = (uint64_t)floor(r * 1e8);
+                S[n].j = j;
+                S[n].r = r;
+                ++n;
             }
             qsort(S, (size_t)n, sizeof(orc_S), orc_S_cmp);
             int cnt[ORC_MAXT] = {0};
             int64_t over = 0;
             for (int k = 0; k < nm; ++k) nlist[i * nm + k] = -1;
-            for (int a = 0; a < ntypes; ++a) nreal[i * ntypes + a] = 0;
             for (int k = 0; k < n; ++k) {
                 int a = S[k].alpha;
                 if (cnt[a] < sel[a]) {
                     nlist[i * nm + off[a] + cnt[a]] = S[k].j;
-                    if (S[k].r < rcut) nreal[i * ntypes + a] = cnt[a] + 1;
                     cnt[a]++;
-                } else if (S[k].r < rcut) {
+                } else {
                     over++;
                 }
             }
+            for (int a = 0; a < ntypes; ++a) nreal[i * ntypes + a] = cnt[a];
             overflow[i] = over;
         }
         free(S);

@@ -115,6 +115,8 @@ struct dp_ctx {
     // device status word + pinned host mirror
     int32_t *d_status;
     int32_t *d_gate;   // conditional-rebuild flag (0 between steps)
+    int32_t *d_retry;  // Algorithm 1 second-pass list: count, then atoms
+    int sort_small;    // width of the first-pass sorting network
     int32_t *h_status;
     // neighbour candidates
     NlistBuffers nb;
@@ -429,6 +431,15 @@ dp_status do_build(dp_ctx *c, const double *coords, const int32_t *types, const 
         c->ncell_cap = ncell;
     }
     for (int a = 0; a < 3; ++a) c->nc[a] = nc[a];
+    {
+        // first-pass sort width: 1.15 x the mean number of neighbours within
+        // rcut, rounded up to a power of two (denser atoms take the second pass)
+        const double vol = b.L[0] * b.L[1] * b.L[2];
+        const double expect = (double)N / vol * 4.0 / 3.0 * M_PI * c->m.rcut * c->m.rcut * c->m.rcut;
+        int sw = 64;
+        while (sw < 1.15 * expect + 8.0 && sw < 1024) sw *= 2;
+        c->sort_small = sw;
+    }
     GroupTimer tm(c, G_BUILD);
     cudaError_t e = cudaSuccess;
     if (gated) e = dp_launch_check_stale(c->stream, coords, c->nb.xref, (int)N, b, 0.25 * skin * skin, c->d_gate,
@@ -446,8 +457,8 @@ dp_status do_build(dp_ctx *c, const double *coords, const int32_t *types, const 
 dp_status enqueue_format(dp_ctx *c, const double *coords, const int32_t *types, const Box3 &b, int64_t N)
 {
     GroupTimer tm(c, G_FORMAT);
-    cudaError_t e = dp_launch_format(c->stream, c->m, coords, types, b, (int)N, c->cap, c->skin, c->nb,
-                                     c->fb, c->d_status, &c->launches);
+    cudaError_t e = dp_launch_format(c->stream, c->m, coords, types, b, (int)N, c->cap, c->sort_small, c->skin,
+                                     c->nb, c->fb, c->d_status, c->d_retry, &c->launches);
     if (e != cudaSuccess) return cuda_fail(e, "format");
     return DP_OK;
 }
@@ -669,6 +680,7 @@ void dp_ctx_free(dp_ctx *c)
     for (cudaEvent_t e : c->events) cudaEventDestroy(e);
     dev_free(c->d_status);
     dev_free(c->d_gate);
+    dev_free(c->d_retry);
     if (c->h_status) cudaFreeHost(c->h_status);
     if (c->h_mass_stage) cudaFreeHost(c->h_mass_stage);
     void *bufs[] = {c->nb.cand, c->nb.ncand, c->nb.xref, c->nb.cell_count, c->nb.cell_start,
@@ -715,6 +727,7 @@ dp_status dp_ctx_create(const dp_model *model, int64_t natoms_max, int32_t cand_
     if (!s) s = dev_alloc(&(ptr), (n), #ptr)
     ALLOC(c->d_status, 1);
     ALLOC(c->d_gate, 1);
+    ALLOC(c->d_retry, N + 1);
     ALLOC(c->nb.ncand, N);
     ALLOC(c->nb.xref, 3 * N);
     ALLOC(c->nb.cell_atoms, N);

@@ -132,9 +132,14 @@ cudaError_t dp_launch_build(cudaStream_t st, const DevModel &m, const double *x,
 // Sets *gate if an atom moved more than sqrt(stale2) from its reference position.
 cudaError_t dp_launch_check_stale(cudaStream_t st, const double *x, const double *xref, int N, Box3 box,
                                   double stale2, int32_t *gate, int64_t *launches);
+// Algorithm 1 on the candidates within rcut.  sort_small (a power of two,
+// 64..1024) is the width of the first pass's sorting network; atoms with more
+// neighbours go to a second pass as wide as cap.  retry: device int32
+// [1 + N] (count, then atom list), cleared here.
 cudaError_t dp_launch_format(cudaStream_t st, const DevModel &m, const double *x,
-                             const int32_t *types, Box3 box, int N, int cap, double skin,
-                             NlistBuffers nb, FormatBuffers fb, int32_t *status, int64_t *launches);
+                             const int32_t *types, Box3 box, int N, int cap, int sort_small, double skin,
+                             NlistBuffers nb, FormatBuffers fb, int32_t *status, int32_t *retry,
+                             int64_t *launches);
 
 struct EvalBuffers {
     double *T;         // [N][4][M]

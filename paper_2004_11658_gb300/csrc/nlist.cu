@@ -332,43 +332,79 @@ __device__ __forceinline__ void warp_bitonic_sort(uint64_t (&v)[KPL], int lane)
     }
 }
 
+// One warp per atom.  The candidates within rcut -- L(i) of Sec. 2 -- are
+// keyed and compacted into a per-warp shared buffer with ballots, then sorted
+// by a KPL*32-wide bitonic network in registers.  In the first pass (retry
+// list null) an atom with more than KPL*32 keys is appended to the retry list
+// and left to a second launch with a network as wide as the candidate cap.
 template <int KPL>
 __global__ void __launch_bounds__(128) k_format(
     DevModel m, const double *__restrict__ x, const int32_t *__restrict__ types, Box3 box, int N,
     int cap, double stale2, const int32_t *__restrict__ cand, const int32_t *__restrict__ ncand,
     const double *__restrict__ xref, int32_t *__restrict__ nlist, uint64_t *__restrict__ keys,
-    int32_t *__restrict__ nreal, int32_t *status)
+    int32_t *__restrict__ nreal, int32_t *status, int32_t *retry_count, int32_t *retry_list, int retry_pass)
 {
-    const int lane = threadIdx.x & 31;
-    const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (i >= N) return;
+    constexpr int S = 32 * KPL;
+    __shared__ uint64_t kbuf[4][S];
+    const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int i;
+    if (retry_pass) {
+        if (w >= *retry_count) return;
+        i = retry_list[w];
+    } else {
+        if (w >= N) return;
+        i = w;
+    }
     const int nm = m.nm, T = m.ntypes;
     const double xi[3] = {x[3 * i], x[3 * i + 1], x[3 * i + 2]};
-    const int n = ncand[i];
-    if (lane == 0 && stale2 > 0.0) {
+    const int ncnd = ncand[i];
+    if (!retry_pass && lane == 0 && stale2 > 0.0) {
         double d[3];
         const double xr[3] = {xref[3 * i], xref[3 * i + 1], xref[3 * i + 2]};
         double r = dp_pinned_dist(xr, xi, box, d);
         if (r * r > stale2) atomicOr(status, DPF_STALE);
     }
     const int32_t *row = cand + (size_t)i * cap;
-    uint64_t v[KPL];
-#pragma unroll
-    for (int e = 0; e < KPL; ++e) {
-        const int idx = e * 32 + lane;
-        v[e] = DP_KEY_NONE;
-        if (idx < n) {
+    uint64_t *kb = kbuf[wl];
+    int n = 0;
+    for (int c0 = 0; c0 < ncnd; c0 += 32) {
+        const int idx = c0 + lane;
+        bool take = false;
+        uint64_t key = 0;
+        if (idx < ncnd) {
             const int j = row[idx];
             const int tj = types[j];
             if ((unsigned)tj < (unsigned)T) {
                 double d[3];
                 const double xj[3] = {x[3 * j], x[3 * j + 1], x[3 * j + 2]};
                 const double r = dp_pinned_dist(xi, xj, box, d);
-                v[e] = dp_pack_key(tj, r, j);
+                if (r <= m.rcut) {
+                    take = true;
+                    key = dp_pack_key(tj, r, j);
+                }
             } else {
                 atomicOr(status, DPF_BAD_TYPE);
             }
         }
+        const unsigned bal = __ballot_sync(FULL, take);
+        const int pos = n + __popc(bal & ((1u << lane) - 1u));
+        if (take && pos < S) kb[pos] = key;
+        n += __popc(bal);
+    }
+    if (n > S) {  // cannot happen in the retry pass (S >= cap >= ncand)
+        if (lane == 0) {
+            const int slot = atomicAdd(retry_count, 1);
+            retry_list[slot] = i;
+        }
+        return;
+    }
+    __syncwarp();
+    uint64_t v[KPL];
+#pragma unroll
+    for (int e = 0; e < KPL; ++e) {
+        const int p = lane * KPL + e;
+        v[e] = p < n ? kb[p] : DP_KEY_NONE;
     }
     warp_bitonic_sort<KPL>(v, lane);
 
@@ -379,22 +415,19 @@ __global__ void __launch_bounds__(128) k_format(
         krow[s] = DP_KEY_NONE;
     }
     __syncwarp();
-
-    // start of each type block in the sorted sequence
-    int start[DP_MAX_TYPES];
+    // start of each type block in the sorted sequence (start[T] = n)
+    int start[DP_MAX_TYPES + 1];
 #pragma unroll
-    for (int a = 0; a < DP_MAX_TYPES; ++a) {
-        int c = 0;
+    for (int a = 0; a <= DP_MAX_TYPES; ++a) {
+        int c = n;
         if (a < T) {
+            c = 0;
 #pragma unroll
             for (int e = 0; e < KPL; ++e) c += (v[e] != DP_KEY_NONE) && ((int)(v[e] >> 60) < a);
             c = __reduce_add_sync(FULL, c);
         }
         start[a] = c;
     }
-    int lastreal[DP_MAX_TYPES];
-#pragma unroll
-    for (int a = 0; a < DP_MAX_TYPES; ++a) lastreal[a] = 0;
     int ovf = 0;
 #pragma unroll
     for (int e = 0; e < KPL; ++e) {
@@ -410,28 +443,23 @@ __global__ void __launch_bounds__(128) k_format(
                 off = m.sel_off[a];
             }
         const int rank = lane * KPL + e - st;
-        double d[3];
-        const double xj[3] = {x[3 * j], x[3 * j + 1], x[3 * j + 2]};
-        const double r = dp_pinned_dist(xi, xj, box, d);
-        const bool within = r < m.rcut;
         if (rank < sel) {
             nrow[off + rank] = j;
             krow[off + rank] = v[e];
-            if (within) {
-#pragma unroll
-                for (int a = 0; a < DP_MAX_TYPES; ++a)
-                    if (a == ta) lastreal[a] = max(lastreal[a], rank + 1);
-            }
-        } else if (within) {
+        } else {
             ++ovf;
         }
     }
+    if (lane < T) {
+        int st = 0, en = 0, sel = 0;
 #pragma unroll
-    for (int a = 0; a < DP_MAX_TYPES; ++a) {
-        if (a < T) {
-            int nr = __reduce_max_sync(FULL, lastreal[a]);
-            if (lane == 0) nreal[(size_t)i * T + a] = nr;
-        }
+        for (int a = 0; a < DP_MAX_TYPES; ++a)
+            if (a == lane) {
+                st = start[a];
+                en = start[a + 1];
+                sel = m.sel[a];
+            }
+        nreal[(size_t)i * T + lane] = min(en - st, sel);
     }
     ovf = __reduce_add_sync(FULL, ovf);
     if (lane == 0 && ovf) atomicOr(status, DPF_SEL_OVERFLOW);
@@ -478,18 +506,32 @@ cudaError_t dp_launch_check_stale(cudaStream_t st, const double *x, const double
 }
 
 cudaError_t dp_launch_format(cudaStream_t st, const DevModel &m, const double *x,
-                             const int32_t *types, Box3 box, int N, int cap, double skin,
-                             NlistBuffers nb, FormatBuffers fb, int32_t *status, int64_t *launches)
+                             const int32_t *types, Box3 box, int N, int cap, int sort_small, double skin,
+                             NlistBuffers nb, FormatBuffers fb, int32_t *status, int32_t *retry,
+                             int64_t *launches)
 {
     const int blocks = (N + 3) / 4;
     const double stale2 = skin > 0.0 ? 0.25 * skin * skin : 0.0;
-#define DP_FMT(K)                                                                                 \
-    k_format<K><<<blocks, 128, 0, st>>>(m, x, types, box, N, cap, stale2, nb.cand, nb.ncand,      \
-                                        nb.xref, fb.nlist, fb.keys, fb.nreal, status)
-    if (cap <= 128) DP_FMT(4);
-    else if (cap <= 256) DP_FMT(8);
-    else if (cap <= 512) DP_FMT(16);
-    else DP_FMT(32);
+    cudaMemsetAsync(retry, 0, sizeof(int32_t), st);
+#define DP_FMT(K, RP)                                                                                  \
+    k_format<K><<<blocks, 128, 0, st>>>(m, x, types, box, N, cap, stale2, nb.cand, nb.ncand, nb.xref,  \
+                                        fb.nlist, fb.keys, fb.nreal, status, retry, retry + 1, RP)
+    // first pass: network of sort_small keys
+    switch (sort_small) {
+    case 64: DP_FMT(2, 0); break;
+    case 128: DP_FMT(4, 0); break;
+    case 256: DP_FMT(8, 0); break;
+    case 512: DP_FMT(16, 0); break;
+    default: DP_FMT(32, 0); break;
+    }
+    // second pass for the atoms the first one could not hold (returns at once when none)
+    if (sort_small < cap) {
+        if (cap <= 128) DP_FMT(4, 1);
+        else if (cap <= 256) DP_FMT(8, 1);
+        else if (cap <= 512) DP_FMT(16, 1);
+        else DP_FMT(32, 1);
+        *launches += 1;
+    }
 #undef DP_FMT
     *launches += 1;
     return cudaGetLastError();

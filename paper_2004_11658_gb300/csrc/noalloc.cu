@@ -28,9 +28,10 @@ constexpr size_t kOffTypePerm = kOffTypeStart + 256;
 constexpr size_t kOffXref = kOffTypePerm + sizeof(int32_t) * kMaxAtoms;
 constexpr size_t kOffCand = kOffXref + sizeof(double) * 3 * kMaxAtoms;
 constexpr size_t kOffKeys = kOffCand + sizeof(int32_t) * (size_t)kMaxAtoms * kCap;
-constexpr size_t kScratchBytes = kOffKeys + sizeof(uint64_t) * (size_t)kMaxAtoms * DP_MAX_NM;
+constexpr size_t kOffRetry = kOffKeys + sizeof(uint64_t) * (size_t)kMaxAtoms * DP_MAX_NM;
+constexpr size_t kScratchBytes = kOffRetry + sizeof(int32_t) * (kMaxAtoms + 64);
 static_assert(kOffNcand % 256 == 0 && kOffTypeStart % 256 == 0 && kOffTypePerm % 256 == 0 &&
-                  kOffXref % 256 == 0 && kOffCand % 256 == 0 && kOffKeys % 256 == 0,
+                  kOffXref % 256 == 0 && kOffCand % 256 == 0 && kOffKeys % 256 == 0 && kOffRetry % 256 == 0,
               "scratch regions must stay 256-byte aligned");
 
 // The scratch itself.  In host code this name is only a stand-in for the
@@ -130,7 +131,8 @@ extern "C" dp_status dp_format_nlist_noalloc(const dp_model_desc *desc, const do
     if (e == cudaSuccess)
         e = dp_launch_build(st, m, coords, types, b, (int)N, rlist, kCap, nc, nb, status, nullptr, &launches);
     if (e == cudaSuccess)
-        e = dp_launch_format(st, m, coords, types, b, (int)N, kCap, 0.0, nb, fb, status, &launches);
+        e = dp_launch_format(st, m, coords, types, b, (int)N, kCap, kCap, 0.0, nb, fb, status,
+                             (int32_t *)(base + kOffRetry), &launches);
     int32_t flags = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&flags, status, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);

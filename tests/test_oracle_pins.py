@@ -89,18 +89,17 @@ def _py_format(x, types, L, sel, rcut, rlist):
                 n = round(v / L[a])            # round half to even, like rint
                 d.append(v - L[a] * n)
             r = math.sqrt((d[0] * d[0] + d[1] * d[1]) + d[2] * d[2])
-            if r <= rlist:
+            if r <= rcut:          # L(i) of Sec. 2 (the skin only widens the candidates)
                 S.append((int(types[j]), math.floor(r * 1e8), j, r))
         S.sort(key=lambda t: (t[0], t[1], t[2]))
         cnt = [0] * len(sel)
         for (a, q, j, r) in S:
             if cnt[a] < sel[a]:
                 nlist[i][off[a] + cnt[a]] = j
-                if r < rcut:
-                    nreal[i][a] = cnt[a] + 1
                 cnt[a] += 1
-            elif r < rcut:
+            else:
                 ovf[i] += 1
+        nreal[i] = cnt
     return np.array(nlist), np.array(nreal), np.array(ovf)
 
 
@@ -131,6 +130,10 @@ def test_format_tie_break_by_index(oracle):
     nl, nr, _ = oracle.format_nlist(x, types, L, ncand, cand, (4,), 4.0)
     assert nl[0].tolist() == [1, 2, 3, -1]
     assert nr[0].tolist() == [3]
+    # the list holds L(i) only: with rcut 1.2 A atom 3 (1.5 A away) is left out
+    nl, nr, _ = oracle.format_nlist(x, types, L, ncand, cand, (4,), 1.2)
+    assert nl[0].tolist() == [1, 2, -1, -1]
+    assert nr[0].tolist() == [2]
 
 
 # ------------------------------------------------- closed-form energies --

@@ -164,6 +164,14 @@ dp_status dp_build_nlist(dp_ctx *ctx, const double *coords, const int32_t *types
 dp_status dp_format_nlist(dp_ctx *ctx, const double *coords, const int32_t *types,
                           const double box[9], int64_t N, int32_t *nlist, int32_t *nreal);
 
+/* The FP64 tanh used by the FP64 kernels (piecewise degree-8 Taylor
+ * polynomials of tanh on intervals of width 1/20, |error| < 1e-16 absolute),
+ * exposed so that its accuracy can be checked: y[i] = tanh(x[i]) for n device
+ * doubles, on stream (NULL = legacy default); returns after the stream has
+ * finished.  The paper's nets use tanh as their activation (Eqs.
+ * embedding-first, embedding-rest, fitting-detail). */
+dp_status dp_tanh_f64(const double *x, double *y, int64_t n, void *stream);
+
 /* No-allocation variant of dp_format_nlist.  The paper has no counterpart:
  * this entry point exists for callers that cannot allocate device memory at
  * the time they need the list -- a host MD engine that owns a fixed device

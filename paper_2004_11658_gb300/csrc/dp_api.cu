@@ -757,6 +757,12 @@ dp_status dp_ctx_create(const dp_model *model, int64_t natoms_max, int32_t cand_
     }
 #undef ALLOC
     if (!s && precision == DP_PREC_MIXED) s = build_mixed(c);
+    if (!s) {
+        const double *tab = nullptr;
+        cudaError_t e = dp_tanh_setup(&tab);
+        if (e != cudaSuccess) s = cuda_fail(e, "tanh table");
+        c->m.tanh_tab = tab;
+    }
     if (!s && cudaMallocHost((void **)&c->h_status, sizeof(int32_t)) != cudaSuccess) {
         c->h_status = nullptr;
         s = fail(DP_ERR_NOMEM, "pinned allocation failed");

@@ -31,6 +31,7 @@ struct DevModel {
     int emb_net_size;                       // doubles per embedding net
     double rcut, rcut_smth, desc_scale;
     const double *params;                   // device
+    const double *tanh_tab;                 // device, see dp_tanh64
     int64_t emb_base[DP_MAX_TYPES * DP_MAX_TYPES];
     int64_t fit_base[DP_MAX_TYPES];
 };
@@ -93,6 +94,31 @@ __device__ __forceinline__ void dp_switch(double r, double rs, double rc, double
         s = 0.0;
         ds = 0.0;
     }
+}
+
+// FP64 tanh by piecewise Taylor polynomials (tanh64.cu): interval k is
+// centred at k/20, k = 0..DP_TANH_NINT-1, and stores [centre, a_0 .. a_8].
+#define DP_TANH_NINT 383
+#define DP_TANH_NCOEF 9
+#define DP_TANH_STRIDE (DP_TANH_NCOEF + 1)
+// Fills the table on the current device (once) and returns its device address.
+cudaError_t dp_tanh_setup(const double **table);
+
+__device__ __forceinline__ double dp_tanh64(double x, const double *__restrict__ tab)
+{
+    const double ax = fabs(x);
+    // |x| >= 19.125: tanh = +-1 to double precision (1 - tanh(19.125) < 2^-55)
+    const long long bits = __double_as_longlong(ax);
+    if (bits >= 0x4033200000000000ll) return bits > 0x7ff0000000000000ll ? x : copysign(1.0, x);  // NaN stays NaN
+    // k = round(20 |x|) from the low bits of 20|x| + 1.5 * 2^52
+    const double v = fma(ax, 20.0, 6755399441055744.0);
+    const int k = (int)(__double_as_longlong(v) & 0xffffffffll);
+    const double *c = tab + k * DP_TANH_STRIDE;
+    const double t = ax - c[0];
+    double p = c[DP_TANH_NCOEF];
+#pragma unroll
+    for (int n = DP_TANH_NCOEF - 1; n >= 1; --n) p = fma(p, t, c[n]);
+    return copysign(p, x);
 }
 
 // Skip kind of an (in -> out) layer: 2 = (x, x), 1 = x, 0 = none.

@@ -104,7 +104,7 @@ __global__ void __launch_bounds__(NTHREADS) k_embed_fwd(
                 {
                     const double sv = srow[lane];
                     for (int o = warp; o < e1; o += NWARPS)
-                        bufA[lane * LD + o] = tanh(fma(sv, Wsm[o], Wsm[e1 + o]));
+                        bufA[lane * LD + o] = dp_tanh64(fma(sv, Wsm[o], Wsm[e1 + o]), m.tanh_tab);
                 }
                 __syncthreads();
                 double *in = bufA, *out = bufB;
@@ -118,7 +118,7 @@ __global__ void __launch_bounds__(NTHREADS) k_embed_fwd(
                     for (int o = warp; o < wout; o += NWARPS) {
                         double z = bb[o];
                         for (int q = 0; q < win; ++q) z = fma(hr[q], W[q * wout + o], z);
-                        const double t = tanh(z);
+                        const double t = dp_tanh64(z, m.tanh_tab);
                         const double skip = sk == 2 ? hr[o < win ? o : o - win] : (sk == 1 ? hr[o] : 0.0);
                         out[lane * LD + o] = skip + t;
                     }
@@ -249,7 +249,7 @@ __global__ void __launch_bounds__(NTHREADS) k_embed_bwd(
                     const double sv = srow[lane];
                     for (int o = warp; o < e1; o += NWARPS) {
                         const double w0 = Wsm[o];
-                        const double t = tanh(fma(sv, w0, Wsm[e1 + o]));
+                        const double t = dp_tanh64(fma(sv, w0, Wsm[e1 + o]), m.tanh_tab);
                         A[lane * LD + o] = t;
                         dA[lane * LD + o] = fma(-t, t, 1.0) * w0;
                     }
@@ -272,7 +272,7 @@ __global__ void __launch_bounds__(NTHREADS) k_embed_bwd(
                             z = fma(hr[q], w, z);
                             dz = fma(dhr[q], w, dz);
                         }
-                        const double t = tanh(z);
+                        const double t = dp_tanh64(z, m.tanh_tab);
                         const int os = o < win ? o : o - win;
                         const double skip = sk == 2 ? hr[os] : (sk == 1 ? hr[o] : 0.0);
                         const double dskip = sk == 2 ? dhr[os] : (sk == 1 ? dhr[o] : 0.0);

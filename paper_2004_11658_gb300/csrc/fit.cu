@@ -141,7 +141,7 @@ __global__ void __launch_bounds__(NTH, 1) k_fit(
                 const int n = tx + 16 * jj;
                 hnew[jj] = 0.0;
                 if (n < F) {
-                    const double t = tanh(acc[jj] + bl[n]);
+                    const double t = dp_tanh64(acc[jj] + bl[n], m.tanh_tab);
                     Ts[(l * RT + ty) * LDH + n] = t;
                     const double skip = sk == 2 ? Hs[ty * LDH + (n < Kin ? n : n - Kin)]
                                                 : (sk == 1 ? Hs[ty * LDH + n] : 0.0);

@@ -95,6 +95,8 @@ def lib():
             L.dp_ctx_kernel_times.argtypes = [_vp, _vp, _vp]
             L.dp_kernel_group_name.restype = ctypes.c_char_p
             L.dp_kernel_group_name.argtypes = [_i32]
+            L.dp_tanh_f64.restype = _i32
+            L.dp_tanh_f64.argtypes = [_vp, _vp, _i64, _vp]
             L.dp_format_nlist_noalloc.restype = _i32
             L.dp_format_nlist_noalloc.argtypes = [ctypes.POINTER(dp_model_desc), _vp, _vp, _vp, _i64, _dbl,
                                                   _vp, _vp, _vp]
@@ -265,6 +267,15 @@ def dp_format_nlist(ctx, coords, types, box, check=True):
     if check:
         _check(s)
     return nlist, nreal, s
+
+
+def dp_tanh_f64(x, stream=None):
+    """The library's FP64 tanh (used by the FP64 kernels) on a CUDA tensor."""
+    y = torch.empty_like(x)
+    st = stream if stream is not None else torch.cuda.current_stream()
+    _check(lib().dp_tanh_f64(_dev(x, torch.float64), _dev(y, torch.float64), x.numel(),
+                             ctypes.c_void_p(st.cuda_stream)))
+    return y
 
 
 def dp_format_nlist_noalloc(desc, coords, types, box, skin=0.0, nlist=None, nreal=None, stream=None,

@@ -677,3 +677,313 @@ int orc_num_threads(void)
     return 1;
 #endif
 }
+
+/* ------------------------------------------------------ parameter gradient */
+
+/* Gradient with respect to every model parameter of
+ *     Phi(W) = cE * E(W) + sum_i lambda_i . F_i(W)
+ *            = cE * E(W) - sum_i lambda_i . dE/dr_i,
+ * i.e. the parameter gradient of any loss on the energy and forces, with
+ * cE = dLoss/dE and lambda_i = dLoss/dF_i (Remark 2: F = -grad E).  Per atom
+ * i, the second term is the directional derivative of E_i along the
+ * neighbour displacements delta r_ij = lambda_j - lambda_i; it is evaluated
+ * by forward tangents through the environment matrix (Algorithm 2), the
+ * embedding net, the descriptor and the fitting net, then differentiated by
+ * plain reverse mode.  grad[nparams] is overwritten. */
+typedef struct {
+    double *R, *dR, *J;      /* [nm][4], [nm][4], [nm][4][3] */
+    double *s, *ds;          /* [nm] */
+    int *real;
+    double *h, *t, *dh;      /* embedding [nm][se] */
+    double *T, *dT, *Tb, *dTb;   /* [4][M] */
+    double *D, *dD, *Db, *dDb;   /* [M2*M] */
+    double *fh, *ft, *fdh;   /* fitting [nf][mf] */
+    double *a0, *a1, *b0, *b1;   /* adjoint buffers [max width] */
+    double *g;               /* per-thread gradient [nparams] */
+} orc_gws;
+
+static void orc_gws_alloc(const orc_model *m, orc_gws *w)
+{
+    int nm = m->nm, M = m->emb[m->n_emb - 1], se = 0, mf = 0;
+    for (int l = 0; l < m->n_emb; ++l) se += m->emb[l];
+    for (int l = 0; l < m->n_fit; ++l) if (m->fit[l] > mf) mf = m->fit[l];
+    int mw = orc_max_width(m);
+    w->R = calloc((size_t)nm * 4, 8); w->dR = calloc((size_t)nm * 4, 8); w->J = calloc((size_t)nm * 12, 8);
+    w->s = calloc(nm, 8); w->ds = calloc(nm, 8); w->real = calloc(nm, sizeof(int));
+    w->h = calloc((size_t)nm * se, 8); w->t = calloc((size_t)nm * se, 8); w->dh = calloc((size_t)nm * se, 8);
+    w->T = calloc(4 * M, 8); w->dT = calloc(4 * M, 8); w->Tb = calloc(4 * M, 8); w->dTb = calloc(4 * M, 8);
+    w->D = calloc(m->m2 * M, 8); w->dD = calloc(m->m2 * M, 8); w->Db = calloc(m->m2 * M, 8); w->dDb = calloc(m->m2 * M, 8);
+    w->fh = calloc((size_t)m->n_fit * mf, 8); w->ft = calloc((size_t)m->n_fit * mf, 8); w->fdh = calloc((size_t)m->n_fit * mf, 8);
+    w->a0 = calloc(mw, 8); w->a1 = calloc(mw, 8); w->b0 = calloc(mw, 8); w->b1 = calloc(mw, 8);
+    w->g = calloc((size_t)m->nparams, 8);
+}
+
+static void orc_gws_free(orc_gws *w)
+{
+    free(w->R); free(w->dR); free(w->J); free(w->s); free(w->ds); free(w->real);
+    free(w->h); free(w->t); free(w->dh); free(w->T); free(w->dT); free(w->Tb); free(w->dTb);
+    free(w->D); free(w->dD); free(w->Db); free(w->dDb); free(w->fh); free(w->ft); free(w->fdh);
+    free(w->a0); free(w->a1); free(w->b0); free(w->b1); free(w->g);
+}
+
+/* reverse through one layer  h = skip(x) + tanh(x W + b),  dh = skip(dx) + (1-t^2)(dx W)
+ * given the primal/tangent adjoints hb, dhb of the output; accumulates the
+ * adjoints of the input into xb, dxb and the weight gradient into gW, gb. */
+static void orc_layer_rev(const double *x, const double *dx, const double *t, const double *W, int in, int out,
+                          int sk, const double *hb, const double *dhb, double *xb, double *dxb, double *gW,
+                          double *gb)
+{
+    for (int q = 0; q < in; ++q) { xb[q] = 0.0; dxb[q] = 0.0; }
+    for (int o = 0; o < out; ++o) {
+        /* recompute dz = dx . W[:, o] */
+        double dz = 0.0;
+        for (int q = 0; q < in; ++q) dz += dx[q] * W[(size_t)q * out + o];
+        const double tt = t[o], one = 1.0 - tt * tt;
+        double tb = hb[o];
+        const double dtb = dhb[o];
+        const double dzb = one * dtb;
+        tb += -2.0 * tt * dz * dtb;
+        const double zb = one * tb;
+        for (int q = 0; q < in; ++q) {
+            gW[(size_t)q * out + o] += x[q] * zb + dx[q] * dzb;
+            xb[q] += zb * W[(size_t)q * out + o];
+            dxb[q] += dzb * W[(size_t)q * out + o];
+        }
+        gb[o] += zb;
+        if (sk == 2) { xb[o % in] += hb[o]; dxb[o % in] += dhb[o]; }
+        else if (sk == 1) { xb[o] += hb[o]; dxb[o] += dhb[o]; }
+    }
+}
+
+static void orc_atom_grad(const orc_model *m, const double *P, int64_t i, const double *x, const int32_t *types,
+                          const double *box, const int32_t *nlist, double cE, const double *lam, orc_gws *w)
+{
+    const int nm = m->nm, ne = m->n_emb, M = m->emb[ne - 1], M2 = m->m2, nf = m->n_fit;
+    int se = 0, mf = 0;
+    for (int l = 0; l < ne; ++l) se += m->emb[l];
+    for (int l = 0; l < nf; ++l) if (m->fit[l] > mf) mf = m->fit[l];
+    const int ai = types[i];
+    const double c = m->desc_scale_nm ? 1.0 / nm : 1.0;
+    double *g = w->g;
+
+    /* rows of the environment matrix, their Jacobians and tangents (Algorithm 2) */
+    for (int k = 0; k < nm; ++k) {
+        w->real[k] = 0;
+        int j = nlist[i * nm + k];
+        if (j < 0) continue;
+        double d[3];
+        orc_min_image(box, x + 3 * i, x + 3 * j, d);
+        double r = orc_norm(d), s, ds;
+        orc_switch(r, m->rcut_smth, m->rcut, &s, &ds);
+        if (s == 0.0) continue;
+        w->real[k] = 1;
+        double u[3] = {d[0] / r, d[1] / r, d[2] / r};
+        double *R = w->R + 4 * k, *J = w->J + 12 * k;
+        R[0] = s; R[1] = s * u[0]; R[2] = s * u[1]; R[3] = s * u[2];
+        for (int b = 0; b < 3; ++b) {
+            J[b] = ds * u[b];
+            for (int a = 0; a < 3; ++a)
+                J[3 * (1 + a) + b] = ds * u[a] * u[b] + s * ((a == b ? 1.0 : 0.0) - u[a] * u[b]) / r;
+        }
+        double dr[3];
+        for (int b = 0; b < 3; ++b) dr[b] = lam[3 * (int64_t)j + b] - lam[3 * i + b];
+        for (int cc = 0; cc < 4; ++cc) {
+            double acc = 0.0;
+            for (int b = 0; b < 3; ++b) acc += J[3 * cc + b] * dr[b];
+            w->dR[4 * k + cc] = acc;
+        }
+        w->s[k] = s;
+        w->ds[k] = w->dR[4 * k];
+    }
+    /* embedding: primal and tangent */
+    for (int k = 0; k < nm; ++k) {
+        if (!w->real[k]) continue;
+        int aj = types[nlist[i * nm + k]];
+        double *h = w->h + (size_t)k * se, *t = w->t + (size_t)k * se, *dh = w->dh + (size_t)k * se;
+        const double *W0 = P + m->emb_W[ai][aj][0], *b0 = P + m->emb_b[ai][aj][0];
+        for (int o = 0; o < m->emb[0]; ++o) {
+            t[o] = tanh(w->s[k] * W0[o] + b0[o]);
+            h[o] = t[o];
+            dh[o] = (1.0 - t[o] * t[o]) * (w->ds[k] * W0[o]);
+        }
+        int in_off = 0;
+        for (int l = 1; l < ne; ++l) {
+            int in = m->emb[l - 1], out = m->emb[l], out_off = in_off + in;
+            const double *Wl = P + m->emb_W[ai][aj][l], *bl = P + m->emb_b[ai][aj][l];
+            int sk = orc_skip_kind(in, out);
+            for (int o = 0; o < out; ++o) {
+                double z = bl[o], dz = 0.0;
+                for (int q = 0; q < in; ++q) {
+                    z += h[in_off + q] * Wl[q * out + o];
+                    dz += dh[in_off + q] * Wl[q * out + o];
+                }
+                t[out_off + o] = tanh(z);
+                double skip = sk == 2 ? h[in_off + (o % in)] : (sk == 1 ? h[in_off + o] : 0.0);
+                double dskip = sk == 2 ? dh[in_off + (o % in)] : (sk == 1 ? dh[in_off + o] : 0.0);
+                h[out_off + o] = skip + t[out_off + o];
+                dh[out_off + o] = dskip + (1.0 - t[out_off + o] * t[out_off + o]) * dz;
+            }
+            in_off = out_off;
+        }
+    }
+    const int g_off = se - M;
+    /* descriptor and its tangent (Eq. descrpt) */
+    for (int cc = 0; cc < 4; ++cc)
+        for (int mm = 0; mm < M; ++mm) {
+            double acc = 0.0, dacc = 0.0;
+            for (int k = 0; k < nm; ++k) {
+                if (!w->real[k]) continue;
+                const double G = w->h[(size_t)k * se + g_off + mm], dG = w->dh[(size_t)k * se + g_off + mm];
+                acc += w->R[4 * k + cc] * G;
+                dacc += w->dR[4 * k + cc] * G + w->R[4 * k + cc] * dG;
+            }
+            w->T[cc * M + mm] = c * acc;
+            w->dT[cc * M + mm] = c * dacc;
+        }
+    for (int a = 0; a < M2; ++a)
+        for (int b = 0; b < M; ++b) {
+            double acc = 0.0, dacc = 0.0;
+            for (int cc = 0; cc < 4; ++cc) {
+                acc += w->T[cc * M + a] * w->T[cc * M + b];
+                dacc += w->dT[cc * M + a] * w->T[cc * M + b] + w->T[cc * M + a] * w->dT[cc * M + b];
+            }
+            w->D[a * M + b] = acc;
+            w->dD[a * M + b] = dacc;
+        }
+    /* fitting net: primal and tangent */
+    const double *xin = w->D, *dxin = w->dD;
+    int in = M2 * M;
+    for (int l = 0; l < nf; ++l) {
+        int out = m->fit[l];
+        const double *W = P + m->fit_W[ai][l], *b = P + m->fit_b[ai][l];
+        int sk = orc_skip_kind(in, out);
+        double *th = w->ft + (size_t)l * mf, *hh = w->fh + (size_t)l * mf, *dhh = w->fdh + (size_t)l * mf;
+        for (int o = 0; o < out; ++o) {
+            double z = b[o], dz = 0.0;
+            for (int q = 0; q < in; ++q) {
+                z += xin[q] * W[(size_t)q * out + o];
+                dz += dxin[q] * W[(size_t)q * out + o];
+            }
+            th[o] = tanh(z);
+            double skip = sk == 2 ? xin[o % in] : (sk == 1 ? xin[o] : 0.0);
+            double dskip = sk == 2 ? dxin[o % in] : (sk == 1 ? dxin[o] : 0.0);
+            hh[o] = skip + th[o];
+            dhh[o] = dskip + (1.0 - th[o] * th[o]) * dz;
+        }
+        xin = hh;
+        dxin = dhh;
+        in = out;
+    }
+    /* reverse: Phi_i = cE E_i - dE_i,  E_i = h_L . wo + bo,  dE_i = dh_L . wo */
+    {
+        const double *wo = P + m->fit_wo[ai];
+        double *gwo = g + m->fit_wo[ai];
+        for (int q = 0; q < in; ++q) {
+            gwo[q] += cE * xin[q] - dxin[q];
+            w->a0[q] = cE * wo[q];
+            w->b0[q] = -wo[q];
+        }
+        g[m->fit_bo[ai]] += cE;
+    }
+    double *hb = w->a0, *dhb = w->b0, *xb = w->a1, *dxb = w->b1;
+    for (int l = nf - 1; l >= 0; --l) {
+        int out = m->fit[l], lin = l == 0 ? M2 * M : m->fit[l - 1];
+        const double *xl = l == 0 ? w->D : w->fh + (size_t)(l - 1) * mf;
+        const double *dxl = l == 0 ? w->dD : w->fdh + (size_t)(l - 1) * mf;
+        orc_layer_rev(xl, dxl, w->ft + (size_t)l * mf, P + m->fit_W[ai][l], lin, out, orc_skip_kind(lin, out),
+                      hb, dhb, xb, dxb, g + m->fit_W[ai][l], g + m->fit_b[ai][l]);
+        double *t1 = hb; hb = xb; xb = t1;
+        double *t2 = dhb; dhb = dxb; dxb = t2;
+    }
+    memcpy(w->Db, hb, sizeof(double) * M2 * M);
+    memcpy(w->dDb, dhb, sizeof(double) * M2 * M);
+    /* descriptor reverse: D = T_<^T T, dD = dT_<^T T + T_<^T dT */
+    for (int cc = 0; cc < 4; ++cc)
+        for (int xx = 0; xx < M; ++xx) {
+            double tb = 0.0, dtb = 0.0;
+            if (xx < M2)
+                for (int b = 0; b < M; ++b) {
+                    tb += w->Db[xx * M + b] * w->T[cc * M + b] + w->dDb[xx * M + b] * w->dT[cc * M + b];
+                    dtb += w->dDb[xx * M + b] * w->T[cc * M + b];
+                }
+            for (int a = 0; a < M2; ++a) {
+                tb += w->Db[a * M + xx] * w->T[cc * M + a] + w->dDb[a * M + xx] * w->dT[cc * M + a];
+                dtb += w->dDb[a * M + xx] * w->T[cc * M + a];
+            }
+            w->Tb[cc * M + xx] = tb;
+            w->dTb[cc * M + xx] = dtb;
+        }
+    /* per row: Gb = c (R Tb + dR dTb), dGb = c R dTb, then back through the embedding */
+    for (int k = 0; k < nm; ++k) {
+        if (!w->real[k]) continue;
+        int aj = types[nlist[i * nm + k]];
+        const double *h = w->h + (size_t)k * se, *t = w->t + (size_t)k * se, *dh = w->dh + (size_t)k * se;
+        double *Gb = w->a0, *dGb = w->b0;
+        for (int mm = 0; mm < M; ++mm) {
+            double acc = 0.0, dacc = 0.0;
+            for (int cc = 0; cc < 4; ++cc) {
+                acc += w->R[4 * k + cc] * w->Tb[cc * M + mm] + w->dR[4 * k + cc] * w->dTb[cc * M + mm];
+                dacc += w->R[4 * k + cc] * w->dTb[cc * M + mm];
+            }
+            Gb[mm] = c * acc;
+            dGb[mm] = c * dacc;
+        }
+        double *ob = w->a0, *dob = w->b0, *ib = w->a1, *dib = w->b1;
+        int out_off = se - M;
+        for (int l = ne - 1; l >= 1; --l) {
+            int out = m->emb[l], lin = m->emb[l - 1], in_off = out_off - lin;
+            orc_layer_rev(h + in_off, dh + in_off, t + out_off, P + m->emb_W[ai][aj][l], lin, out,
+                          orc_skip_kind(lin, out), ob, dob, ib, dib, g + m->emb_W[ai][aj][l],
+                          g + m->emb_b[ai][aj][l]);
+            double *t1 = ob; ob = ib; ib = t1;
+            double *t2 = dob; dob = dib; dib = t2;
+            out_off = in_off;
+        }
+        /* layer 0: h0 = tanh(s W0 + b0), dh0 = (1 - t0^2) ds W0 */
+        const double *W0 = P + m->emb_W[ai][aj][0];
+        double *gW0 = g + m->emb_W[ai][aj][0], *gb0 = g + m->emb_b[ai][aj][0];
+        for (int o = 0; o < m->emb[0]; ++o) {
+            const double tt = t[o], one = 1.0 - tt * tt, dz = w->ds[k] * W0[o];
+            double tb = ob[o];
+            const double dzb = one * dob[o];
+            tb += -2.0 * tt * dz * dob[o];
+            const double zb = one * tb;
+            gW0[o] += w->s[k] * zb + w->ds[k] * dzb;
+            gb0[o] += zb;
+        }
+    }
+}
+
+int orc_param_grad(const int32_t *idesc, const double *ddesc, const double *params, int64_t N, const double *x,
+                   const int32_t *types, const double *box, const int32_t *nlist, double cE, const double *lam,
+                   double *grad)
+{
+    orc_model m;
+    if (orc_parse(idesc, ddesc, &m)) return -1;
+    int nth = 1;
+#ifdef _OPENMP
+    nth = omp_get_max_threads();
+#endif
+    double *parts = calloc((size_t)nth * m.nparams, sizeof(double));
+    if (!parts) return -2;
+#pragma omp parallel
+    {
+        int tid = 0;
+#ifdef _OPENMP
+        tid = omp_get_thread_num();
+#endif
+        orc_gws w;
+        orc_gws_alloc(&m, &w);
+#pragma omp for schedule(static)
+        for (int64_t i = 0; i < N; ++i) orc_atom_grad(&m, params, i, x, types, box, nlist, cE, lam, &w);
+        memcpy(parts + (size_t)tid * m.nparams, w.g, sizeof(double) * m.nparams);
+        orc_gws_free(&w);
+    }
+    for (long q = 0; q < m.nparams; ++q) {
+        double acc = 0.0;
+        for (int th = 0; th < nth; ++th) acc += parts[(size_t)th * m.nparams + q];
+        grad[q] = acc;
+    }
+    free(parts);
+    return 0;
+}

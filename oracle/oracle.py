@@ -56,6 +56,7 @@ def lib():
                                  _d, _i32, _d]
             L.orc_md.restype = ctypes.c_int64
             L.orc_num_threads.restype = ctypes.c_int
+            L.orc_param_grad.argtypes = [_i32, _d, _d, ctypes.c_int64, _d, _i32, _d, _i32, ctypes.c_double, _d, _d]
             _lib = L
     return _lib
 
@@ -186,3 +187,25 @@ def md(desc, params, coords, vel, types, box, masses, dt, nsteps, rebuild_every=
     if st < 0:
         raise RuntimeError(f"orc_md failed: {st}")
     return x, v, F, thermo, int(st)
+
+
+def param_grad(desc, params, coords, types, box, cE, lam, skin=0.0, cap=None):
+    """d/dW of cE * E + sum_i lam_i . F_i (the parameter gradient of any loss
+    on E and F with dLoss/dE = cE, dLoss/dF = lam), on the formatted list."""
+    i, d = _desc_arrays(desc)
+    x = np.ascontiguousarray(coords, dtype=np.float64)
+    t = np.ascontiguousarray(types, dtype=np.int32)
+    b = np.ascontiguousarray(box, dtype=np.float64)
+    P = np.ascontiguousarray(params, dtype=np.float64)
+    N = len(x)
+    if cap is None:
+        cap = default_cap(desc, box, N, skin)
+    ncand, cand, over = candidates(x, b, desc["rcut"] + skin, cap)
+    nlist, _, _ = format_nlist(x, t, b, ncand, cand, desc["sel"], desc["rcut"])
+    lam = np.ascontiguousarray(lam, dtype=np.float64)
+    g = np.zeros(len(P))
+    rc = lib().orc_param_grad(_p(i, _i32), _p(d, _d), _p(P, _d), N, _p(x, _d), _p(t, _i32), _p(b, _d),
+                              _p(nlist, _i32), float(cE), _p(lam, _d), _p(g, _d))
+    if rc != 0:
+        raise RuntimeError(f"orc_param_grad failed: {rc}")
+    return g

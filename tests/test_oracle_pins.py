@@ -450,3 +450,60 @@ def test_md_time_reversible(oracle, synth):
     d -= w["box"] * np.round(d / w["box"])
     assert np.abs(d).max() < 1e-9
     np.testing.assert_allclose(-v2, v0, atol=1e-10)
+
+
+# ------------------------------------------------------- parameter gradient --
+
+def _phi(oracle, desc, P, w, cE, lam):
+    o = oracle.evaluate(desc, P, w["coords"], w["types"], w["box"])
+    return cE * o["energy"] + float((lam * o["force"]).sum())
+
+
+@pytest.mark.parametrize("cE,fw", [(1.0, 0.0), (0.0, 1.0), (0.7, 30.0)])
+def test_param_grad_directional_fd(oracle, synth, cE, fw):
+    """d/dW of cE E + sum lambda . F against Richardson-extrapolated central
+    differences along random directions in parameter space (the force term
+    differentiates through F = -grad E: a second derivative)."""
+    w = synth.workload("water192")
+    desc = w["model"]
+    P = synth.model_params(desc, 0)
+    rng = np.random.default_rng(31)
+    lam = fw * rng.standard_normal((len(w["coords"]), 3))
+    g = oracle.param_grad(desc, P, w["coords"], w["types"], w["box"], cE, lam)
+    for trial in range(2):
+        V = rng.standard_normal(len(P))
+        V /= np.linalg.norm(V)
+        def fd(h):
+            return (_phi(oracle, desc, P + h * V, w, cE, lam) - _phi(oracle, desc, P - h * V, w, cE, lam)) / (2 * h)
+        d1, d2 = fd(2e-4), fd(1e-4)
+        rich = (4 * d2 - d1) / 3
+        assert rich == pytest.approx(float(g @ V), rel=1e-6, abs=1e-9 * (abs(cE) + fw))
+
+
+def test_param_grad_single_parameters(oracle, synth):
+    """Central differences on single parameters of every kind: embedding W0,
+    b0, inner W and b of both neighbour types, fitting W1, hidden W, w_out,
+    b_out."""
+    w = synth.workload("water192")
+    desc = w["model"]
+    P = synth.model_params(desc, 0)
+    rng = np.random.default_rng(32)
+    lam = 20.0 * rng.standard_normal((len(w["coords"]), 3))
+    cE = 0.3
+    g = oracle.param_grad(desc, P, w["coords"], w["types"], w["box"], cE, lam)
+    offs, off = {}, 0
+    for name, shape in synth.layer_shapes(desc):
+        offs[name] = off
+        off += int(np.prod(shape))
+    picks = [offs["emb00.W0"] + 3, offs["emb01.b0"] + 7, offs["emb10.W1"] + 111, offs["emb11.b2"] + 42,
+             offs["emb01.W2"] + 2500, offs["fit0.W1"] + 5000, offs["fit1.W2"] + 777, offs["fit0.wo"] + 5,
+             offs["fit1.bo"], offs["fit1.b3"] + 9]
+    for p in picks:
+        def fd(h):
+            Pp, Pm = P.copy(), P.copy()
+            Pp[p] += h
+            Pm[p] -= h
+            return (_phi(oracle, desc, Pp, w, cE, lam) - _phi(oracle, desc, Pm, w, cE, lam)) / (2 * h)
+        d1, d2 = fd(2e-4), fd(1e-4)
+        rich = (4 * d2 - d1) / 3
+        assert rich == pytest.approx(g[p], rel=1e-5, abs=1e-8 * max(1.0, np.abs(g).max()))

@@ -226,6 +226,26 @@ dp_status dp_md_step(dp_ctx *ctx, double *coords, double *vel, const int32_t *ty
                      const double box[9], const double *mass_per_type, int64_t N,
                      double dt_fs, int32_t nsteps, int32_t rebuild_every, double skin,
                      double *thermo);
+/* Parameter gradient for training (the paper trains the model by
+ * back-propagation; forces are -grad E, Remark 2):
+ *     grad = d/dW [ cE * E(W) + sum_i lambda_i . F_i(W) ],
+ * i.e. the gradient of any loss L(E, F) with cE = dL/dE and lambda = dL/dF,
+ * at the current coordinates.  The force term is a mixed second derivative,
+ * evaluated as forward tangents of the environment matrix, embedding,
+ * descriptor and fitting nets along the neighbour displacements
+ * lambda_j - lambda_i followed by reverse mode; G is recomputed, never
+ * stored.  lambda: device [N][3]; grad: device [nparams] (flat layout of
+ * dp_model_nparams), overwritten.  FP64 contexts only (DP_ERR_UNSUPPORTED
+ * otherwise).  Reproducible bit for bit.  Scratch of about
+ * num_SMs * nparams doubles plus ~30 KB per atom is allocated on the first
+ * call. */
+dp_status dp_param_grad(dp_ctx *ctx, const double *coords, const int32_t *types, const double box[9],
+                        int64_t N, double cE, const double *lambda, double *grad);
+/* Replace the parameters of a model (host array, nparams doubles).  Contexts
+ * made from the model see the new values on their next call; mixed-precision
+ * contexts keep the BF16 copies made at their creation and must be recreated. */
+dp_status dp_model_set_params(dp_model *model, const double *params, int64_t nparams);
+
 /* Copy the context's MD force ([N][3]) to a device buffer. */
 dp_status dp_md_get_force(dp_ctx *ctx, double *force, int64_t N);
 /* Forget the MD force and step counter (next dp_md_step recomputes both). */

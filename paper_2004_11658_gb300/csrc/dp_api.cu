@@ -131,6 +131,8 @@ struct dp_ctx {
     // MD state
     double *md_force, *ke_part, *d_inv_mass_conv, *d_mass, *h_mass_stage;
     double last_mass[DP_MAX_TYPES];
+    // parameter gradient scratch (allocated on first use)
+    PGradBuffers pb;
     // mixed precision: BF16 / FP32 copies of the parameters
     MixedModel mx;
     float *d_p32;
@@ -688,7 +690,8 @@ void dp_ctx_free(dp_ctx *c)
                     c->nb.type_perm, c->nb.type_start, c->fb.nlist, c->fb.keys, c->fb.nreal,
                     c->eb.T, c->eb.D, c->eb.gD, c->eb.Ei, c->eb.pair_g, c->eb.f_own, c->eb.vir_part,
                     c->d_energy, c->d_virial, c->md_force, c->ke_part, c->d_inv_mass_conv, c->d_mass,
-                    c->eb.fit_t, c->eb.fit_h, c->d_p32, c->d_emb_ops, c->d_fit_fwd, c->d_fit_bwd};
+                    c->eb.fit_t, c->eb.fit_h, c->d_p32, c->d_emb_ops, c->d_fit_fwd, c->d_fit_bwd,
+                    c->pb.dT, c->pb.dD, c->pb.Db, c->pb.dDb, c->pb.fit_scr, c->pb.rowscr, c->pb.slices};
     for (void *p : bufs) dev_free(p);
     delete c;
 }
@@ -956,6 +959,53 @@ dp_status dp_md_step(dp_ctx *c, double *coords, double *vel, const int32_t *type
         }
         if (e != cudaSuccess) return cuda_fail(e, "kick_thermo");
     }
+    return finish(c);
+}
+
+dp_status dp_model_set_params(dp_model *md, const double *params, int64_t nparams)
+{
+    if (!md || !params) return fail(DP_ERR_ARG, "model/params is NULL");
+    if (nparams != md->nparams) return fail(DP_ERR_ARG, "nparams does not match the model");
+    for (int64_t q = 0; q < nparams; ++q)
+        if (!std::isfinite(params[q])) return fail(DP_ERR_ARG, "non-finite parameter");
+    std::memcpy(md->h_params, params, sizeof(double) * nparams);
+    DP_CUDA(cudaMemcpy(md->d_params, params, sizeof(double) * nparams, cudaMemcpyHostToDevice), "dp_model_set_params");
+    return DP_OK;
+}
+
+dp_status dp_param_grad(dp_ctx *c, const double *coords, const int32_t *types, const double box[9], int64_t N,
+                        double cE, const double *lambda, double *grad)
+{
+    dp_status s = check_common(c, coords, types, N);
+    if (s) return s;
+    if (!lambda || !grad) return fail(DP_ERR_ARG, "lambda/grad is NULL");
+    if (c->precision != DP_PREC_FP64) return fail(DP_ERR_UNSUPPORTED, "parameter gradients need an FP64 context");
+    for (int l = 1; l < c->m.n_fit; ++l)
+        if (dp_skip_kind(c->m.fit[l - 1], c->m.fit[l]) == 2)
+            return fail(DP_ERR_UNSUPPORTED, "parameter gradients support equal-width fitting skips only");
+    Box3 b;
+    if ((s = read_box(box, b))) return s;
+    if (!c->nlist_valid || c->nlist_N != N)
+        if ((s = do_build(c, coords, types, b, N, 0.0))) return s;
+    const int64_t np = c->model->nparams;
+    const size_t Nmax = (size_t)c->natoms_max, M = (size_t)c->m.M, nd = (size_t)c->m.m2 * M;
+    if (!c->pb.slices) {
+#define ALLOCP(ptr, n) \
+    if (!s) s = dev_alloc(&(ptr), (n), #ptr)
+        ALLOCP(c->pb.dT, Nmax * 4 * M);
+        ALLOCP(c->pb.dD, Nmax * nd);
+        ALLOCP(c->pb.Db, Nmax * nd);
+        ALLOCP(c->pb.dDb, Nmax * nd);
+        ALLOCP(c->pb.fit_scr, dp_pgrad_fit_scratch((int)Nmax));
+        ALLOCP(c->pb.rowscr, dp_pgrad_row_scratch(c->num_sms));
+        ALLOCP(c->pb.slices, (size_t)c->num_sms * np);
+#undef ALLOCP
+        if (s) return s;
+    }
+    if ((s = enqueue_format(c, coords, types, b, N))) return s;
+    cudaError_t e = dp_launch_pgrad(c->stream, c->m, np, coords, types, b, (int)N, lambda, cE, c->fb, c->nb, c->eb,
+                                    c->pb, c->num_sms, grad, &c->launches);
+    if (e != cudaSuccess) return cuda_fail(e, "dp_param_grad");
     return finish(c);
 }
 

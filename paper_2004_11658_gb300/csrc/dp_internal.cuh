@@ -226,6 +226,22 @@ cudaError_t dp_launch_embed_bwd_mx(cudaStream_t st, const DevModel &m, const Mix
 // true if the mixed-precision kernels support this model shape
 bool dp_mixed_supported(const DevModel &m);
 
+// Parameter gradient of cE E + sum lambda . F (pgrad.cu).
+struct PGradBuffers {
+    double *dT;       // [N][4][M] tangent of T
+    double *dD;       // [N][m2*M]
+    double *Db, *dDb; // [N][m2*M] adjoints of D and dD
+    double *fit_scr;  // dp_pgrad_fit_scratch(N) doubles
+    double *rowscr;   // dp_pgrad_row_scratch(num_sms) doubles
+    double *slices;   // [num_sms][nparams] per-CTA gradient partials
+};
+size_t dp_pgrad_fit_scratch(int N);
+size_t dp_pgrad_row_scratch(int num_sms);
+cudaError_t dp_launch_pgrad(cudaStream_t st, const DevModel &m, int64_t nparams, const double *x, const int32_t *types,
+                            Box3 box, int N, const double *lam, double cE, const FormatBuffers &fb,
+                            const NlistBuffers &nb, EvalBuffers eb, PGradBuffers pb, int num_sms, double *grad,
+                            int64_t *launches);
+
 // MD integrator kernels.
 cudaError_t dp_launch_kick_drift(cudaStream_t st, int N, double *x, double *v, const double *f,
                                  const int32_t *types, const double *inv_mass_conv, double dt,

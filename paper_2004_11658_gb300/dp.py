@@ -95,6 +95,10 @@ def lib():
             L.dp_ctx_kernel_times.argtypes = [_vp, _vp, _vp]
             L.dp_kernel_group_name.restype = ctypes.c_char_p
             L.dp_kernel_group_name.argtypes = [_i32]
+            L.dp_param_grad.restype = _i32
+            L.dp_param_grad.argtypes = [_vp, _vp, _vp, _vp, _i64, _dbl, _vp, _vp]
+            L.dp_model_set_params.restype = _i32
+            L.dp_model_set_params.argtypes = [_vp, _vp, _i64]
             L.dp_tanh_f64.restype = _i32
             L.dp_tanh_f64.argtypes = [_vp, _vp, _i64, _vp]
             L.dp_format_nlist_noalloc.restype = _i32
@@ -178,6 +182,10 @@ class Model:
 
     def save(self, path):
         _check(lib().dp_model_save(self._h, os.fsencode(path)))
+
+    def set_params(self, params):
+        p = np.ascontiguousarray(params, dtype=np.float64)
+        _check(lib().dp_model_set_params(self._h, p.ctypes.data_as(_vp), len(p)))
 
     @property
     def handle(self):
@@ -269,6 +277,19 @@ def dp_format_nlist(ctx, coords, types, box, check=True):
     return nlist, nreal, s
 
 
+def dp_param_grad(ctx, coords, types, box, cE, lam, grad=None):
+    """d/dW of cE * E + sum_i lam_i . F_i (device tensor [nparams])."""
+    N = coords.shape[0]
+    if grad is None:
+        grad = torch.empty(dp_model_nparams(ctx.model.desc), dtype=torch.float64, device=coords.device)
+    b = _box9(box)
+    lam = lam.contiguous()
+    _check(lib().dp_param_grad(ctx.handle, _dev(coords, torch.float64, (N, 3), "coords"),
+                               _dev(types, torch.int32, (N,), "types"), b.ctypes.data_as(_vp), N, float(cE),
+                               _dev(lam, torch.float64, (N, 3), "lambda"), _dev(grad, torch.float64, None, "grad")))
+    return grad
+
+
 def dp_tanh_f64(x, stream=None):
     """The library's FP64 tanh (used by the FP64 kernels) on a CUDA tensor."""
     y = torch.empty_like(x)
@@ -350,3 +371,35 @@ def dp_md_get_force(ctx, N, device="cuda"):
 
 def dp_md_reset(ctx):
     _check(lib().dp_md_reset(ctx.handle))
+
+
+class DPEnergyForces(torch.autograd.Function):
+    """(E, F, virial) of a model as a differentiable function of its flat
+    parameter vector.  Forward: dp_eval.  Backward: dp_param_grad with
+    cE = dL/dE and lambda = dL/dF, so any loss on the energy and forces
+    trains the model through the hand-written kernels.  A gradient flowing
+    into the virial output is not supported (raises).
+
+    Usage:  E, F, V = DPEnergyForces.apply(params, coords, types, box, ctx)
+    where params is a float64 tensor (any device) of dp_model_nparams values
+    and ctx a FP64 Context of the model whose parameters are trained."""
+
+    @staticmethod
+    def forward(fctx, params, coords, types, box, dpctx):
+        dpctx.model.set_params(params.detach().to("cpu", torch.float64).numpy())
+        out = dp_eval(dpctx, coords, types, box)
+        fctx.dpctx = dpctx
+        fctx.box = box
+        fctx.save_for_backward(coords, types)
+        fctx.params_device = params.device
+        return out["energy"].clone(), out["force"].clone(), out["virial"].clone()
+
+    @staticmethod
+    def backward(fctx, gE, gF, gV):
+        coords, types = fctx.saved_tensors
+        if gV is not None and bool(torch.any(gV != 0)):
+            raise NotImplementedError("gradients through the virial are not supported")
+        cE = float(gE.sum().item()) if gE is not None else 0.0
+        lam = gF.contiguous().to(torch.float64) if gF is not None else torch.zeros_like(coords)
+        grad = dp_param_grad(fctx.dpctx, coords, types, fctx.box, cE, lam)
+        return grad.to(fctx.params_device), None, None, None, None

@@ -210,6 +210,24 @@ dp_status dp_eval(dp_ctx *ctx, const double *coords, const int32_t *types, const
                   int64_t N, double *energy, double *force, double *virial,
                   double *atom_energy);
 
+/* Sub-region evaluation for spatial domain decomposition (Sec. 3.1 and
+ * Remark 4).  Atoms [0, nloc) are the centres (the atoms a process owns);
+ * atoms [nloc, N) are ghost atoms, copies of other processes' atoms within
+ * the ghost width of the sub-region, that enter only as neighbours.
+ * energy: sum of E_i over the centres; virial: -sum over the centres i of
+ * r_ij[a] dE_i/dr_ij[b]; force: device [N][3], for the centres the sum of
+ * all increments of the centres, for a ghost the increments -dE_i/dr_j of
+ * the centres i (which its owner adds to the atom's force: the reverse halo
+ * exchange); atom_energy: device [nloc] or NULL.  Summed over the
+ * sub-regions of a partition these equal dp_eval of the whole system.  The
+ * cell is periodic as given: a non-periodic edge of a sub-region is padded by
+ * the caller (edge >= sub-region + 2 ghost widths + rcut + skin).  nloc == N
+ * is dp_eval; nloc == 0 gives zero energy and forces.  DP_ERR_ARG unless
+ * 0 <= nloc <= N. */
+dp_status dp_eval_local(dp_ctx *ctx, const double *coords, const int32_t *types, const double box[9],
+                        int64_t N, int64_t nloc, double *energy, double *force, double *virial,
+                        double *atom_energy);
+
 /* nsteps of velocity-Verlet NVE (Sec. 4): v += F/m dt/2; x += v dt; wrap
  * into the cell; rebuild the candidates when the context's MD step counter
  * is a multiple of rebuild_every (and at the first step of a context), and

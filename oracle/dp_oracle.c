@@ -520,18 +520,23 @@ static double orc_atom(const orc_model *m, const double *P, int64_t i, const dou
     return Ei;
 }
 
-/* Energy, forces and virial for a formatted neighbour list (nlist[N][N_m]).
+/* Energy, forces and virial of the centres 0..nloc-1 for a formatted
+ * neighbour list (nlist[nloc][N_m]); atoms nloc..N-1 are only neighbours (the
+ * ghost atoms of a sub-region, Sec. 3.1).
  * F_i += dE_i/dr_ij, F_j -= dE_i/dr_ij (Remark 2 and Remark 4: the j-side
- * terms are kept, there is no Newton-3 shortcut); virial
- * Xi[a][b] = -sum r_ij[a] dE_i/dr_ij[b], row-major 3x3.  Any output pointer
+ * terms are kept, there is no Newton-3 shortcut), so ghost atoms receive the
+ * force increments that Sec. 3.1 sends back to their owners; virial
+ * Xi[a][b] = -sum r_ij[a] dE_i/dr_ij[b] over the centres, row-major 3x3;
+ * E and atom_energy over the centres.  force is [N][3].  Any output pointer
  * may be NULL except energy. */
-int orc_eval(const int32_t *idesc, const double *ddesc, const double *params, int64_t N,
-             const double *x, const int32_t *types, const double *box, const int32_t *nlist,
-             double *energy, double *force, double *virial, double *atom_energy,
-             double *descriptor)
+int orc_eval_local(const int32_t *idesc, const double *ddesc, const double *params, int64_t N, int64_t nloc,
+                   const double *x, const int32_t *types, const double *box, const int32_t *nlist,
+                   double *energy, double *force, double *virial, double *atom_energy,
+                   double *descriptor)
 {
     orc_model m;
     if (orc_parse(idesc, ddesc, &m)) return -1;
+    if (nloc < 0 || nloc > N) return -1;
     const int nm = m.nm;
     double *Ei = (double *)malloc(sizeof(double) * (size_t)(N > 0 ? N : 1));
     double *g = (double *)malloc(sizeof(double) * (size_t)(N > 0 ? N : 1) * nm * 3);
@@ -541,18 +546,18 @@ int orc_eval(const int32_t *idesc, const double *ddesc, const double *params, in
         orc_ws w;
         orc_ws_alloc(&m, &w);
 #pragma omp for schedule(dynamic, 4)
-        for (int64_t i = 0; i < N; ++i)
+        for (int64_t i = 0; i < nloc; ++i)
             Ei[i] = orc_atom(&m, params, i, x, types, box, nlist, &w, g + (size_t)i * nm * 3,
                              descriptor);
         orc_ws_free(&w);
     }
     double E = 0.0;
-    for (int64_t i = 0; i < N; ++i) E += Ei[i];
+    for (int64_t i = 0; i < nloc; ++i) E += Ei[i];
     *energy = E;
-    if (atom_energy) memcpy(atom_energy, Ei, sizeof(double) * (size_t)N);
+    if (atom_energy) memcpy(atom_energy, Ei, sizeof(double) * (size_t)nloc);
     if (force) for (int64_t q = 0; q < 3 * N; ++q) force[q] = 0.0;
     double V[9] = {0};
-    for (int64_t i = 0; i < N; ++i)
+    for (int64_t i = 0; i < nloc; ++i)
         for (int k = 0; k < nm; ++k) {
             int j = nlist[i * nm + k];
             if (j < 0) continue;
@@ -572,6 +577,16 @@ int orc_eval(const int32_t *idesc, const double *ddesc, const double *params, in
     free(Ei);
     free(g);
     return 0;
+}
+
+/* All N atoms are centres (a whole periodic system). */
+int orc_eval(const int32_t *idesc, const double *ddesc, const double *params, int64_t N,
+             const double *x, const int32_t *types, const double *box, const int32_t *nlist,
+             double *energy, double *force, double *virial, double *atom_energy,
+             double *descriptor)
+{
+    return orc_eval_local(idesc, ddesc, params, N, N, x, types, box, nlist, energy, force, virial, atom_energy,
+                          descriptor);
 }
 
 /* ---------------------------------------------------------------------- MD */

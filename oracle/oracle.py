@@ -51,6 +51,8 @@ def lib():
             L.orc_format.argtypes = [ctypes.c_int64, _d, _i32, _d, _i32, _i32, ctypes.c_int32,
                                      ctypes.c_int32, _i32, ctypes.c_double, _i32, _i32, _i64]
             L.orc_eval.argtypes = [_i32, _d, _d, ctypes.c_int64, _d, _i32, _d, _i32, _d, _d, _d, _d, _d]
+            L.orc_eval_local.argtypes = [_i32, _d, _d, ctypes.c_int64, ctypes.c_int64, _d, _i32, _d, _i32,
+                                         _d, _d, _d, _d, _d]
             L.orc_md.argtypes = [_i32, _d, _d, ctypes.c_int64, _d, _d, _i32, _d, _d, ctypes.c_double,
                                  ctypes.c_int32, ctypes.c_int32, ctypes.c_double, ctypes.c_int32,
                                  _d, _i32, _d]
@@ -140,6 +142,33 @@ def eval_nlist(desc, params, coords, types, box, nlist, want_descriptor=False):
     if want_descriptor:
         out["descriptor"] = D
     return out
+
+
+def evaluate_local(desc, params, coords, types, box, nloc, cap=None):
+    """Sub-region evaluation (Sec. 3.1): atoms [0, nloc) are the centres,
+    [nloc, N) ghost atoms that only appear as neighbours.  Returns E and the
+    virial of the centres and the force increments on all N atoms."""
+    N = len(coords)
+    if cap is None:
+        cap = default_cap(desc, box, N, 0.0)
+    i, d = _desc_arrays(desc)
+    x = np.ascontiguousarray(coords, dtype=np.float64)
+    t = np.ascontiguousarray(types, dtype=np.int32)
+    b = np.ascontiguousarray(box, dtype=np.float64)
+    P = np.ascontiguousarray(params, dtype=np.float64)
+    ncand, cand, over = candidates(x, b, desc["rcut"], cap)
+    if over:
+        raise RuntimeError("candidate capacity exceeded")
+    nlist, _, _ = format_nlist(x, t, b, ncand, cand, desc["sel"], desc["rcut"])
+    E = np.zeros(1)
+    F = np.zeros((N, 3))
+    V = np.zeros(9)
+    Ei = np.zeros(max(nloc, 1))
+    rc = lib().orc_eval_local(_p(i, _i32), _p(d, _d), _p(P, _d), N, int(nloc), _p(x, _d), _p(t, _i32), _p(b, _d),
+                              _p(nlist, _i32), _p(E, _d), _p(F, _d), _p(V, _d), _p(Ei, _d), None)
+    if rc != 0:
+        raise RuntimeError(f"orc_eval_local failed: {rc}")
+    return dict(energy=float(E[0]), force=F, virial=V.reshape(3, 3), atom_energy=Ei[:nloc])
 
 
 def default_cap(desc, box, N, skin):

@@ -124,6 +124,7 @@ struct dp_ctx {
     int nc[3];
     bool nlist_valid;
     int64_t nlist_N;
+    int64_t perm_n;    // centres covered by nb.type_perm (-1: unknown)
     double skin;
     FormatBuffers fb;
     EvalBuffers eb;
@@ -452,7 +453,21 @@ dp_status do_build(dp_ctx *c, const double *coords, const int32_t *types, const 
     if (e != cudaSuccess) return cuda_fail(e, "dp_build_nlist");
     c->nlist_valid = true;
     c->nlist_N = N;
+    // a gated build may or may not have rebuilt the type partition (over N)
+    if (!gated || c->perm_n != N) c->perm_n = gated ? -1 : N;
     c->skin = skin;
+    return DP_OK;
+}
+
+// The type partition of the centres 0..n-1 (all atoms, or the owned atoms of
+// a sub-region).
+dp_status ensure_perm(dp_ctx *c, const int32_t *types, int64_t n)
+{
+    if (c->perm_n == n) return DP_OK;
+    GroupTimer tm(c, G_BUILD);
+    cudaError_t e = dp_launch_type_perm(c->stream, c->m, types, (int)n, c->nb, c->d_status, &c->launches);
+    if (e != cudaSuccess) return cuda_fail(e, "type partition");
+    c->perm_n = n;
     return DP_OK;
 }
 
@@ -466,43 +481,47 @@ dp_status enqueue_format(dp_ctx *c, const double *coords, const int32_t *types, 
 }
 
 dp_status enqueue_eval(dp_ctx *c, const double *coords, const int32_t *types, const Box3 &b, int64_t N,
-                       double *energy, double *force, double *virial, double *atom_energy)
+                       int64_t nloc, double *energy, double *force, double *virial, double *atom_energy)
 {
-    dp_status s = enqueue_format(c, coords, types, b, N);
+    dp_status s = ensure_perm(c, types, nloc);
     if (s) return s;
     cudaError_t e;
     const bool mixed = c->precision == DP_PREC_MIXED;
-    {
-        GroupTimer tm(c, G_EMBED_FWD);
-        e = mixed ? dp_launch_embed_fwd_mx(c->stream, c->m, c->mx, coords, types, b, (int)N, c->fb, c->nb, c->eb,
-                                           c->num_sms, c->d_status, &c->launches)
-                  : dp_launch_embed_fwd(c->stream, c->m, coords, types, b, (int)N, c->fb, c->nb, c->eb, c->num_sms,
-                                        &c->launches);
-        if (e != cudaSuccess) return cuda_fail(e, "embed_fwd");
-    }
-    {
-        GroupTimer tm(c, G_FIT);
-        e = mixed ? dp_launch_fit_mx(c->stream, c->m, c->mx, (int)N, c->nb, c->eb, c->d_status, &c->launches)
-                  : dp_launch_fit(c->stream, c->m, (int)N, c->nb, c->eb, &c->launches);
-        if (e != cudaSuccess) return cuda_fail(e, "fit");
-    }
-    {
-        GroupTimer tm(c, G_EMBED_BWD);
-        e = mixed ? dp_launch_embed_bwd_mx(c->stream, c->m, c->mx, coords, types, b, (int)N, c->fb, c->nb, c->eb,
-                                           c->num_sms, c->d_status, &c->launches)
-                  : dp_launch_embed_bwd(c->stream, c->m, coords, types, b, (int)N, c->fb, c->nb, c->eb, c->num_sms,
-                                        &c->launches);
-        if (e != cudaSuccess) return cuda_fail(e, "embed_bwd");
+    const int n = (int)nloc;  // the centres
+    if (n > 0) {
+        if ((s = enqueue_format(c, coords, types, b, nloc))) return s;
+        {
+            GroupTimer tm(c, G_EMBED_FWD);
+            e = mixed ? dp_launch_embed_fwd_mx(c->stream, c->m, c->mx, coords, types, b, n, c->fb, c->nb, c->eb,
+                                               c->num_sms, c->d_status, &c->launches)
+                      : dp_launch_embed_fwd(c->stream, c->m, coords, types, b, n, c->fb, c->nb, c->eb, c->num_sms,
+                                            &c->launches);
+            if (e != cudaSuccess) return cuda_fail(e, "embed_fwd");
+        }
+        {
+            GroupTimer tm(c, G_FIT);
+            e = mixed ? dp_launch_fit_mx(c->stream, c->m, c->mx, n, c->nb, c->eb, c->d_status, &c->launches)
+                      : dp_launch_fit(c->stream, c->m, n, c->nb, c->eb, &c->launches);
+            if (e != cudaSuccess) return cuda_fail(e, "fit");
+        }
+        {
+            GroupTimer tm(c, G_EMBED_BWD);
+            e = mixed ? dp_launch_embed_bwd_mx(c->stream, c->m, c->mx, coords, types, b, n, c->fb, c->nb, c->eb,
+                                               c->num_sms, c->d_status, &c->launches)
+                      : dp_launch_embed_bwd(c->stream, c->m, coords, types, b, n, c->fb, c->nb, c->eb, c->num_sms,
+                                            &c->launches);
+            if (e != cudaSuccess) return cuda_fail(e, "embed_bwd");
+        }
     }
     {
         GroupTimer tm(c, G_FORCE);
-        if ((e = dp_launch_force(c->stream, c->m, coords, types, b, (int)N, c->cap, c->nb, c->fb, c->eb, force,
+        if ((e = dp_launch_force(c->stream, c->m, coords, types, b, (int)N, n, c->cap, c->nb, c->fb, c->eb, force,
                                  &c->launches)) != cudaSuccess)
             return cuda_fail(e, "force");
     }
     {
         GroupTimer tm(c, G_REDUCE);
-        if ((e = dp_launch_reduce(c->stream, (int)N, c->eb, energy, virial, atom_energy, c->d_status,
+        if ((e = dp_launch_reduce(c->stream, n, c->eb, energy, virial, atom_energy, c->d_status,
                                   &c->launches)) != cudaSuccess)
             return cuda_fail(e, "reduce");
     }
@@ -716,6 +735,7 @@ dp_status dp_ctx_create(const dp_model *model, int64_t natoms_max, int32_t cand_
     c->natoms_max = natoms_max;
     c->cap_fixed = cand_cap;
     c->cap = 0;
+    c->perm_n = -1;
     c->precision = precision;
     c->stream = (cudaStream_t)stream;
     c->sync = 1;
@@ -890,7 +910,22 @@ dp_status dp_eval(dp_ctx *c, const double *coords, const int32_t *types, const d
     if ((s = read_box(box, b))) return s;
     if (!c->nlist_valid || c->nlist_N != N)
         if ((s = do_build(c, coords, types, b, N, 0.0))) return s;
-    if ((s = enqueue_eval(c, coords, types, b, N, energy, force, virial, atom_energy))) return s;
+    if ((s = enqueue_eval(c, coords, types, b, N, N, energy, force, virial, atom_energy))) return s;
+    return finish(c);
+}
+
+dp_status dp_eval_local(dp_ctx *c, const double *coords, const int32_t *types, const double box[9], int64_t N,
+                        int64_t nloc, double *energy, double *force, double *virial, double *atom_energy)
+{
+    dp_status s = check_common(c, coords, types, N);
+    if (s) return s;
+    if (!energy || !force || !virial) return fail(DP_ERR_ARG, "energy/force/virial is NULL");
+    if (nloc < 0 || nloc > N) return fail(DP_ERR_ARG, "nloc must be in [0, N]");
+    Box3 b;
+    if ((s = read_box(box, b))) return s;
+    if (!c->nlist_valid || c->nlist_N != N)
+        if ((s = do_build(c, coords, types, b, N, 0.0))) return s;
+    if ((s = enqueue_eval(c, coords, types, b, N, nloc, energy, force, virial, atom_energy))) return s;
     return finish(c);
 }
 
@@ -928,7 +963,8 @@ dp_status dp_md_step(dp_ctx *c, double *coords, double *vel, const int32_t *type
     const double vol = b.L[0] * b.L[1] * b.L[2];
     if (!c->md_force_valid || c->md_N != N) {
         if ((s = do_build(c, coords, types, b, N, skin))) return s;
-        if ((s = enqueue_eval(c, coords, types, b, N, c->d_energy, c->md_force, c->d_virial, nullptr))) return s;
+        if ((s = enqueue_eval(c, coords, types, b, N, N, c->d_energy, c->md_force, c->d_virial, nullptr)))
+            return s;
         c->md_force_valid = true;
         c->md_N = N;
         c->md_step = 0;
@@ -948,7 +984,8 @@ dp_status dp_md_step(dp_ctx *c, double *coords, double *vel, const int32_t *type
             // rebuild on the device as soon as an atom has moved more than skin/2
             if ((s = do_build(c, coords, types, b, N, skin, true))) return s;
         }
-        if ((s = enqueue_eval(c, coords, types, b, N, c->d_energy, c->md_force, c->d_virial, nullptr))) return s;
+        if ((s = enqueue_eval(c, coords, types, b, N, N, c->d_energy, c->md_force, c->d_virial, nullptr)))
+            return s;
         {
             GroupTimer tm(c, G_MD);
             e = dp_launch_kick_thermo(c->stream, (int)N, vel, c->md_force, types, c->d_inv_mass_conv, c->d_mass,
@@ -1002,6 +1039,7 @@ dp_status dp_param_grad(dp_ctx *c, const double *coords, const int32_t *types, c
 #undef ALLOCP
         if (s) return s;
     }
+    if ((s = ensure_perm(c, types, N))) return s;
     if ((s = enqueue_format(c, coords, types, b, N))) return s;
     cudaError_t e = dp_launch_pgrad(c->stream, c->m, np, coords, types, b, (int)N, lambda, cE, c->fb, c->nb, c->eb,
                                     c->pb, c->num_sms, grad, &c->launches);

@@ -155,6 +155,10 @@ struct FormatBuffers {
 cudaError_t dp_launch_build(cudaStream_t st, const DevModel &m, const double *x, const int32_t *types,
                             Box3 box, int N, double rlist, int cap, int nc[3], NlistBuffers nb,
                             int32_t *status, int32_t *gate, int64_t *launches);
+// Type partition of the centres 0..n-1 alone (sub-region evaluation: atoms
+// n..N-1 are ghosts); the build computes it for all N atoms.
+cudaError_t dp_launch_type_perm(cudaStream_t st, const DevModel &m, const int32_t *types, int n,
+                                NlistBuffers nb, int32_t *status, int64_t *launches);
 // Sets *gate if an atom moved more than sqrt(stale2) from its reference position.
 cudaError_t dp_launch_check_stale(cudaStream_t st, const double *x, const double *xref, int N, Box3 box,
                                   double stale2, int32_t *gate, int64_t *launches);
@@ -204,8 +208,11 @@ cudaError_t dp_launch_embed_bwd(cudaStream_t st, const DevModel &m, const double
                                 const int32_t *types, Box3 box, int N, const FormatBuffers &fb,
                                 const NlistBuffers &nb, EvalBuffers eb, int num_sms,
                                 int64_t *launches);
+// Forces on all N atoms from the centres 0..nloc-1 (nloc == N: every atom
+// is a centre; nloc < N: atoms nloc..N-1 are ghosts and receive only the
+// increments of the centres).
 cudaError_t dp_launch_force(cudaStream_t st, const DevModel &m, const double *x,
-                            const int32_t *types, Box3 box, int N, int cap,
+                            const int32_t *types, Box3 box, int N, int nloc, int cap,
                             const NlistBuffers &nb, const FormatBuffers &fb, EvalBuffers eb,
                             double *force, int64_t *launches);
 cudaError_t dp_launch_reduce(cudaStream_t st, int N, EvalBuffers eb, double *energy,

@@ -9,7 +9,9 @@
 // symmetric), recomputes the sort key that j has in i's formatted list with
 // the same pinned arithmetic, and finds it by binary search in i's sorted
 // type block.  Every sum runs in a fixed order, so results are reproducible
-// run to run.
+// run to run.  In a sub-region evaluation (Sec. 3.1) only atoms below nloc
+// are centres; the ghost atoms above it collect the j-side increments that
+// are sent back to the processes owning them.
 #include "dp_internal.cuh"
 
 namespace {
@@ -18,7 +20,7 @@ constexpr unsigned FULL = 0xffffffffu;
 
 __global__ void __launch_bounds__(128) k_force_gather(
     DevModel m, const double *__restrict__ x, const int32_t *__restrict__ types, Box3 box, int N,
-    int cap, const int32_t *__restrict__ cand, const int32_t *__restrict__ ncand,
+    int nloc, int cap, const int32_t *__restrict__ cand, const int32_t *__restrict__ ncand,
     const uint64_t *__restrict__ keys, const int32_t *__restrict__ nreal,
     const double *__restrict__ pair_g, const double *__restrict__ f_own, double *__restrict__ force)
 {
@@ -27,9 +29,10 @@ __global__ void __launch_bounds__(128) k_force_gather(
     if (j >= N) return;
     const int nm = m.nm, T = m.ntypes;
     const int tj = types[j];
+    const bool centre = j < nloc;
     if ((unsigned)tj >= (unsigned)T) {  // flagged by format; only the own part
         if (lane == 0)
-            for (int q = 0; q < 3; ++q) force[3 * j + q] = f_own[3 * j + q];
+            for (int q = 0; q < 3; ++q) force[3 * j + q] = centre ? f_own[3 * j + q] : 0.0;
         return;
     }
     int off = 0;
@@ -42,6 +45,7 @@ __global__ void __launch_bounds__(128) k_force_gather(
     const int32_t *row = cand + (size_t)j * cap;
     for (int p = lane; p < n; p += 32) {
         const int i = row[p];
+        if (i >= nloc) continue;  // a ghost is no centre
         const int nb = nreal[(size_t)i * T + tj];
         if (nb == 0) continue;
         const double xi[3] = {x[3 * i], x[3 * i + 1], x[3 * i + 2]};
@@ -70,9 +74,9 @@ __global__ void __launch_bounds__(128) k_force_gather(
         f[2] += __shfl_xor_sync(FULL, f[2], o);
     }
     if (lane == 0) {
-        force[3 * j + 0] = f_own[3 * j + 0] + f[0];
-        force[3 * j + 1] = f_own[3 * j + 1] + f[1];
-        force[3 * j + 2] = f_own[3 * j + 2] + f[2];
+        force[3 * j + 0] = (centre ? f_own[3 * j + 0] : 0.0) + f[0];
+        force[3 * j + 1] = (centre ? f_own[3 * j + 1] : 0.0) + f[1];
+        force[3 * j + 2] = (centre ? f_own[3 * j + 2] : 0.0) + f[2];
     }
 }
 
@@ -196,11 +200,11 @@ __global__ void __launch_bounds__(1024) k_thermo(int N, const double *__restrict
 }  // namespace
 
 cudaError_t dp_launch_force(cudaStream_t st, const DevModel &m, const double *x,
-                            const int32_t *types, Box3 box, int N, int cap,
+                            const int32_t *types, Box3 box, int N, int nloc, int cap,
                             const NlistBuffers &nb, const FormatBuffers &fb, EvalBuffers eb,
                             double *force, int64_t *launches)
 {
-    k_force_gather<<<(N + 3) / 4, 128, 0, st>>>(m, x, types, box, N, cap, nb.cand, nb.ncand, fb.keys,
+    k_force_gather<<<(N + 3) / 4, 128, 0, st>>>(m, x, types, box, N, nloc, cap, nb.cand, nb.ncand, fb.keys,
                                                 fb.nreal, eb.pair_g, eb.f_own, force);
     *launches += 1;
     return cudaGetLastError();

@@ -497,6 +497,14 @@ cudaError_t dp_launch_build(cudaStream_t st, const DevModel &m, const double *x,
     return cudaGetLastError();
 }
 
+cudaError_t dp_launch_type_perm(cudaStream_t st, const DevModel &m, const int32_t *types, int n,
+                                NlistBuffers nb, int32_t *status, int64_t *launches)
+{
+    k_type_perm<<<1, 1024, 0, st>>>(types, n, m.ntypes, nb.type_perm, nb.type_start, status, nullptr);
+    *launches += 1;
+    return cudaGetLastError();
+}
+
 cudaError_t dp_launch_check_stale(cudaStream_t st, const double *x, const double *xref, int N, Box3 box,
                                   double stale2, int32_t *gate, int64_t *launches)
 {

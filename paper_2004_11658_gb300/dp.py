@@ -24,6 +24,7 @@ STATUS_NAMES = {
     -4: "DP_ERR_NLIST_STALE", -5: "DP_ERR_NONFINITE", -6: "DP_ERR_FILE", -7: "DP_ERR_CUDA",
     -8: "DP_ERR_UNSUPPORTED", -9: "DP_ERR_CAPACITY", -10: "DP_ERR_NOMEM", -11: "DP_ERR_TYPE",
 }
+globals().update({name: code for code, name in STATUS_NAMES.items()})
 DP_PREC_FP64 = 0
 DP_PREC_MIXED = 1
 
@@ -83,6 +84,8 @@ def lib():
             L.dp_format_nlist.argtypes = [_vp, _vp, _vp, _vp, _i64, _vp, _vp]
             L.dp_eval.restype = _i32
             L.dp_eval.argtypes = [_vp, _vp, _vp, _vp, _i64, _vp, _vp, _vp, _vp]
+            L.dp_eval_local.restype = _i32
+            L.dp_eval_local.argtypes = [_vp, _vp, _vp, _vp, _i64, _i64, _vp, _vp, _vp, _vp]
             L.dp_md_step.restype = _i32
             L.dp_md_step.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, _i64, _dbl, _i32, _i32, _dbl, _vp]
             L.dp_md_get_force.restype = _i32
@@ -342,6 +345,30 @@ def dp_eval(ctx, coords, types, box, energy=None, force=None, virial=None, atom_
                       _dev(energy, torch.float64, (1,), "energy"), _dev(force, torch.float64, (N, 3), "force"),
                       _dev(virial, torch.float64, (9,), "virial"),
                       _dev(atom_energy, torch.float64, (N,), "atom_energy") if atom_energy is not None else None)
+    if check:
+        _check(s)
+    return dict(energy=energy, force=force, virial=virial, atom_energy=atom_energy, status=s)
+
+
+def dp_eval_local(ctx, coords, types, box, nloc, energy=None, force=None, virial=None, atom_energy=None,
+                  check=True):
+    """Sub-region evaluation: atoms [0, nloc) are centres, [nloc, N) ghosts.
+    Returns dict(energy [1], force [N, 3], virial [9], atom_energy, status)."""
+    N = coords.shape[0]
+    dev = coords.device
+    if energy is None:
+        energy = torch.empty(1, dtype=torch.float64, device=dev)
+    if force is None:
+        force = torch.empty((N, 3), dtype=torch.float64, device=dev)
+    if virial is None:
+        virial = torch.empty(9, dtype=torch.float64, device=dev)
+    b = _box9(box)
+    s = lib().dp_eval_local(ctx.handle, _dev(coords, torch.float64, (N, 3), "coords"),
+                            _dev(types, torch.int32, (N,), "types"), b.ctypes.data_as(_vp), N, int(nloc),
+                            _dev(energy, torch.float64, (1,), "energy"), _dev(force, torch.float64, (N, 3), "force"),
+                            _dev(virial, torch.float64, (9,), "virial"),
+                            _dev(atom_energy, torch.float64, (int(nloc),), "atom_energy")
+                            if atom_energy is not None else None)
     if check:
         _check(s)
     return dict(energy=energy, force=force, virial=virial, atom_energy=atom_energy, status=s)

@@ -62,8 +62,11 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision measurement")
+    p.add_argument("--no-student", action="store_true", help="skip the student-model measurement")
     p.add_argument("--profile-eval", type=int, default=0, metavar="N",
                    help="run N energy/force evaluations of the workload and exit (profiling driver)")
+    p.add_argument("--profile-precision", choices=["fp64", "mixed"], default="fp64")
+    p.add_argument("--profile-model", choices=["full", "student"], default="full")
     return p.parse_args()
 
 
@@ -239,34 +242,49 @@ def mixed_kernel_flops(desc, rows, natoms):
     }
 
 
-def measure_mixed(args, dp, synth, w, desc, P, v0, dev, world, flush):
-    """Mixed-precision MD on the same workload: throughput, per-kernel times,
-    roofline of the dominant kernel and accuracy against the FP64 path."""
+def _accuracy(dp, ctx, judge, x, t, box):
+    """Forces, energy and virial of ctx against the judge context (FP64 full
+    model) on the configuration x: RMSE per component, per-atom |dF|
+    percentiles, energy error per atom, virial error relative to its max."""
     import torch
-    N = len(v0)
-    model = dp.Model(desc, P)
-    ctx = dp.Context(model, N, precision=dp.DP_PREC_MIXED)
-    ref = dp.Context(model, N)
-    x = torch.tensor(w["coords"], dtype=torch.float64, device=dev)
-    v = torch.tensor(v0, dtype=torch.float64, device=dev)
-    t = torch.tensor(w["types"], dtype=torch.int32, device=dev)
-    # accuracy on the initial configuration, same candidates
-    dp.dp_build_nlist(ctx, x, t, w["box"], SKIN)
-    dp.dp_build_nlist(ref, x, t, w["box"], SKIN)
-    a = dp.dp_eval(ctx, x, t, w["box"])
-    b = dp.dp_eval(ref, x, t, w["box"])
+    N = x.shape[0]
+    dp.dp_build_nlist(ctx, x, t, box, SKIN)
+    dp.dp_build_nlist(judge, x, t, box, SKIN)
+    a = dp.dp_eval(ctx, x, t, box)
+    a = {k: v.clone() for k, v in a.items() if torch.is_tensor(v)}
+    b = dp.dp_eval(judge, x, t, box)
     dF = (a["force"] - b["force"]).double()
     rmse = float(dF.pow(2).mean().sqrt())
     frms = float(b["force"].pow(2).mean().sqrt())
-    e_err = abs(a["energy"].item() - b["energy"].item()) / N
-    v_err = float((a["virial"] - b["virial"]).abs().max() / b["virial"].abs().max())
-    del ref
+    pa = dF.norm(dim=1).cpu().numpy()
+    p50, p90, p99 = (float(q) for q in np.percentile(pa, [50, 90, 99]))
+    return {"force_rmse_eV_per_A": rmse, "force_rms_eV_per_A": frms,
+            "rel_force_rmse": rmse / frms if frms > 0 else None,
+            "atom_force_err_p50_p90_p99_eV_per_A": [p50, p90, p99],
+            "energy_err_eV_per_atom": abs(a["energy"].item() - b["energy"].item()) / N,
+            "virial_rel_err": float((a["virial"] - b["virial"]).abs().max() / b["virial"].abs().max())}
+
+
+def measure_mode(args, dp, w, run_desc, run_P, judge_model, v0, dev, world, flush, dtype):
+    """MD with another model or precision on the same workload: throughput,
+    per-kernel times, roofline of the dominant kernel, and accuracy against
+    the FP64 full model on the first and on the last configuration."""
+    import torch
+    N = len(v0)
+    model = dp.Model(run_desc, run_P)
+    ctx = dp.Context(model, N, precision=dp.DP_PREC_MIXED)
+    judge = dp.Context(judge_model, N)
+    x = torch.tensor(w["coords"], dtype=torch.float64, device=dev)
+    v = torch.tensor(v0, dtype=torch.float64, device=dev)
+    t = torch.tensor(w["types"], dtype=torch.int32, device=dev)
+    acc_first = _accuracy(dp, ctx, judge, x, t, w["box"])
     th = torch.empty((MD_PER_STEP, 4), dtype=torch.float64, device=dev)
 
     def step():
         dp.dp_md_step(ctx, x, v, t, w["box"], w["masses"], DT_FS, MD_PER_STEP, rebuild_every=MD_PER_STEP,
                       skin=SKIN, thermo=th, check=False)
 
+    dp.dp_md_reset(ctx)
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -285,9 +303,15 @@ def measure_mixed(args, dp, synth, w, desc, P, v0, dev, world, flush):
     kt = ctx.kernel_times()
     ctx.set_timing(0)
     total_ms = sum(e0.elapsed_time(e1) for e0, e1 in evs)
+    tmax = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    total_ms = float(tmax.item())
     nl, nr, _ = dp.dp_format_nlist(ctx, x, t, w["box"], check=False)
     rows = int(nr.sum().item())
-    fl = mixed_kernel_flops(desc, rows, N)
+    acc_last = _accuracy(dp, ctx, judge, x, t, w["box"])
+    fl = mixed_kernel_flops(run_desc, rows, N)
     groups = {g: {"ms": ms, "launches": n} for g, (ms, n) in kt.items() if n > 0}
     dom = max(groups, key=lambda g: groups[g]["ms"])
     roof = None
@@ -308,14 +332,17 @@ def measure_mixed(args, dp, synth, w, desc, P, v0, dev, world, flush):
     th_all = torch.stack(thermo_all).cpu().numpy().reshape(-1, 4)
     etot = th_all[:, 0] + th_all[:, 1]
     return {"value": world * N * MD_PER_STEP * args.steps / (total_ms / 1000.0), "unit": METRIC,
-            "ms_per_step": total_ms / args.steps, "dtype": "bf16 GEMMs (fp32 accumulate) + f64",
+            "ms_per_step": total_ms / args.steps, "dtype": dtype,
+            "model": "se_a water %s / M2 %d / fit %s" % ("-".join(map(str, run_desc["emb"])), run_desc["m2"],
+                                                        "x".join(map(str, run_desc["fit"]))),
             "kernels_ms_per_step": {g: d["ms"] / args.steps for g, d in groups.items()},
             "roofline": roof,
-            "accuracy_vs_fp64": {"force_rmse_eV_per_A": rmse, "force_rms_eV_per_A": frms,
-                                 "rel_force_rmse": rmse / frms if frms > 0 else None,
-                                 "energy_err_eV_per_atom": e_err, "virial_rel_err": v_err},
+            "accuracy_vs_fp64_full_model": {"first_config": acc_first, "last_config": acc_last},
             "nve": {"max_abs_drift_eV_per_atom": float(np.abs(etot - etot[0]).max() / N),
                     "T_last_K": float(th_all[-1, 2])}}
+
+
+STUDENT_PARAMS = os.path.join(ROOT, "paper_2004_11658_gb300", "data", "student_water12288.npy")
 
 
 def run_ours(args, rank, world, local_rank):
@@ -448,7 +475,17 @@ def run_ours(args, rank, world, local_rank):
 
     modes = {}
     if not args.no_mixed:
-        modes["mixed"] = measure_mixed(args, dp, synth, w, desc, P, v0, dev, world, flush)
+        modes["mixed"] = measure_mode(args, dp, w, desc, P, model, v0, dev, world, flush,
+                                      "bf16 GEMMs (fp32 accumulate) + f64")
+    if not args.no_student and args.workload.startswith("water"):
+        if os.path.exists(STUDENT_PARAMS):
+            Ps = np.load(STUDENT_PARAMS).astype(np.float64)
+            modes["student"] = measure_mode(args, dp, w, synth.WATER_STUDENT, Ps, model, v0, dev, world, flush,
+                                            "bf16 GEMMs (fp32 accumulate) + f64")
+            modes["student"]["params"] = os.path.relpath(STUDENT_PARAMS, ROOT)
+        else:
+            modes["student"] = {"unavailable": "no trained student parameters at "
+                                + os.path.relpath(STUDENT_PARAMS, ROOT)}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -486,8 +523,12 @@ def profile_eval(args):
     from paper_2004_11658_gb300 import dp, synth
     w = synth.workload(args.workload)
     desc = w["model"]
-    model = dp.Model(desc, synth.model_params(desc, 0))
-    ctx = dp.Context(model, len(w["coords"]))
+    P = synth.model_params(desc, 0)
+    if args.profile_model == "student":
+        desc, P = synth.WATER_STUDENT, np.load(STUDENT_PARAMS).astype(np.float64)
+    model = dp.Model(desc, P)
+    prec = dp.DP_PREC_MIXED if args.profile_precision == "mixed" else dp.DP_PREC_FP64
+    ctx = dp.Context(model, len(w["coords"]), precision=prec)
     x = torch.tensor(w["coords"], device="cuda")
     t = torch.tensor(w["types"], device="cuda")
     for _ in range(args.profile_eval):

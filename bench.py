@@ -46,9 +46,10 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # DRAM bytes per launch of the dominant kernel from one ncu capture;
 # reported only while the kernel source is the one captured.
 TRAFFIC = {
-    # ncu --set full, k_embed_bwd, one 12,288-atom water evaluation:
-    # dram__bytes_read.sum + dram__bytes_write.sum
-    "embed_bwd": {"bytes_per_launch": 207.849984e6 + 20.871680e6, "file": "embed.cu", "src_sha": "6034564e8b7128ac"},
+    # ncu --set full, one 12,288-atom water evaluation (bench.py --profile-eval 2):
+    # dram__bytes_read.sum + dram__bytes_write.sum of the dominant kernel
+    "embed_bwd": {"bytes_per_launch": 206.358016e6 + 19.876096e6, "file": "embed.cu", "src_sha": "c982a146b11862b2"},
+    "embed_bwd_mx<25>": {"bytes_per_launch": 204.823552e6 + 17.918464e6, "file": "mixed.cu", "src_sha": "1d36586835464fdc"},
 }
 
 
@@ -161,8 +162,12 @@ def measured_peaks():
 
 
 def source_sha(fn):
-    with open(os.path.join(ROOT, "paper_2004_11658_gb300", "csrc", fn), "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+    """Hash of a kernel source file together with the shared device header."""
+    h = hashlib.sha256()
+    for name in (fn, "dp_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_2004_11658_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
 
 
 # ------------------------------------------------------------ reference --
@@ -322,10 +327,12 @@ def measure_mode(args, dp, w, run_desc, run_P, judge_model, v0, dev, world, flus
         ach_t = fl[dom]["tensor"] / sec / 1e12
         ach_d = fl[dom]["fp64"] / sec / 1e12
         ft, fd = ach_t / bf16_peak, ach_d / FP64_PEAK_TFLOPS
-        roof = {"bound": "alu" if fd >= ft else "tensor", "kernel": dom,
+        tr = TRAFFIC.get(f"{dom}_mx<{run_desc['emb'][0]}>")
+        traffic = tr["bytes_per_launch"] if tr and tr.get("src_sha") == source_sha(tr["file"]) else None
+        roof = {"bound": "alu" if fd >= ft else "tensor", "kernel": f"{dom}_mx<{run_desc['emb'][0]}>",
                 "achieved": ach_d if fd >= ft else ach_t,
                 "peak": FP64_PEAK_TFLOPS if fd >= ft else bf16_peak, "unit": "TFLOP/s",
-                "frac": max(fd, ft), "traffic": None,
+                "frac": max(fd, ft), "traffic": traffic,
                 "fp64": {"achieved": ach_d, "peak": FP64_PEAK_TFLOPS, "frac": fd},
                 "tensor_bf16": {"achieved": ach_t, "peak": bf16_peak, "frac": ft,
                                 "peak_source": "MEASURED_PEAKS bf16_tflops (burst, of measured)"}}

@@ -507,3 +507,28 @@ def test_param_grad_single_parameters(oracle, synth):
         d1, d2 = fd(2e-4), fd(1e-4)
         rich = (4 * d2 - d1) / 3
         assert rich == pytest.approx(g[p], rel=1e-5, abs=1e-8 * max(1.0, np.abs(g).max()))
+
+
+def test_eval_local_partition_additivity(oracle, synth):
+    """Sub-region evaluation: with every atom a centre it is the whole-system
+    evaluation; over a partition of the centres (the rest as ghosts) the
+    energies, forces and virials add up to the whole system's."""
+    w = synth.workload("water192")
+    desc = w["model"]
+    P = synth.model_params(desc, 0)
+    N = len(w["coords"])
+    ref = oracle.evaluate(desc, P, w["coords"], w["types"], w["box"])
+    full = oracle.evaluate_local(desc, P, w["coords"], w["types"], w["box"], N)
+    assert full["energy"] == ref["energy"]
+    assert np.array_equal(full["force"], ref["force"])
+    perm = np.random.default_rng(3).permutation(N)
+    E, F, V = 0.0, np.zeros((N, 3)), np.zeros((3, 3))
+    for part in (perm[:70], perm[70:150], perm[150:]):
+        order = np.concatenate([part, np.setdiff1d(np.arange(N), part)])
+        r = oracle.evaluate_local(desc, P, w["coords"][order], w["types"][order], w["box"], len(part))
+        E += r["energy"]
+        F[order] += r["force"]
+        V += r["virial"]
+    assert E == pytest.approx(ref["energy"], rel=1e-13)
+    assert np.abs(F - ref["force"]).max() < 1e-13 * np.abs(ref["force"]).max()
+    assert np.abs(V - ref["virial"]).max() < 1e-12 * np.abs(ref["virial"]).max()

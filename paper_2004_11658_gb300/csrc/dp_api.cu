@@ -99,6 +99,7 @@ struct dp_model {
     int64_t nparams;
     double *d_params;
     double *h_params;
+    int64_t version;  // incremented by dp_model_set_params
     DevModel dev;
 };
 
@@ -134,6 +135,14 @@ struct dp_ctx {
     double last_mass[DP_MAX_TYPES];
     // parameter gradient scratch (allocated on first use)
     PGradBuffers pb;
+    // FP64 fitting net on the tensor cores (exact splitting): weight digits
+    // (made from the model's parameters of version oz_version) and scratch
+    bool use_oz;
+    OzModel oz;
+    OzBuffers ob;
+    uint16_t *d_oz_w;
+    int32_t *d_oz_e;
+    int64_t oz_w_elems, oz_e_elems, oz_version;
     // mixed precision: BF16 / FP32 copies of the parameters
     MixedModel mx;
     float *d_p32;
@@ -480,6 +489,37 @@ dp_status enqueue_format(dp_ctx *c, const double *coords, const int32_t *types, 
     return DP_OK;
 }
 
+// Weight digits of the tensor-core FP64 fitting net (again whenever the
+// model's parameters changed) and its scratch (first use).
+dp_status ensure_oz(dp_ctx *c)
+{
+    dp_status s = DP_OK;
+    if (!c->ob.a) {
+        const int64_t N = c->natoms_max;
+        const int T = c->m.ntypes, nf = c->m.n_fit;
+        OzBuffers &ob = c->ob;
+        ob.tiles = (int)((N + DP_OZ_TILE - 1) / DP_OZ_TILE) + T;
+        ob.a_stride = c->oz.in_w;
+        ob.nmax = N;
+        const size_t plane = (size_t)N * c->oz.fmax;
+        if ((s = dev_alloc(&ob.a, (size_t)ob.tiles * ob.a_stride, "fitting digits"))) return s;
+        if ((s = dev_alloc(&ob.aexp, (size_t)ob.tiles * DP_OZ_TILE, "fitting digits"))) return s;
+        if ((s = dev_alloc(&ob.t, (size_t)nf * plane, "fitting activations"))) return s;
+        if ((s = dev_alloc(&ob.h, 2 * plane, "fitting activations"))) return s;
+        if ((s = dev_alloc(&ob.g, 2 * plane, "fitting activations"))) return s;
+    }
+    if (c->oz_version != c->model->version) {
+        std::vector<uint16_t> w((size_t)c->oz_w_elems, 0);
+        std::vector<int32_t> e((size_t)c->oz_e_elems, 0);
+        dp_oz_split_weights(c->m, c->model->h_params, c->oz, w.data(), e.data());
+        DP_CUDA(cudaStreamSynchronize(c->stream), "fitting digits");
+        DP_CUDA(cudaMemcpy(c->d_oz_w, w.data(), w.size() * 2, cudaMemcpyHostToDevice), "fitting digits");
+        DP_CUDA(cudaMemcpy(c->d_oz_e, e.data(), e.size() * 4, cudaMemcpyHostToDevice), "fitting digits");
+        c->oz_version = c->model->version;
+    }
+    return DP_OK;
+}
+
 dp_status enqueue_eval(dp_ctx *c, const double *coords, const int32_t *types, const Box3 &b, int64_t N,
                        int64_t nloc, double *energy, double *force, double *virial, double *atom_energy)
 {
@@ -498,10 +538,13 @@ dp_status enqueue_eval(dp_ctx *c, const double *coords, const int32_t *types, co
                                             &c->launches);
             if (e != cudaSuccess) return cuda_fail(e, "embed_fwd");
         }
+        if (!mixed && c->use_oz && (s = ensure_oz(c))) return s;
         {
             GroupTimer tm(c, G_FIT);
-            e = mixed ? dp_launch_fit_mx(c->stream, c->m, c->mx, n, c->nb, c->eb, c->d_status, &c->launches)
-                      : dp_launch_fit(c->stream, c->m, n, c->nb, c->eb, &c->launches);
+            e = mixed     ? dp_launch_fit_mx(c->stream, c->m, c->mx, n, c->nb, c->eb, c->d_status, &c->launches)
+                : c->use_oz ? dp_launch_fit_oz(c->stream, c->m, c->oz, c->ob, n, c->nb, c->eb, c->d_status,
+                                               &c->launches)
+                            : dp_launch_fit(c->stream, c->m, n, c->nb, c->eb, &c->launches);
             if (e != cudaSuccess) return cuda_fail(e, "fit");
         }
         {
@@ -710,7 +753,8 @@ void dp_ctx_free(dp_ctx *c)
                     c->eb.T, c->eb.D, c->eb.gD, c->eb.Ei, c->eb.pair_g, c->eb.f_own, c->eb.vir_part,
                     c->d_energy, c->d_virial, c->md_force, c->ke_part, c->d_inv_mass_conv, c->d_mass,
                     c->eb.fit_t, c->eb.fit_h, c->d_p32, c->d_emb_ops, c->d_fit_fwd, c->d_fit_bwd,
-                    c->pb.dT, c->pb.dD, c->pb.Db, c->pb.dDb, c->pb.fit_scr, c->pb.rowscr, c->pb.slices};
+                    c->pb.dT, c->pb.dD, c->pb.Db, c->pb.dDb, c->pb.fit_scr, c->pb.rowscr, c->pb.slices,
+                    c->d_oz_w, c->d_oz_e, c->ob.a, c->ob.aexp, c->ob.t, c->ob.h, c->ob.g};
     for (void *p : bufs) dev_free(p);
     delete c;
 }
@@ -723,7 +767,7 @@ dp_status dp_ctx_create(const dp_model *model, int64_t natoms_max, int32_t cand_
     if (!model) return fail(DP_ERR_ARG, "model is NULL");
     if (natoms_max < 1 || natoms_max >= (1 << 26)) return fail(DP_ERR_ARG, "natoms_max must be in [1, 2^26)");
     if (cand_cap < 0 || cand_cap > 1024) return fail(DP_ERR_ARG, "cand_cap must be in [0, 1024]");
-    if (precision != DP_PREC_FP64 && precision != DP_PREC_MIXED)
+    if (precision != DP_PREC_FP64 && precision != DP_PREC_MIXED && precision != DP_PREC_FP64_SIMT)
         return fail(DP_ERR_UNSUPPORTED, "unknown precision mode");
     if (precision == DP_PREC_MIXED && !dp_mixed_supported(model->dev))
         return fail(DP_ERR_UNSUPPORTED, "mixed precision needs a 3-layer doubling embedding net (s_1 in {16, 25, 32}) "
@@ -777,6 +821,15 @@ dp_status dp_ctx_create(const dp_model *model, int64_t natoms_max, int32_t cand_
     if (precision == DP_PREC_MIXED) {
         ALLOC(c->eb.fit_t, N * (size_t)c->m.n_fit * 256);
         ALLOC(c->eb.fit_h, N * 256);
+    }
+    c->use_oz = false;
+    c->oz_version = -1;
+    if (precision == DP_PREC_FP64 && dp_oz_plan(c->m, c->oz, c->oz_w_elems, c->oz_e_elems)) {
+        ALLOC(c->d_oz_w, (size_t)c->oz_w_elems);
+        ALLOC(c->d_oz_e, (size_t)c->oz_e_elems);
+        c->oz.w = c->d_oz_w;
+        c->oz.wexp = c->d_oz_e;
+        c->use_oz = true;
     }
 #undef ALLOC
     if (!s && precision == DP_PREC_MIXED) s = build_mixed(c);
@@ -1007,6 +1060,7 @@ dp_status dp_model_set_params(dp_model *md, const double *params, int64_t nparam
         if (!std::isfinite(params[q])) return fail(DP_ERR_ARG, "non-finite parameter");
     std::memcpy(md->h_params, params, sizeof(double) * nparams);
     DP_CUDA(cudaMemcpy(md->d_params, params, sizeof(double) * nparams, cudaMemcpyHostToDevice), "dp_model_set_params");
+    md->version += 1;
     return DP_OK;
 }
 
@@ -1016,7 +1070,7 @@ dp_status dp_param_grad(dp_ctx *c, const double *coords, const int32_t *types, c
     dp_status s = check_common(c, coords, types, N);
     if (s) return s;
     if (!lambda || !grad) return fail(DP_ERR_ARG, "lambda/grad is NULL");
-    if (c->precision != DP_PREC_FP64) return fail(DP_ERR_UNSUPPORTED, "parameter gradients need an FP64 context");
+    if (c->precision == DP_PREC_MIXED) return fail(DP_ERR_UNSUPPORTED, "parameter gradients need an FP64 context");
     for (int l = 1; l < c->m.n_fit; ++l)
         if (dp_skip_kind(c->m.fit[l - 1], c->m.fit[l]) == 2)
             return fail(DP_ERR_UNSUPPORTED, "parameter gradients support equal-width fitting skips only");

@@ -219,6 +219,49 @@ cudaError_t dp_launch_reduce(cudaStream_t st, int N, EvalBuffers eb, double *ene
                              double *virial, double *atom_energy, int32_t *status,
                              int64_t *launches);
 
+// FP64 fitting net with its GEMMs on the tensor cores by exact splitting
+// (csrc/fit_oz.cu).  Every GEMM Y = X W (X: 128-atom tiles, W: weights) is
+//   Y = 2^(e_r + f_n) sum_{s+t <= S+1} 2^(-beta (s+t)) (A_s B_t),
+// A_s, B_t the integer digits (|.| <= 2^beta) of X and W in base 2^beta
+// relative to per-row / per-column power-of-two scales, stored as BF16; the
+// products and their sums over K are integers below 2^24, so the FP32 tensor
+// core accumulators hold them exactly and Y is an FP64-accurate product.
+constexpr int DP_OZ_TILE = 128;  // atoms per tile (MMA M)
+constexpr int DP_OZ_NC = 32;     // output columns per CTA (MMA N)
+constexpr int DP_OZ_KC = 16;     // K per chunk (MMA K)
+struct OzGemm {
+    int K, N;          // contraction and output widths (unpadded)
+    int nK, nN;        // chunks of DP_OZ_KC and DP_OZ_NC
+    int beta, S;       // digit width (bits) and digit count
+    int64_t w_off[DP_MAX_TYPES];  // element offset of the type's weight digits
+    int64_t e_off[DP_MAX_TYPES];  // offset of the type's column exponents
+};
+struct OzModel {
+    int ok;                                   // the model's fitting net is supported
+    OzGemm fwd[DP_MAX_LAYERS];                // h_l = act(h_{l-1} W_l + b_l)
+    OzGemm bwd[DP_MAX_LAYERS];                // g_{l-1} = gz_l W_l^T (+ skip)
+    int in_w;                                 // widest GEMM input (K), padded
+    int fmax;                                 // widest hidden layer
+    const uint16_t *w;                        // device: weight digits
+    const int32_t *wexp;                      // device: column exponents
+};
+struct OzBuffers {
+    uint16_t *a;            // A digits, [tiles][a_stride]
+    int32_t *aexp;          // row exponents, [tiles][128]
+    int64_t a_stride;       // elements per tile
+    int tiles;              // tile capacity
+    double *t;              // tanh values [n_fit][Nmax][fmax]
+    double *h;              // activations, 2 x [Nmax][fmax]
+    double *g;              // gradients, 2 x [Nmax][fmax]
+    int64_t nmax;
+};
+// Host: shapes of the split GEMMs (returns false if the fitting net is not
+// supported: hidden widths must be <= DP_MAX_FIT_W), then the weight digits.
+bool dp_oz_plan(const DevModel &m, OzModel &oz, int64_t &w_elems, int64_t &e_elems);
+void dp_oz_split_weights(const DevModel &m, const double *h_params, const OzModel &oz, uint16_t *w, int32_t *e);
+cudaError_t dp_launch_fit_oz(cudaStream_t st, const DevModel &m, const OzModel &oz, const OzBuffers &ob, int N,
+                             const NlistBuffers &nb, EvalBuffers eb, int32_t *status, int64_t *launches);
+
 // Mixed precision (BF16 tensor-core GEMMs, FP64 environment / contractions).
 cudaError_t dp_launch_embed_fwd_mx(cudaStream_t st, const DevModel &m, const MixedModel &mx, const double *x,
                                    const int32_t *types, Box3 box, int N, const FormatBuffers &fb,

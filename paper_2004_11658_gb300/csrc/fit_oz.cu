@@ -1,0 +1,645 @@
+// fit_oz.cu -- the fitting net N_a (Eqs. fitting, fitting-detail; one net per
+// centre type, Remark 1), forward and backward to the descriptor, with FP64
+// accuracy and every GEMM on the 5th-generation tensor cores.
+//
+// Exact splitting (Ozaki's scheme).  A GEMM Y = X W with FP64 operands is
+// written with a power-of-two scale per row of X (2^e_r >= max_k |X_rk|) and
+// per column of W (2^f_n), and the scaled values as S signed digits in base
+// 2^beta:
+//   X_rk = 2^e_r sum_s a_s,rk 2^(-beta s),   W_kn = 2^f_n sum_t b_t,kn 2^(-beta t),
+// with |a_1|, |b_1| <= 2^beta and |a_s|, |b_t| <= 2^(beta-1) for s, t >= 2
+// (balanced digits of the integers round(X_rk 2^(beta S - e_r))).  Then
+//   Y_rn = 2^(e_r + f_n) sum_g 2^(-beta g) C_g,   C_g = sum_{s+t=g} A_s B_t,
+// summed over g = 2 .. S+1 (the terms beyond are below FP64 rounding).  A digit
+// is an integer of at most 8 bits, exact in BF16; every product is exact in
+// FP32, and beta is chosen per GEMM from its contraction length K so that
+//   K 4^(beta-1) (S + 2) < 2^24,
+// which bounds every partial sum of every C_g: the FP32 tensor-core
+// accumulators hold C_g exactly, in any summation order.  The result is the
+// exact product of the digit expansions, rounded once per group into FP64,
+// and is reproducible bit for bit.
+//
+// Kernels.  k_oz_split: one warp per row of a 128-atom tile of one type;
+// row maximum, exponent, digits written as S BF16 matrices in the canonical
+// K-major layout of the MMA A operand (16-column chunks).  The weights'
+// digits are made once on the host.  k_oz_gemm: one CTA per (tile, 32-column
+// chunk of Y); one thread streams the digit chunks of A and W with bulk copies
+// (cp.async.bulk, 3-stage ring on mbarriers) and issues S(S+1)/2 MMAs of
+// 128 x 32 x 16 per chunk into S group accumulators in tensor memory; the
+// epilogue (4 warps, one row per thread) combines the groups in FP64 and
+// applies the layer's bias, tanh and skip (forward) or the skip gradient
+// (backward).  Every wait is bounded; on a timeout the kernel sets
+// DPF_MMA_TIMEOUT, waits for its copies and MMAs, frees tensor memory and
+// returns.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "dp_internal.cuh"
+#include "tc.cuh"
+
+namespace {
+
+constexpr int OZ_ST = 3;                    // pipeline stages
+constexpr int OZ_A_BLK = DP_OZ_TILE * DP_OZ_KC;  // elements of one A digit chunk (128 x 16)
+constexpr int OZ_B_BLK = DP_OZ_NC * DP_OZ_KC;    // elements of one W digit chunk (32 x 16)
+
+// Element offset of (row, k) inside a 16-column chunk in the canonical K-major
+// layout: 8 x 8 core matrices of 16-byte rows, the two core matrices of a row
+// group 64 elements apart, row groups 128 elements apart.
+__host__ __device__ __forceinline__ int oz_kofs(int row, int k)
+{
+    return (row >> 3) * 128 + (k >> 3) * 64 + (row & 7) * 8 + (k & 7);
+}
+
+// Balanced base-2^beta digits of I, most significant first: I = sum_s d[s] 2^(beta (S-1-s)).
+__host__ __device__ __forceinline__ int oz_digit_step(long long &I, int beta)
+{
+    const long long mask = (1ll << beta) - 1, half = 1ll << (beta - 1);
+    long long r = I & mask;
+    I >>= beta;
+    if (r > half) {
+        r -= (1ll << beta);
+        I += 1;
+    }
+    return (int)r;
+}
+
+// BF16 bits of a small integer (|d| <= 256): exact.
+__host__ __device__ __forceinline__ uint16_t oz_bf16_int(int d)
+{
+    const float f = (float)d;
+#ifdef __CUDA_ARCH__
+    const uint32_t u = __float_as_uint(f);
+#else
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+#endif
+    return (uint16_t)(u >> 16);
+}
+
+// 2^e as a double (normal range).
+__host__ __device__ __forceinline__ double oz_pow2(int e)
+{
+    const long long b = (long long)(e + 1023) << 52;
+#ifdef __CUDA_ARCH__
+    return __longlong_as_double(b);
+#else
+    double d;
+    std::memcpy(&d, &b, 8);
+    return d;
+#endif
+}
+
+struct TileRef {
+    int a, first, cnt;
+};
+
+// Tile index -> (type, first position in type_perm, atoms); a = -1 past the end.
+__device__ __forceinline__ TileRef oz_tile(int tl, const int32_t *__restrict__ type_start, int ntypes)
+{
+    TileRef t{-1, 0, 0};
+    for (int a = 0; a < ntypes; ++a) {
+        const int n_a = type_start[a + 1] - type_start[a];
+        const int tiles = (n_a + DP_OZ_TILE - 1) / DP_OZ_TILE;
+        if (tl < tiles) {
+            t.a = a;
+            t.first = type_start[a] + tl * DP_OZ_TILE;
+            t.cnt = min(DP_OZ_TILE, n_a - tl * DP_OZ_TILE);
+            return t;
+        }
+        tl -= tiles;
+    }
+    return t;
+}
+
+// ------------------------------------------------------------------ split --
+
+struct OzSplitArgs {
+    int mode;  // 0: x = src; 1: x = src (1 - t^2); 2: x = w_out (1 - t^2) and E_i = src . w_out + b_out
+    const double *src;
+    int lds;
+    const double *tv;
+    int ldt;
+    const double *wout[DP_MAX_TYPES];
+    const double *bout[DP_MAX_TYPES];
+    double *Ei;
+    int K, nK, beta, S;
+    const int32_t *type_perm, *type_start;
+    int ntypes;
+    uint16_t *a;
+    int32_t *aexp;
+    int64_t a_stride;
+};
+
+__global__ void __launch_bounds__(256) k_oz_split(OzSplitArgs p)
+{
+    const int lane = threadIdx.x & 31;
+    const int gw = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+    const int tl = gw / DP_OZ_TILE, r = gw % DP_OZ_TILE;
+    const TileRef T = oz_tile(tl, p.type_start, p.ntypes);
+    if (T.a < 0) return;
+    const int i = r < T.cnt ? p.type_perm[T.first + r] : -1;
+    const int Kp = p.nK * DP_OZ_KC;
+    const double *srow = i >= 0 ? p.src + (size_t)i * p.lds : nullptr;
+    const double *trow = (i >= 0 && p.mode != 0) ? p.tv + (size_t)i * p.ldt : nullptr;
+    const double *wo = p.mode == 2 ? p.wout[T.a] : nullptr;
+
+    // the 8 values of columns k8 .. k8+7
+    auto load8 = [&](int k8, double (&v)[8]) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) v[q] = 0.0;
+        if (i < 0 || k8 >= p.K) return;
+        if (k8 + 8 <= p.K && (p.mode == 2 || (p.lds & 1) == 0)) {
+            if (p.mode == 2) {
+#pragma unroll
+                for (int q = 0; q < 8; ++q) v[q] = wo[k8 + q];
+            } else {
+                const double2 *s2 = reinterpret_cast<const double2 *>(srow + k8);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const double2 u = s2[q];
+                    v[2 * q] = u.x;
+                    v[2 * q + 1] = u.y;
+                }
+            }
+        } else {
+            for (int q = 0; q < 8 && k8 + q < p.K; ++q) v[q] = p.mode == 2 ? wo[k8 + q] : srow[k8 + q];
+        }
+        if (p.mode != 0) {
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                if (k8 + q < p.K) {
+                    const double t = trow[k8 + q];
+                    v[q] *= fma(-t, t, 1.0);
+                }
+            }
+        }
+    };
+
+    // output layer energy: E_i = b_out + h . w_out (lane partials in k order, fixed shuffle tree)
+    if (p.mode == 2) {
+        double e = 0.0;
+        if (i >= 0)
+            for (int k = lane; k < p.K; k += 32) e = fma(srow[k], wo[k], e);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+        if (i >= 0 && lane == 0) p.Ei[i] = *p.bout[T.a] + e;
+    }
+
+    // row exponent: 2^e > max |x|
+    double mx = 0.0;
+    for (int k8 = lane * 8; k8 < Kp; k8 += 256) {
+        double v[8];
+        load8(k8, v);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) mx = fmax(mx, fabs(v[q]));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    int e = 0;
+    const int bS = p.beta * p.S;
+    bool zero = !(mx > 0.0);
+    if (!zero) {
+        frexp(mx, &e);
+        if (e < bS - 1020) zero = true;  // below 2^-960: a zero row
+    }
+    if (zero) e = 0;
+    if (lane == 0) p.aexp[(size_t)tl * DP_OZ_TILE + r] = e;
+    const double scale = zero ? 0.0 : oz_pow2(bS - e);
+
+    uint16_t *out = p.a + (size_t)tl * p.a_stride;
+    for (int k8 = lane * 8; k8 < Kp; k8 += 256) {
+        double v[8];
+        load8(k8, v);
+        long long I[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) I[q] = __double2ll_rn(v[q] * scale);
+        const int kc = k8 / DP_OZ_KC;
+        const int ofs = oz_kofs(r, k8 % DP_OZ_KC);
+        for (int s = p.S - 1; s >= 0; --s) {
+            int d[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) d[q] = s > 0 ? oz_digit_step(I[q], p.beta) : (int)I[q];
+            uint4 u;
+            u.x = (uint32_t)oz_bf16_int(d[0]) | ((uint32_t)oz_bf16_int(d[1]) << 16);
+            u.y = (uint32_t)oz_bf16_int(d[2]) | ((uint32_t)oz_bf16_int(d[3]) << 16);
+            u.z = (uint32_t)oz_bf16_int(d[4]) | ((uint32_t)oz_bf16_int(d[5]) << 16);
+            u.w = (uint32_t)oz_bf16_int(d[6]) | ((uint32_t)oz_bf16_int(d[7]) << 16);
+            *reinterpret_cast<uint4 *>(out + ((size_t)kc * p.S + s) * OZ_A_BLK + ofs) = u;
+        }
+    }
+}
+
+// ------------------------------------------------------------------- gemm --
+
+struct OzGemmArgs {
+    const uint16_t *a;
+    const int32_t *aexp;
+    int64_t a_stride;
+    const uint16_t *w;
+    const int32_t *wexp;
+    OzGemm g;
+    const int32_t *type_perm, *type_start;
+    int ntypes;
+    int epi;      // 0: forward (bias, tanh, skip); 1: backward (skip gradient)
+    int skip;     // skip kind of the layer
+    int skip_in;  // input width of the layer
+    const double *bias[DP_MAX_TYPES];
+    const double *hin;  // forward: layer input (skip); backward: dL/dh_l per atom
+    int ldh;
+    const double *gbc[DP_MAX_TYPES];  // backward: dL/dh_l broadcast per type (last layer), else null
+    double *tout;
+    double *hout;
+    int ldo;
+    const double *tanh_tab;
+    int32_t *status;
+};
+
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *mbar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+            tc::smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(tc::smem_u32(mbar))
+        : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *mbar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(tc::smem_u32(mbar)), "r"(bytes)
+                 : "memory");
+}
+
+__global__ void __launch_bounds__(DP_OZ_TILE, 1) k_oz_gemm(OzGemmArgs p)
+{
+    extern __shared__ __align__(1024) unsigned char smraw[];
+    __shared__ __align__(8) uint64_t full[OZ_ST], empty[OZ_ST], done;
+    __shared__ uint32_t tslot;
+    __shared__ int fail;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const OzGemm &g = p.g;
+    const int nchunk = blockIdx.x % g.nN;
+    const TileRef T = oz_tile(blockIdx.x / g.nN, p.type_start, p.ntypes);
+    if (T.a < 0) return;
+    const int tl = blockIdx.x / g.nN;
+    const int S = g.S, nK = g.nK;
+    const uint32_t a_bytes = (uint32_t)S * OZ_A_BLK * 2, b_bytes = (uint32_t)S * OZ_B_BLK * 2;
+    const uint32_t stage_bytes = a_bytes + b_bytes;
+
+    if (warp == 0) tc::tmem_alloc(&tslot, 512);
+    if (tid == 0) {
+        for (int s = 0; s < OZ_ST; ++s) {
+            tc::mbar_init(&full[s], 1);
+            tc::mbar_init(&empty[s], 1);
+        }
+        tc::mbar_init(&done, 1);
+        fail = 0;
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tbase = tslot;
+
+    if (tid == 0) {
+        const uint16_t *asrc = p.a + (size_t)tl * p.a_stride;
+        const uint16_t *bsrc = p.w + g.w_off[T.a] + (size_t)nchunk * nK * S * OZ_B_BLK;
+        int issued = 0;  // chunks whose copies were issued
+        auto load = [&](int kc) {
+            unsigned char *st = smraw + (size_t)(kc % OZ_ST) * stage_bytes;
+            mbar_expect_tx(&full[kc % OZ_ST], stage_bytes);
+            bulk_g2s(st, asrc + (size_t)kc * S * OZ_A_BLK, a_bytes, &full[kc % OZ_ST]);
+            bulk_g2s(st + a_bytes, bsrc + (size_t)kc * S * OZ_B_BLK, b_bytes, &full[kc % OZ_ST]);
+            ++issued;
+        };
+        for (int kc = 0; kc < OZ_ST && kc < nK; ++kc) load(kc);
+        const uint32_t idesc = tc::make_idesc_bf16(DP_OZ_TILE, DP_OZ_NC);
+        int consumed = 0;
+        bool ok = true;
+        for (int kc = 0; kc < nK; ++kc) {
+            const int st = kc % OZ_ST;
+            if (!tc::mbar_wait(&full[st], (kc / OZ_ST) & 1)) {
+                ok = false;
+                break;
+            }
+            ++consumed;
+            const uint32_t abase = tc::smem_u32(smraw + (size_t)st * stage_bytes);
+            const uint32_t bbase = abase + a_bytes;
+            for (int s = 1; s <= S; ++s) {
+                const uint64_t ad = tc::make_desc(abase + (uint32_t)(s - 1) * OZ_A_BLK * 2, 128, 256);
+                for (int t = 1; t + s <= S + 1; ++t) {
+                    const uint64_t bd = tc::make_desc(bbase + (uint32_t)(t - 1) * OZ_B_BLK * 2, 128, 256);
+                    tc::mma_bf16(tbase + (uint32_t)(s + t - 2) * DP_OZ_NC, ad, bd, idesc, kc > 0 || s > 1);
+                }
+            }
+            tc::mma_commit(&empty[st]);
+            // refill the stage of the previous chunk once its MMAs are done
+            if (kc >= 1 && kc - 1 + OZ_ST < nK) {
+                const int ps = (kc - 1) % OZ_ST;
+                if (!tc::mbar_wait(&empty[ps], ((kc - 1) / OZ_ST) & 1)) {
+                    ok = false;
+                    break;
+                }
+                load(kc - 1 + OZ_ST);
+            }
+        }
+        tc::mma_commit(&done);
+        if (!ok) {
+            fail = 1;
+            atomicOr(p.status, DPF_MMA_TIMEOUT);
+            // copies still in flight must land before the CTA leaves
+            for (int kc = consumed; kc < issued; ++kc) tc::mbar_wait(&full[kc % OZ_ST], (kc / OZ_ST) & 1);
+        }
+    }
+    const bool waited = tc::mbar_wait(&done, 0);
+    const bool bad = __syncthreads_or(!waited) || fail;
+    tc::fence_after_sync();
+    if (bad) {
+        if (tid == 0) atomicOr(p.status, DPF_MMA_TIMEOUT);
+    } else {
+        const int r = tid;
+        const int i = r < T.cnt ? p.type_perm[T.first + r] : -1;
+        const uint32_t tl_lane = tbase + ((uint32_t)(32 * warp) << 16);
+        double y[DP_OZ_NC];
+#pragma unroll
+        for (int n = 0; n < DP_OZ_NC; ++n) y[n] = 0.0;
+        // groups from the smallest scale up
+        for (int gg = S + 1; gg >= 2; --gg) {
+            float v0[16], v1[16];
+            tc::tmem_ld16(tl_lane + (uint32_t)(gg - 2) * DP_OZ_NC, v0);
+            tc::tmem_ld16(tl_lane + (uint32_t)(gg - 2) * DP_OZ_NC + 16, v1);
+            const double c = oz_pow2(-g.beta * gg);
+#pragma unroll
+            for (int n = 0; n < 16; ++n) {
+                y[n] = fma((double)v0[n], c, y[n]);
+                y[16 + n] = fma((double)v1[n], c, y[16 + n]);
+            }
+        }
+        if (i >= 0) {
+            const int er = p.aexp[(size_t)tl * DP_OZ_TILE + r];
+            const int32_t *fe = p.wexp + g.e_off[T.a] + (size_t)nchunk * DP_OZ_NC;
+            const int n0 = nchunk * DP_OZ_NC;
+            double *ho = p.hout + (size_t)i * p.ldo;
+            if (p.epi == 0) {
+                const double *b = p.bias[T.a];
+                const double *hi = p.hin + (size_t)i * p.ldh;
+                double *to = p.tout + (size_t)i * p.ldo;
+#pragma unroll
+                for (int n = 0; n < DP_OZ_NC; ++n) {
+                    const int col = n0 + n;
+                    if (col < g.N) {
+                        const double z = ldexp(y[n], er + fe[n]) + b[col];
+                        const double t = dp_tanh64(z, p.tanh_tab);
+                        const double sk =
+                            p.skip == 2 ? hi[col % p.skip_in] : (p.skip == 1 ? hi[col] : 0.0);
+                        to[col] = t;
+                        ho[col] = sk + t;
+                    }
+                }
+            } else {
+                const double *gh = p.gbc[T.a] != nullptr ? p.gbc[T.a] : p.hin + (size_t)i * p.ldh;
+#pragma unroll
+                for (int n = 0; n < DP_OZ_NC; ++n) {
+                    const int q = n0 + n;
+                    if (q < g.N) {
+                        double v = ldexp(y[n], er + fe[n]);
+                        if (p.skip == 1) v += gh[q];
+                        else if (p.skip == 2) v += gh[q] + gh[q + p.skip_in];
+                        ho[q] = v;
+                    }
+                }
+            }
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tbase, 512);
+}
+
+// digit width and count for a contraction of length K
+void oz_beta(int K, int &beta, int &S)
+{
+    for (beta = 7; beta >= 4; --beta) {
+        S = (55 + beta - 1) / beta;
+        const double bound = (double)K * std::pow(4.0, beta - 1) * (S + 2);
+        if (bound < 16777216.0) return;
+    }
+    beta = 0;
+    S = 0;
+}
+
+size_t gemm_smem(int S) { return (size_t)OZ_ST * S * (OZ_A_BLK + OZ_B_BLK) * 2; }
+
+}  // namespace
+
+bool dp_oz_plan(const DevModel &m, OzModel &oz, int64_t &w_elems, int64_t &e_elems)
+{
+    std::memset(&oz, 0, sizeof(oz));
+    const int nf = m.n_fit;
+    if (nf < 1 || nf > DP_MAX_LAYERS) return false;
+    int kin = m.m2 * m.M;
+    int fmax = 0, in_w = 0;
+    w_elems = 0;
+    e_elems = 0;
+    for (int l = 0; l < nf; ++l) {
+        const int F = m.fit[l];
+        if (F > DP_MAX_FIT_W) return false;
+        fmax = std::max(fmax, F);
+        OzGemm *gs[2] = {&oz.fwd[l], &oz.bwd[l]};
+        const int Ks[2] = {kin, F}, Ns[2] = {F, kin};
+        for (int d = 0; d < 2; ++d) {
+            OzGemm &g = *gs[d];
+            g.K = Ks[d];
+            g.N = Ns[d];
+            g.nK = (g.K + DP_OZ_KC - 1) / DP_OZ_KC;
+            g.nN = (g.N + DP_OZ_NC - 1) / DP_OZ_NC;
+            oz_beta(g.K, g.beta, g.S);
+            if (g.beta == 0 || g.S * DP_OZ_NC > 512 || gemm_smem(g.S) > 200 * 1024) return false;
+            in_w = std::max(in_w, g.nK * g.S * OZ_A_BLK);
+            for (int a = 0; a < m.ntypes; ++a) {
+                g.w_off[a] = w_elems;
+                w_elems += (int64_t)g.nN * g.nK * g.S * OZ_B_BLK;
+                g.e_off[a] = e_elems;
+                e_elems += (int64_t)g.nN * DP_OZ_NC;
+            }
+        }
+        kin = F;
+    }
+    oz.in_w = in_w;
+    oz.fmax = fmax;
+    oz.ok = 1;
+    return true;
+}
+
+void dp_oz_split_weights(const DevModel &m, const double *h_params, const OzModel &oz, uint16_t *w, int32_t *e)
+{
+    const int nf = m.n_fit;
+    for (int a = 0; a < m.ntypes; ++a) {
+        const double *W = h_params + m.fit_base[a];
+        int kin = m.m2 * m.M;
+        for (int l = 0; l < nf; ++l) {
+            const int F = m.fit[l];
+            // element (k, n) of W_l is W[k * F + n]; the forward GEMM's B operand is
+            // B[n][k] = W[k][n] (columns n), the backward's is B[q][n] = W[q][n] (rows q)
+            for (int d = 0; d < 2; ++d) {
+                const OzGemm &g = d == 0 ? oz.fwd[l] : oz.bwd[l];
+                auto elem = [&](int row, int k) -> double {  // B[row][k]
+                    if (d == 0) return (k < kin && row < F) ? W[(size_t)k * F + row] : 0.0;
+                    return (k < F && row < kin) ? W[(size_t)row * F + k] : 0.0;
+                };
+                const int Np = g.nN * DP_OZ_NC, Kp = g.nK * DP_OZ_KC;
+                for (int row = 0; row < Np; ++row) {
+                    double mx = 0.0;
+                    for (int k = 0; k < Kp; ++k) mx = std::max(mx, std::fabs(elem(row, k)));
+                    int ex = 0;
+                    bool zero = !(mx > 0.0);
+                    if (!zero) {
+                        std::frexp(mx, &ex);
+                        if (ex < g.beta * g.S - 1020) zero = true;
+                    }
+                    if (zero) ex = 0;
+                    e[g.e_off[a] + row] = ex;
+                    const double scale = zero ? 0.0 : std::ldexp(1.0, g.beta * g.S - ex);
+                    const int nc = row / DP_OZ_NC, rl = row % DP_OZ_NC;
+                    for (int k = 0; k < Kp; ++k) {
+                        long long I = std::llrint(elem(row, k) * scale);
+                        const int kc = k / DP_OZ_KC;
+                        uint16_t *blk = w + g.w_off[a] + ((size_t)nc * g.nK + kc) * g.S * OZ_B_BLK;
+                        for (int s = g.S - 1; s >= 0; --s) {
+                            const int dg = s > 0 ? oz_digit_step(I, g.beta) : (int)I;
+                            blk[(size_t)s * OZ_B_BLK + oz_kofs(rl, k % DP_OZ_KC)] = oz_bf16_int(dg);
+                        }
+                    }
+                }
+            }
+            W += (size_t)kin * F + F;
+            kin = F;
+        }
+    }
+}
+
+cudaError_t dp_launch_fit_oz(cudaStream_t st, const DevModel &m, const OzModel &oz, const OzBuffers &ob, int N,
+                             const NlistBuffers &nb, EvalBuffers eb, int32_t *status, int64_t *launches)
+{
+    const int nf = m.n_fit, T = m.ntypes;
+    const int tiles = (N + DP_OZ_TILE - 1) / DP_OZ_TILE + T;
+    if (tiles > ob.tiles) return cudaErrorInvalidValue;
+    static size_t configured = 0;
+    {
+        size_t need = 0;
+        for (int l = 0; l < nf; ++l) need = std::max(need, std::max(gemm_smem(oz.fwd[l].S), gemm_smem(oz.bwd[l].S)));
+        if (need > configured) {
+            cudaError_t e = cudaFuncSetAttribute(k_oz_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need);
+            if (e != cudaSuccess) return e;
+            configured = need;
+        }
+    }
+    const int K1 = m.m2 * m.M;
+    const size_t plane = (size_t)ob.nmax * oz.fmax;
+    double *H[2] = {ob.h, ob.h + plane};
+    double *G[2] = {ob.g, ob.g + plane};
+    // parameter offsets of layer l (W_l, b_l) and of the output layer inside a type's block
+    int64_t boff[DP_MAX_LAYERS], wo_off = 0;
+    {
+        int64_t off = 0;
+        int kin = K1;
+        for (int l = 0; l < nf; ++l) {
+            off += (int64_t)kin * m.fit[l];
+            boff[l] = off;
+            off += m.fit[l];
+            kin = m.fit[l];
+        }
+        wo_off = off;
+    }
+    const int split_blocks = tiles * DP_OZ_TILE * 32 / 256;
+
+    auto split = [&](int mode, const double *src, int lds, const double *tv, const OzGemm &g) -> cudaError_t {
+        OzSplitArgs a;
+        std::memset(&a, 0, sizeof(a));
+        a.mode = mode;
+        a.src = src;
+        a.lds = lds;
+        a.tv = tv;
+        a.ldt = oz.fmax;
+        for (int t = 0; t < T; ++t) {
+            a.wout[t] = m.params + m.fit_base[t] + wo_off;
+            a.bout[t] = m.params + m.fit_base[t] + wo_off + m.fit[nf - 1];
+        }
+        a.Ei = eb.Ei;
+        a.K = g.K;
+        a.nK = g.nK;
+        a.beta = g.beta;
+        a.S = g.S;
+        a.type_perm = nb.type_perm;
+        a.type_start = nb.type_start;
+        a.ntypes = T;
+        a.a = ob.a;
+        a.aexp = ob.aexp;
+        a.a_stride = ob.a_stride;
+        k_oz_split<<<split_blocks, 256, 0, st>>>(a);
+        *launches += 1;
+        return cudaGetLastError();
+    };
+    auto gemm = [&](const OzGemm &g, int epi, int skip, int skip_in, int l, const double *hin, int ldh,
+                    bool bcast_wout, double *tout, double *hout, int ldo) -> cudaError_t {
+        OzGemmArgs a;
+        std::memset(&a, 0, sizeof(a));
+        a.a = ob.a;
+        a.aexp = ob.aexp;
+        a.a_stride = ob.a_stride;
+        a.w = oz.w;
+        a.wexp = oz.wexp;
+        a.g = g;
+        a.type_perm = nb.type_perm;
+        a.type_start = nb.type_start;
+        a.ntypes = T;
+        a.epi = epi;
+        a.skip = skip;
+        a.skip_in = skip_in;
+        for (int t = 0; t < T; ++t) {
+            a.bias[t] = m.params + m.fit_base[t] + boff[l];
+            a.gbc[t] = bcast_wout ? m.params + m.fit_base[t] + wo_off : nullptr;
+        }
+        a.hin = hin;
+        a.ldh = ldh;
+        a.tout = tout;
+        a.hout = hout;
+        a.ldo = ldo;
+        a.tanh_tab = m.tanh_tab;
+        a.status = status;
+        k_oz_gemm<<<tiles * g.nN, DP_OZ_TILE, gemm_smem(g.S), st>>>(a);
+        *launches += 1;
+        return cudaGetLastError();
+    };
+
+    cudaError_t e;
+    // forward: h_l = skip(h_{l-1}) + tanh(h_{l-1} W_l + b_l), h_{-1} = D
+    int kin = K1;
+    for (int l = 0; l < nf; ++l) {
+        const double *x = l == 0 ? eb.D : H[(l - 1) & 1];
+        const int ldx = l == 0 ? K1 : oz.fmax;
+        if ((e = split(0, x, ldx, nullptr, oz.fwd[l])) != cudaSuccess) return e;
+        if ((e = gemm(oz.fwd[l], 0, dp_skip_kind(kin, m.fit[l]), kin, l, x, ldx, false,
+                      ob.t + (size_t)l * plane, H[l & 1], oz.fmax)) != cudaSuccess)
+            return e;
+        kin = m.fit[l];
+    }
+    // output layer (E_i) and dL/dz of the last layer (dL/dh = w_out)
+    if ((e = split(2, H[(nf - 1) & 1], oz.fmax, ob.t + (size_t)(nf - 1) * plane, oz.bwd[nf - 1])) != cudaSuccess)
+        return e;
+    // backward: dL/dh_{l-1} = (dL/dz_l) W_l^T + skip'(dL/dh_l)
+    for (int l = nf - 1; l >= 0; --l) {
+        const int kin_l = l == 0 ? K1 : m.fit[l - 1];
+        const bool last = l == nf - 1;
+        double *out = l == 0 ? eb.gD : G[(l - 1) & 1];
+        const int ldo = l == 0 ? K1 : oz.fmax;
+        if ((e = gemm(oz.bwd[l], 1, dp_skip_kind(kin_l, m.fit[l]), kin_l, l, last ? nullptr : G[l & 1], oz.fmax,
+                      last, nullptr, out, ldo)) != cudaSuccess)
+            return e;
+        if (l > 0)
+            if ((e = split(1, G[(l - 1) & 1], oz.fmax, ob.t + (size_t)(l - 1) * plane, oz.bwd[l - 1])) != cudaSuccess)
+                return e;
+    }
+    return cudaSuccess;
+}

@@ -27,6 +27,7 @@ STATUS_NAMES = {
 globals().update({name: code for code, name in STATUS_NAMES.items()})
 DP_PREC_FP64 = 0
 DP_PREC_MIXED = 1
+DP_PREC_FP64_SIMT = 2
 
 
 class DPError(RuntimeError):

@@ -54,10 +54,10 @@ def oracle_nlist(oracle, w, desc, skin):
     return nl, nr
 
 
-def gpu_run(dp, desc, P, w, skin=0.0, cand_cap=0):
+def gpu_run(dp, desc, P, w, skin=0.0, cand_cap=0, precision=None):
     N = len(w["coords"])
     model = dp.Model(desc, P)
-    ctx = dp.Context(model, N, cand_cap=cand_cap)
+    ctx = dp.Context(model, N, cand_cap=cand_cap, precision=dp.DP_PREC_FP64 if precision is None else precision)
     x = torch.tensor(w["coords"], dtype=torch.float64, device="cuda")
     t = torch.tensor(w["types"], dtype=torch.int32, device="cuda")
     dp.dp_build_nlist(ctx, x, t, w["box"], skin)
@@ -83,11 +83,16 @@ def test_format_bit_exact(dp, oracle, synth, name):
 
 
 @pytest.mark.parametrize("name", ["water192", "water648", "cu864"])
-def test_eval_parity(dp, oracle, synth, name):
+@pytest.mark.parametrize("fit", ["tensor", "simt"])
+def test_eval_parity(dp, oracle, synth, name, fit):
+    """FP64 modes: the fitting net's GEMMs on the tensor cores by exact
+    splitting (DP_PREC_FP64) and on the FP64 units (DP_PREC_FP64_SIMT)."""
     w, d, P, o = oracle_eval(oracle, synth, name)
-    model, ctx, x, t = gpu_run(dp, d, P, w)
+    prec = dp.DP_PREC_FP64 if fit == "tensor" else dp.DP_PREC_FP64_SIMT
+    model, ctx, x, t = gpu_run(dp, d, P, w, precision=prec)
     g = dp.dp_eval(ctx, x, t, w["box"], want_atom_energy=True)
     eE, eF, eV = rel_errors(g, o)
+    print(f"{name} {fit}: E {eE:.2e} F {eF:.2e} V {eV:.2e}")
     assert eE < TOL and eF < TOL and eV < TOL, (eE, eF, eV)
     ea = np.abs(g["atom_energy"].cpu().numpy() - o["atom_energy"]).max() / np.abs(o["atom_energy"]).max()
     assert ea < TOL
@@ -334,3 +339,16 @@ def test_fp64_tanh_accuracy(dp):
     assert np.all(y[z] == 0.0) and np.array_equal(np.signbit(y[z]), np.signbit(x[z]))
     nan = dp.dp_tanh_f64(torch.tensor([float("nan")], dtype=torch.float64, device="cuda")).cpu().numpy()
     assert np.isnan(nan[0])
+
+
+def test_set_params_refreshes_fp64_contexts(dp, oracle, synth):
+    """After dp_model_set_params an existing FP64 context evaluates the new
+    parameters (the tensor-core fitting net re-makes its weight digits)."""
+    w, d, P, o = oracle_eval(oracle, synth, "water192")
+    model, ctx, x, t = gpu_run(dp, d, P, w)
+    dp.dp_eval(ctx, x, t, w["box"])
+    P2 = synth.model_params(d, 5)
+    model.set_params(P2)
+    g = dp.dp_eval(ctx, x, t, w["box"])
+    o2 = oracle.evaluate(d, P2, w["coords"], w["types"], w["box"])
+    assert max(rel_errors(g, o2)) < TOL

@@ -41,7 +41,7 @@
 
 namespace {
 
-constexpr int OZ_ST = 3;                    // pipeline stages
+constexpr int OZ_STMAX = 4;                 // pipeline stages (at most)
 constexpr int OZ_A_BLK = DP_OZ_TILE * DP_OZ_KC;  // elements of one A digit chunk (128 x 16)
 constexpr int OZ_B_BLK = DP_OZ_NC * DP_OZ_KC;    // elements of one W digit chunk (32 x 16)
 
@@ -133,103 +133,89 @@ struct OzSplitArgs {
     int64_t a_stride;
 };
 
+// One warp per group of 8 rows of a tile (a row group of the canonical
+// layout), so that every digit plane of a 16-column chunk is written as one
+// contiguous 256-byte block: lane = row (0..7) + 8 * (column half) + 16 *
+// (chunk parity).
 __global__ void __launch_bounds__(256) k_oz_split(OzSplitArgs p)
 {
     const int lane = threadIdx.x & 31;
     const int gw = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
-    const int tl = gw / DP_OZ_TILE, r = gw % DP_OZ_TILE;
+    const int tl = gw / (DP_OZ_TILE / 8), r0 = (gw % (DP_OZ_TILE / 8)) * 8;
     const TileRef T = oz_tile(tl, p.type_start, p.ntypes);
     if (T.a < 0) return;
-    const int i = r < T.cnt ? p.type_perm[T.first + r] : -1;
     const int Kp = p.nK * DP_OZ_KC;
-    const double *srow = i >= 0 ? p.src + (size_t)i * p.lds : nullptr;
-    const double *trow = (i >= 0 && p.mode != 0) ? p.tv + (size_t)i * p.ldt : nullptr;
     const double *wo = p.mode == 2 ? p.wout[T.a] : nullptr;
+    const int bS = p.beta * p.S;
 
-    // the 8 values of columns k8 .. k8+7
-    auto load8 = [&](int k8, double (&v)[8]) {
-#pragma unroll
-        for (int q = 0; q < 8; ++q) v[q] = 0.0;
-        if (i < 0 || k8 >= p.K) return;
-        if (k8 + 8 <= p.K && (p.mode == 2 || (p.lds & 1) == 0)) {
-            if (p.mode == 2) {
-#pragma unroll
-                for (int q = 0; q < 8; ++q) v[q] = wo[k8 + q];
-            } else {
-                const double2 *s2 = reinterpret_cast<const double2 *>(srow + k8);
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const double2 u = s2[q];
-                    v[2 * q] = u.x;
-                    v[2 * q + 1] = u.y;
-                }
-            }
-        } else {
-            for (int q = 0; q < 8 && k8 + q < p.K; ++q) v[q] = p.mode == 2 ? wo[k8 + q] : srow[k8 + q];
-        }
+    // value of column k of row r of the tile (0 past the row's end or the tile's atoms)
+    auto value = [&](int i, int k) -> double {
+        if (i < 0 || k >= p.K) return 0.0;
+        double v = p.mode == 2 ? wo[k] : p.src[(size_t)i * p.lds + k];
         if (p.mode != 0) {
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                if (k8 + q < p.K) {
-                    const double t = trow[k8 + q];
-                    v[q] *= fma(-t, t, 1.0);
-                }
-            }
+            const double t = p.tv[(size_t)i * p.ldt + k];
+            v *= fma(-t, t, 1.0);
         }
+        return v;
     };
 
-    // output layer energy: E_i = b_out + h . w_out (lane partials in k order, fixed shuffle tree)
-    if (p.mode == 2) {
-        double e = 0.0;
-        if (i >= 0)
-            for (int k = lane; k < p.K; k += 32) e = fma(srow[k], wo[k], e);
+    // per row: output-layer energy (mode 2) and exponent, lanes striding over k
+    int e_row = 0;  // lane j < 8 keeps the exponent of row r0 + j
+    double sc_row = 0.0;
+    for (int j = 0; j < 8; ++j) {
+        const int r = r0 + j;
+        const int i = r < T.cnt ? p.type_perm[T.first + r] : -1;
+        if (p.mode == 2) {
+            double e = 0.0;
+            if (i >= 0)
+                for (int k = lane; k < p.K; k += 32) e = fma(p.src[(size_t)i * p.lds + k], wo[k], e);
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
-        if (i >= 0 && lane == 0) p.Ei[i] = *p.bout[T.a] + e;
+            for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+            if (i >= 0 && lane == 0) p.Ei[i] = *p.bout[T.a] + e;
+        }
+        double mx = 0.0;
+        for (int k = lane; k < p.K; k += 32) mx = fmax(mx, fabs(value(i, k)));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        int e = 0;
+        bool zero = !(mx > 0.0);
+        if (!zero) {
+            frexp(mx, &e);
+            if (e < bS - 1020) zero = true;  // below 2^-960: a zero row
+        }
+        if (zero) e = 0;
+        if (lane == j) {
+            e_row = e;
+            sc_row = zero ? 0.0 : oz_pow2(bS - e);
+        }
     }
+    if (lane < 8) p.aexp[(size_t)tl * DP_OZ_TILE + r0 + lane] = e_row;
 
-    // row exponent: 2^e > max |x|
-    double mx = 0.0;
-    for (int k8 = lane * 8; k8 < Kp; k8 += 256) {
-        double v[8];
-        load8(k8, v);
-#pragma unroll
-        for (int q = 0; q < 8; ++q) mx = fmax(mx, fabs(v[q]));
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    int e = 0;
-    const int bS = p.beta * p.S;
-    bool zero = !(mx > 0.0);
-    if (!zero) {
-        frexp(mx, &e);
-        if (e < bS - 1020) zero = true;  // below 2^-960: a zero row
-    }
-    if (zero) e = 0;
-    if (lane == 0) p.aexp[(size_t)tl * DP_OZ_TILE + r] = e;
-    const double scale = zero ? 0.0 : oz_pow2(bS - e);
-
+    // digits: lane handles row r0 + (lane & 7), columns kh*8 .. kh*8+7 of chunk kc
+    const int jr = lane & 7, kh = (lane >> 3) & 1, cpar = lane >> 4;
+    const int r = r0 + jr;
+    const int i = r < T.cnt ? p.type_perm[T.first + r] : -1;
+    const double scale = __shfl_sync(0xffffffffu, sc_row, jr);
     uint16_t *out = p.a + (size_t)tl * p.a_stride;
-    for (int k8 = lane * 8; k8 < Kp; k8 += 256) {
-        double v[8];
-        load8(k8, v);
+    const int ofs = oz_kofs(r, kh * 8);
+    for (int kc = cpar; kc < p.nK; kc += 2) {
+        const int k8 = kc * DP_OZ_KC + kh * 8;
         long long I[8];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) I[q] = __double2ll_rn(v[q] * scale);
-        const int kc = k8 / DP_OZ_KC;
-        const int ofs = oz_kofs(r, k8 % DP_OZ_KC);
-        for (int s = p.S - 1; s >= 0; --s) {
+        for (int q = 0; q < 8; ++q) I[q] = __double2ll_rn(value(i, k8 + q) * scale);
+        for (int sd = p.S - 1; sd >= 0; --sd) {
             int d[8];
 #pragma unroll
-            for (int q = 0; q < 8; ++q) d[q] = s > 0 ? oz_digit_step(I[q], p.beta) : (int)I[q];
+            for (int q = 0; q < 8; ++q) d[q] = sd > 0 ? oz_digit_step(I[q], p.beta) : (int)I[q];
             uint4 u;
             u.x = (uint32_t)oz_bf16_int(d[0]) | ((uint32_t)oz_bf16_int(d[1]) << 16);
             u.y = (uint32_t)oz_bf16_int(d[2]) | ((uint32_t)oz_bf16_int(d[3]) << 16);
             u.z = (uint32_t)oz_bf16_int(d[4]) | ((uint32_t)oz_bf16_int(d[5]) << 16);
             u.w = (uint32_t)oz_bf16_int(d[6]) | ((uint32_t)oz_bf16_int(d[7]) << 16);
-            *reinterpret_cast<uint4 *>(out + ((size_t)kc * p.S + s) * OZ_A_BLK + ofs) = u;
+            *reinterpret_cast<uint4 *>(out + ((size_t)kc * p.S + sd) * OZ_A_BLK + ofs) = u;
         }
     }
+    (void)Kp;
 }
 
 // ------------------------------------------------------------------- gemm --
@@ -255,6 +241,8 @@ struct OzGemmArgs {
     int ldo;
     const double *tanh_tab;
     int32_t *status;
+    int nst;        // pipeline stages
+    uint32_t tcols; // tensor-memory columns allocated (S * 32 rounded up to 256 or 512)
 };
 
 __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *mbar)
@@ -272,10 +260,13 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t *mbar, uint32_t bytes)
                  : "memory");
 }
 
+template <int S>
 __global__ void __launch_bounds__(DP_OZ_TILE, 1) k_oz_gemm(OzGemmArgs p)
 {
     extern __shared__ __align__(1024) unsigned char smraw[];
-    __shared__ __align__(8) uint64_t full[OZ_ST], empty[OZ_ST], done;
+    __shared__ __align__(8) uint64_t full[OZ_STMAX], empty[OZ_STMAX], done;
+    __shared__ int fe_s[DP_OZ_NC];
+    __shared__ double bias_s[DP_OZ_NC];
     __shared__ uint32_t tslot;
     __shared__ int fail;
     const int tid = threadIdx.x, warp = tid >> 5;
@@ -284,13 +275,19 @@ __global__ void __launch_bounds__(DP_OZ_TILE, 1) k_oz_gemm(OzGemmArgs p)
     const TileRef T = oz_tile(blockIdx.x / g.nN, p.type_start, p.ntypes);
     if (T.a < 0) return;
     const int tl = blockIdx.x / g.nN;
-    const int S = g.S, nK = g.nK;
+    const int nK = g.nK;
     const uint32_t a_bytes = (uint32_t)S * OZ_A_BLK * 2, b_bytes = (uint32_t)S * OZ_B_BLK * 2;
     const uint32_t stage_bytes = a_bytes + b_bytes;
+    const int NST = p.nst;
 
-    if (warp == 0) tc::tmem_alloc(&tslot, 512);
+    if (warp == 0) tc::tmem_alloc(&tslot, p.tcols);
+    if (tid < DP_OZ_NC) {
+        const int col = nchunk * DP_OZ_NC + tid;
+        fe_s[tid] = p.wexp[g.e_off[T.a] + col];
+        bias_s[tid] = (p.epi == 0 && col < g.N) ? p.bias[T.a][col] : 0.0;
+    }
     if (tid == 0) {
-        for (int s = 0; s < OZ_ST; ++s) {
+        for (int s = 0; s < NST; ++s) {
             tc::mbar_init(&full[s], 1);
             tc::mbar_init(&empty[s], 1);
         }
@@ -307,41 +304,44 @@ __global__ void __launch_bounds__(DP_OZ_TILE, 1) k_oz_gemm(OzGemmArgs p)
         const uint16_t *bsrc = p.w + g.w_off[T.a] + (size_t)nchunk * nK * S * OZ_B_BLK;
         int issued = 0;  // chunks whose copies were issued
         auto load = [&](int kc) {
-            unsigned char *st = smraw + (size_t)(kc % OZ_ST) * stage_bytes;
-            mbar_expect_tx(&full[kc % OZ_ST], stage_bytes);
-            bulk_g2s(st, asrc + (size_t)kc * S * OZ_A_BLK, a_bytes, &full[kc % OZ_ST]);
-            bulk_g2s(st + a_bytes, bsrc + (size_t)kc * S * OZ_B_BLK, b_bytes, &full[kc % OZ_ST]);
+            unsigned char *st = smraw + (size_t)(kc % NST) * stage_bytes;
+            mbar_expect_tx(&full[kc % NST], stage_bytes);
+            bulk_g2s(st, asrc + (size_t)kc * S * OZ_A_BLK, a_bytes, &full[kc % NST]);
+            bulk_g2s(st + a_bytes, bsrc + (size_t)kc * S * OZ_B_BLK, b_bytes, &full[kc % NST]);
             ++issued;
         };
-        for (int kc = 0; kc < OZ_ST && kc < nK; ++kc) load(kc);
+        for (int kc = 0; kc < NST && kc < nK; ++kc) load(kc);
         const uint32_t idesc = tc::make_idesc_bf16(DP_OZ_TILE, DP_OZ_NC);
         int consumed = 0;
         bool ok = true;
         for (int kc = 0; kc < nK; ++kc) {
-            const int st = kc % OZ_ST;
-            if (!tc::mbar_wait(&full[st], (kc / OZ_ST) & 1)) {
+            const int st = kc % NST;
+            if (!tc::mbar_wait(&full[st], (kc / NST) & 1)) {
                 ok = false;
                 break;
             }
             ++consumed;
             const uint32_t abase = tc::smem_u32(smraw + (size_t)st * stage_bytes);
-            const uint32_t bbase = abase + a_bytes;
+            // descriptors of digit plane 1; plane s is (s - 1) blocks further (the
+            // address field holds bytes / 16 and stays below 2^14 inside shared memory)
+            const uint64_t ad0 = tc::make_desc(abase, 128, 256);
+            const uint64_t bd0 = tc::make_desc(abase + a_bytes, 128, 256);
+#pragma unroll
             for (int s = 1; s <= S; ++s) {
-                const uint64_t ad = tc::make_desc(abase + (uint32_t)(s - 1) * OZ_A_BLK * 2, 128, 256);
-                for (int t = 1; t + s <= S + 1; ++t) {
-                    const uint64_t bd = tc::make_desc(bbase + (uint32_t)(t - 1) * OZ_B_BLK * 2, 128, 256);
-                    tc::mma_bf16(tbase + (uint32_t)(s + t - 2) * DP_OZ_NC, ad, bd, idesc, kc > 0 || s > 1);
-                }
+#pragma unroll
+                for (int t = 1; t + s <= S + 1; ++t)
+                    tc::mma_bf16(tbase + (uint32_t)(s + t - 2) * DP_OZ_NC, ad0 + (uint64_t)((s - 1) * OZ_A_BLK * 2 / 16),
+                                 bd0 + (uint64_t)((t - 1) * OZ_B_BLK * 2 / 16), idesc, kc > 0 || s > 1);
             }
             tc::mma_commit(&empty[st]);
             // refill the stage of the previous chunk once its MMAs are done
-            if (kc >= 1 && kc - 1 + OZ_ST < nK) {
-                const int ps = (kc - 1) % OZ_ST;
-                if (!tc::mbar_wait(&empty[ps], ((kc - 1) / OZ_ST) & 1)) {
+            if (kc >= 1 && kc - 1 + NST < nK) {
+                const int ps = (kc - 1) % NST;
+                if (!tc::mbar_wait(&empty[ps], ((kc - 1) / NST) & 1)) {
                     ok = false;
                     break;
                 }
-                load(kc - 1 + OZ_ST);
+                load(kc - 1 + NST);
             }
         }
         tc::mma_commit(&done);
@@ -349,7 +349,7 @@ __global__ void __launch_bounds__(DP_OZ_TILE, 1) k_oz_gemm(OzGemmArgs p)
             fail = 1;
             atomicOr(p.status, DPF_MMA_TIMEOUT);
             // copies still in flight must land before the CTA leaves
-            for (int kc = consumed; kc < issued; ++kc) tc::mbar_wait(&full[kc % OZ_ST], (kc / OZ_ST) & 1);
+            for (int kc = consumed; kc < issued; ++kc) tc::mbar_wait(&full[kc % NST], (kc / NST) & 1);
         }
     }
     const bool waited = tc::mbar_wait(&done, 0);
@@ -378,18 +378,17 @@ __global__ void __launch_bounds__(DP_OZ_TILE, 1) k_oz_gemm(OzGemmArgs p)
         }
         if (i >= 0) {
             const int er = p.aexp[(size_t)tl * DP_OZ_TILE + r];
-            const int32_t *fe = p.wexp + g.e_off[T.a] + (size_t)nchunk * DP_OZ_NC;
+            const int *fe = fe_s;
             const int n0 = nchunk * DP_OZ_NC;
             double *ho = p.hout + (size_t)i * p.ldo;
             if (p.epi == 0) {
-                const double *b = p.bias[T.a];
                 const double *hi = p.hin + (size_t)i * p.ldh;
                 double *to = p.tout + (size_t)i * p.ldo;
 #pragma unroll
                 for (int n = 0; n < DP_OZ_NC; ++n) {
                     const int col = n0 + n;
                     if (col < g.N) {
-                        const double z = ldexp(y[n], er + fe[n]) + b[col];
+                        const double z = ldexp(y[n], er + fe[n]) + bias_s[n];
                         const double t = dp_tanh64(z, p.tanh_tab);
                         const double sk =
                             p.skip == 2 ? hi[col % p.skip_in] : (p.skip == 1 ? hi[col] : 0.0);
@@ -414,7 +413,7 @@ __global__ void __launch_bounds__(DP_OZ_TILE, 1) k_oz_gemm(OzGemmArgs p)
     }
     tc::fence_before_sync();
     __syncthreads();
-    if (warp == 0) tc::tmem_dealloc(tbase, 512);
+    if (warp == 0) tc::tmem_dealloc(tbase, p.tcols);
 }
 
 // digit width and count for a contraction of length K
@@ -429,7 +428,16 @@ void oz_beta(int K, int &beta, int &S)
     S = 0;
 }
 
-size_t gemm_smem(int S) { return (size_t)OZ_ST * S * (OZ_A_BLK + OZ_B_BLK) * 2; }
+// Up to 8 digits: 2 stages and 256 tensor-memory columns, so two CTAs share an
+// SM (one's epilogue overlaps the other's MMAs); more digits: 4 stages, one CTA.
+int gemm_stages(int S)
+{
+    if (S <= 8) return 2;
+    const int fit = (int)((225 * 1024) / ((size_t)S * (OZ_A_BLK + OZ_B_BLK) * 2));
+    return fit < OZ_STMAX ? fit : OZ_STMAX;
+}
+uint32_t gemm_tcols(int S) { return S * DP_OZ_NC <= 256 ? 256u : 512u; }
+size_t gemm_smem(int S) { return (size_t)gemm_stages(S) * S * (OZ_A_BLK + OZ_B_BLK) * 2; }
 
 }  // namespace
 
@@ -455,7 +463,7 @@ bool dp_oz_plan(const DevModel &m, OzModel &oz, int64_t &w_elems, int64_t &e_ele
             g.nK = (g.K + DP_OZ_KC - 1) / DP_OZ_KC;
             g.nN = (g.N + DP_OZ_NC - 1) / DP_OZ_NC;
             oz_beta(g.K, g.beta, g.S);
-            if (g.beta == 0 || g.S * DP_OZ_NC > 512 || gemm_smem(g.S) > 200 * 1024) return false;
+            if (g.beta == 0 || g.S * DP_OZ_NC > 512 || gemm_smem(g.S) > 225 * 1024) return false;
             in_w = std::max(in_w, g.nK * g.S * OZ_A_BLK);
             for (int a = 0; a < m.ntypes; ++a) {
                 g.w_off[a] = w_elems;
@@ -530,7 +538,13 @@ cudaError_t dp_launch_fit_oz(cudaStream_t st, const DevModel &m, const OzModel &
         size_t need = 0;
         for (int l = 0; l < nf; ++l) need = std::max(need, std::max(gemm_smem(oz.fwd[l].S), gemm_smem(oz.bwd[l].S)));
         if (need > configured) {
-            cudaError_t e = cudaFuncSetAttribute(k_oz_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need);
+            cudaError_t e = cudaFuncSetAttribute(k_oz_gemm<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need);
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(k_oz_gemm<10>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need);
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(k_oz_gemm<11>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need);
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(k_oz_gemm<14>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need);
             if (e != cudaSuccess) return e;
             configured = need;
         }
@@ -552,7 +566,7 @@ cudaError_t dp_launch_fit_oz(cudaStream_t st, const DevModel &m, const OzModel &
         }
         wo_off = off;
     }
-    const int split_blocks = tiles * DP_OZ_TILE * 32 / 256;
+    const int split_blocks = (tiles * (DP_OZ_TILE / 8) * 32 + 255) / 256;
 
     auto split = [&](int mode, const double *src, int lds, const double *tv, const OzGemm &g) -> cudaError_t {
         OzSplitArgs a;
@@ -608,7 +622,15 @@ cudaError_t dp_launch_fit_oz(cudaStream_t st, const DevModel &m, const OzModel &
         a.ldo = ldo;
         a.tanh_tab = m.tanh_tab;
         a.status = status;
-        k_oz_gemm<<<tiles * g.nN, DP_OZ_TILE, gemm_smem(g.S), st>>>(a);
+        a.nst = gemm_stages(g.S);
+        a.tcols = gemm_tcols(g.S);
+        const size_t smem = gemm_smem(g.S);
+        switch (g.S) {
+        case 8: k_oz_gemm<8><<<tiles * g.nN, DP_OZ_TILE, smem, st>>>(a); break;
+        case 10: k_oz_gemm<10><<<tiles * g.nN, DP_OZ_TILE, smem, st>>>(a); break;
+        case 11: k_oz_gemm<11><<<tiles * g.nN, DP_OZ_TILE, smem, st>>>(a); break;
+        default: k_oz_gemm<14><<<tiles * g.nN, DP_OZ_TILE, smem, st>>>(a); break;
+        }
         *launches += 1;
         return cudaGetLastError();
     };

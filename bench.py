@@ -35,6 +35,8 @@ import numpy as np  # noqa: E402
 METRIC = "atom-steps/s"
 MD_PER_STEP = 10
 DT_FS = 0.5
+# MD conditions per workload: (dt in fs, T0 in K); the copper box runs at 1 fs and 330 K
+MD_CONDITIONS = {"cu32000": (1.0, 330.0)}
 SKIN = 2.0
 T0 = 300.0
 L2_BYTES = 129 * 1024 * 1024
@@ -340,7 +342,7 @@ def measure_mode(args, dp, w, run_desc, run_P, judge_model, v0, dev, world, flus
     etot = th_all[:, 0] + th_all[:, 1]
     return {"value": world * N * MD_PER_STEP * args.steps / (total_ms / 1000.0), "unit": METRIC,
             "ms_per_step": total_ms / args.steps, "dtype": dtype,
-            "model": "se_a water %s / M2 %d / fit %s" % ("-".join(map(str, run_desc["emb"])), run_desc["m2"],
+            "model": "se_a %s / M2 %d / fit %s" % ("-".join(map(str, run_desc["emb"])), run_desc["m2"],
                                                         "x".join(map(str, run_desc["fit"]))),
             "kernels_ms_per_step": {g: d["ms"] / args.steps for g, d in groups.items()},
             "roofline": roof,
@@ -505,7 +507,9 @@ def run_ours(args, rank, world, local_rank):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": args.workload, "atoms": N, "md_steps_per_step": MD_PER_STEP, "dt_fs": DT_FS,
                        "skin": SKIN, "rebuild_every": MD_PER_STEP, "T0_K": T0,
-                       "model": "se_a water 25-50-100 / M2 16 / fit 240x3, seeded FP64 weights",
+                       "model": "se_a %s %s / M2 %d / fit %s, seeded FP64 weights" % (
+                           "copper" if desc["ntypes"] == 1 else "water", "-".join(map(str, desc["emb"])), desc["m2"],
+                           "x".join(map(str, desc["fit"]))),
                        "l2": "flushed between steps (256 MB write)",
                        "parallelism": f"replicas x{world}"},
             "gpu_launches": launches,
@@ -548,7 +552,9 @@ def profile_eval(args):
 
 
 def main():
+    global DT_FS, T0
     args = parse()
+    DT_FS, T0 = MD_CONDITIONS.get(args.workload, (DT_FS, T0))
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

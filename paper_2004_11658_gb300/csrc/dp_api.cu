@@ -146,7 +146,7 @@ struct dp_ctx {
     // mixed precision: BF16 / FP32 copies of the parameters
     MixedModel mx;
     float *d_p32;
-    unsigned char *d_emb_ops, *d_fit_fwd, *d_fit_bwd;
+    unsigned char *d_emb_ops, *d_fit_fwd, *d_fit_bwd, *d_dtile;
     bool md_force_valid;
     int64_t md_N;
     int64_t md_step;
@@ -754,7 +754,7 @@ void dp_ctx_free(dp_ctx *c)
                     c->d_energy, c->d_virial, c->md_force, c->ke_part, c->d_inv_mass_conv, c->d_mass,
                     c->eb.fit_t, c->eb.fit_h, c->d_p32, c->d_emb_ops, c->d_fit_fwd, c->d_fit_bwd,
                     c->pb.dT, c->pb.dD, c->pb.Db, c->pb.dDb, c->pb.fit_scr, c->pb.rowscr, c->pb.slices,
-                    c->d_oz_w, c->d_oz_e, c->ob.a, c->ob.aexp, c->ob.t, c->ob.h, c->ob.g};
+                    c->d_oz_w, c->d_oz_e, c->ob.a, c->ob.aexp, c->ob.t, c->ob.h, c->ob.g, c->d_dtile};
     for (void *p : bufs) dev_free(p);
     delete c;
 }
@@ -833,6 +833,12 @@ dp_status dp_ctx_create(const dp_model *model, int64_t natoms_max, int32_t cand_
     }
 #undef ALLOC
     if (!s && precision == DP_PREC_MIXED) s = build_mixed(c);
+    if (!s && precision == DP_PREC_MIXED) {
+        // BF16 descriptor tiles of the fitting kernel: [tiles][K1p / 64][128 x 64]
+        const size_t tiles = (N + 127) / 128 + T;
+        s = dev_alloc(&c->d_dtile, tiles * (size_t)c->mx.fit_kp[0] * 128 * 2, "bf16 descriptor tiles");
+        c->mx.dtile = c->d_dtile;
+    }
     if (!s) {
         const double *tab = nullptr;
         cudaError_t e = dp_tanh_setup(&tab);

@@ -196,6 +196,7 @@ struct MixedModel {
     int fit_kp[DP_MAX_LAYERS];     // K_in,l padded to 64 (forward K)
     int fit_kinp[DP_MAX_LAYERS];   // K_in,l padded to 16 (MMA N, backward)
     int fit_fp[DP_MAX_LAYERS];     // F_l padded to 64 (backward K)
+    unsigned char *dtile;          // scratch: the descriptor in BF16, [tile][K1p/64][128 x 64] canonical
 };
 
 cudaError_t dp_launch_embed_fwd(cudaStream_t st, const DevModel &m, const double *x,

@@ -605,6 +605,57 @@ __global__ void __launch_bounds__(MXT, 1) k_embed_bwd_mx(
 // ----------------------------------------------------------------- fitting --
 
 constexpr int FIT_KC = 64;  // K per streamed chunk
+constexpr int FIT_NS = 3;   // pipeline stages
+
+__device__ __forceinline__ void bulk_g2s_mx(void *dst, const void *src, uint32_t bytes, uint64_t *mbar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+            tc::smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(tc::smem_u32(mbar))
+        : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx_mx(uint64_t *mbar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(tc::smem_u32(mbar)), "r"(bytes)
+                 : "memory");
+}
+
+// The descriptor D (FP64, [N][K1]) as BF16 tiles of the fitting kernel's A
+// operand: tile = 128 atoms of one type in type order, [K1p / 64] chunks of
+// 128 x 64 in the canonical K-major layout.  One warp per row of a tile.
+__global__ void __launch_bounds__(256) k_d2bf(const double *__restrict__ D, int K1, int nK,
+                                              const int32_t *__restrict__ type_perm,
+                                              const int32_t *__restrict__ type_start, int ntypes,
+                                              unsigned char *__restrict__ out)
+{
+    const int lane = threadIdx.x & 31;
+    const int gw = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+    int tl = gw / MXT;
+    const int r = gw % MXT;
+    int first = 0, cnt = -1;
+    for (int t = 0; t < ntypes; ++t) {
+        const int n_t = type_start[t + 1] - type_start[t];
+        const int tiles = (n_t + MXT - 1) / MXT;
+        if (tl < tiles) {
+            first = type_start[t] + tl * MXT;
+            cnt = min(MXT, n_t - tl * MXT);
+            break;
+        }
+        tl -= tiles;
+    }
+    if (cnt < 0) return;
+    const int i = r < cnt ? type_perm[first + r] : -1;
+    unsigned char *o = out + (size_t)(gw / MXT) * nK * (MXT * FIT_KC * 2);
+    for (int g8 = lane; g8 < nK * (FIT_KC / 8); g8 += 32) {
+        const int k0 = g8 * 8, kc = k0 / FIT_KC;
+        float v[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) v[q] = (i >= 0 && k0 + q < K1) ? (float)D[(size_t)i * K1 + k0 + q] : 0.f;
+        st8(o + (size_t)kc * (MXT * FIT_KC * 2), r, k0 % FIT_KC, FIT_KC, v);
+    }
+}
 
 // One CTA = one tile of up to 128 atoms of one type.
 __global__ void __launch_bounds__(MXT, 1) k_fit_mx(DevModel m, MixedModel mx, int N,
@@ -615,11 +666,12 @@ __global__ void __launch_bounds__(MXT, 1) k_fit_mx(DevModel m, MixedModel mx, in
                                                    float *__restrict__ hbuf, int32_t *status)
 {
     extern __shared__ __align__(1024) unsigned char smraw[];
-    unsigned char *Ab = smraw;                          // [2][128][64] bf16 (layer-1 input chunks)
-    unsigned char *Bb = Ab + 2 * MXT * FIT_KC * 2;      // [2][256][64] bf16 (weight chunks)
-    unsigned char *Hb = Bb + 2 * 256 * FIT_KC * 2;      // [128][256] bf16 (activation / gradient)
-    __shared__ __align__(8) uint64_t mbar[2];
+    unsigned char *Ab = smraw;                               // [FIT_NS][128][64] bf16 (layer-1 input chunks)
+    unsigned char *Bb = Ab + FIT_NS * MXT * FIT_KC * 2;      // [FIT_NS][256][64] bf16 (weight chunks)
+    unsigned char *Hb = Bb + FIT_NS * 256 * FIT_KC * 2;      // [128][256] bf16 (activation / gradient)
+    __shared__ __align__(8) uint64_t full[FIT_NS], empty[FIT_NS], dbar;
     __shared__ uint32_t tslot;
+    __shared__ int pfail;
     __shared__ int rows_atom[MXT];
     constexpr int HK = 256;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -627,6 +679,7 @@ __global__ void __launch_bounds__(MXT, 1) k_fit_mx(DevModel m, MixedModel mx, in
     const int M = m.M, K1 = m.m2 * M, nf = m.n_fit;
 
     int bid = blockIdx.x, a = -1, first = 0, cnt = 0;
+    const int tile_id = blockIdx.x;
     for (int t = 0; t < m.ntypes; ++t) {
         const int n_t = type_start[t + 1] - type_start[t];
         const int tiles = (n_t + MXT - 1) / MXT;
@@ -641,68 +694,94 @@ __global__ void __launch_bounds__(MXT, 1) k_fit_mx(DevModel m, MixedModel mx, in
     if (a < 0) return;
     if (warp == 0) tc::tmem_alloc(&tslot, 256);
     if (tid == 0) {
-        tc::mbar_init(&mbar[0], 1);
-        tc::mbar_init(&mbar[1], 1);
+        for (int q = 0; q < FIT_NS; ++q) {
+            tc::mbar_init(&full[q], 1);
+            tc::mbar_init(&empty[q], 1);
+        }
+        tc::mbar_init(&dbar, 1);
+        pfail = 0;
     }
+    int ctr = 0;         // chunks issued so far (thread 0)
+    uint32_t dph = 0;    // parity of the next completion of dbar
     rows_atom[tid] = tid < cnt ? type_perm[first + tid] : -1;
     tc_sync();
     const uint32_t tbase = tslot;
     const uint32_t tlane = tbase + ((uint32_t)(32 * warp) << 16);
     const int my = rows_atom[tid];
     const bool warp_live = 32 * warp < cnt;
-    uint32_t ph[2] = {0, 0};
     bool alive = true;
     const float *P32 = mx.p32 + m.fit_base[a];
     float *tb = tbuf + (size_t)(my < 0 ? 0 : my) * nf * HK;
     float *hb = hbuf + (size_t)(my < 0 ? 0 : my) * HK;
 
-    // streamed GEMM into TMEM columns [0, Np): for K-chunk kc, A is either the
-    // layer-1 input chunk (converted here) or the resident Hb, B is the chunk
-    // of the weight operand (rows [n0, n0 + Np) of a K-chunked operand).
+    // Streamed GEMM into TMEM columns [0, Np): K-chunks of FIT_KC.  B (weights,
+    // K-chunked, chunk kc at Bsrc + kc * chunk_bytes + row_off_bytes) always comes
+    // by bulk copy; A is the layer-1 input (the descriptor's BF16 tile, bulk
+    // copy) or the resident activation Hb.  One thread runs a FIT_NS-stage ring:
+    // wait for the chunk, issue its MMAs, release the stage by commit, refill the
+    // stage of the previous chunk.  Chunks are numbered across calls (ctr) so the
+    // barrier parities stay consistent; every call ends with all MMAs complete.
+    const unsigned char *dtile = mx.dtile + (size_t)tile_id * (mx.fit_kp[0] / FIT_KC) * (MXT * FIT_KC * 2);
     auto gemm = [&](bool from_D, int nK, const unsigned char *Bsrc, int64_t chunk_bytes, int64_t row_off_bytes,
                     int Np) -> bool {
         const uint32_t idesc = tc::make_idesc_bf16(MXT, Np);
-        const int bbytes = Np * FIT_KC * 2;
-        int issued = 0;
-        for (int kc = 0; kc < nK; ++kc) {
-            const int buf = kc & 1;
-            if (kc >= 2) {  // buffer reuse: the MMAs of chunk kc-2 must be done
-                if (!tc_wait(&mbar[buf], ph[buf], status)) return false;
-            }
-            copy16(Bb + buf * 256 * FIT_KC * 2, Bsrc + kc * chunk_bytes + row_off_bytes, bbytes);
-            if (from_D) {
-                unsigned char *Ac = Ab + buf * MXT * FIT_KC * 2;
-#pragma unroll
-                for (int k8 = 0; k8 < FIT_KC; k8 += 8) {
-                    float v[8];
-#pragma unroll
-                    for (int q = 0; q < 8; ++q) {
-                        const int k = kc * FIT_KC + k8 + q;
-                        v[q] = (my >= 0 && k < K1) ? (float)D[(size_t)my * K1 + k] : 0.f;
-                    }
-                    st8(Ac, tid, k8, FIT_KC, v);
+        const uint32_t bbytes = (uint32_t)Np * FIT_KC * 2;
+        const uint32_t abytes = from_D ? (uint32_t)MXT * FIT_KC * 2 : 0u;
+        if (tid == 0) {
+            const int c0 = ctr;
+            int issued = 0, consumed = 0;
+            auto load = [&](int c) {
+                const int s = c % FIT_NS, kc = c - c0;
+                mbar_expect_tx_mx(&full[s], abytes + bbytes);
+                bulk_g2s_mx(Bb + (size_t)s * 256 * FIT_KC * 2, Bsrc + kc * chunk_bytes + row_off_bytes, bbytes,
+                            &full[s]);
+                if (from_D)
+                    bulk_g2s_mx(Ab + (size_t)s * MXT * FIT_KC * 2, dtile + (size_t)kc * MXT * FIT_KC * 2, abytes,
+                                &full[s]);
+                ++issued;
+            };
+            for (int c = c0; c < c0 + FIT_NS && c < c0 + nK; ++c) load(c);
+            bool ok = true;
+            for (int c = c0; c < c0 + nK; ++c) {
+                const int s = c % FIT_NS, kc = c - c0;
+                if (!tc::mbar_wait(&full[s], (c / FIT_NS) & 1)) {
+                    ok = false;
+                    break;
                 }
-            }
-            tc_sync();
-            if (tid == 0) {
+                ++consumed;
 #pragma unroll
                 for (int kk = 0; kk < FIT_KC / 16; ++kk) {
                     const uint64_t ad =
-                        from_D ? tc::make_desc(tc::smem_u32(Ab + buf * MXT * FIT_KC * 2) + kk * 256, 128, FIT_KC * 16)
+                        from_D ? tc::make_desc(tc::smem_u32(Ab + (size_t)s * MXT * FIT_KC * 2) + kk * 256, 128, FIT_KC * 16)
                                : tc::make_desc(tc::smem_u32(Hb) + (kc * (FIT_KC / 16) + kk) * 256, 128, HK * 16);
                     const uint64_t bd =
-                        tc::make_desc(tc::smem_u32(Bb + buf * 256 * FIT_KC * 2) + kk * 256, 128, FIT_KC * 16);
+                        tc::make_desc(tc::smem_u32(Bb + (size_t)s * 256 * FIT_KC * 2) + kk * 256, 128, FIT_KC * 16);
                     tc::mma_bf16(tbase, ad, bd, idesc, kc > 0 || kk > 0);
                 }
-                tc::mma_commit(&mbar[buf]);
+                tc::mma_commit(&empty[s]);
+                if (c - 1 >= c0 && c - 1 + FIT_NS < c0 + nK) {
+                    const int ps = (c - 1) % FIT_NS;
+                    if (!tc::mbar_wait(&empty[ps], ((c - 1) / FIT_NS) & 1)) {
+                        ok = false;
+                        break;
+                    }
+                    load(c - 1 + FIT_NS);
+                }
             }
-            ++issued;
+            tc::mma_commit(&dbar);
+            if (!ok) {
+                atomicOr(status, DPF_MMA_TIMEOUT);
+                for (int c = c0 + consumed; c < c0 + issued; ++c) tc::mbar_wait(&full[c % FIT_NS], (c / FIT_NS) & 1);
+                pfail = 1;
+            }
+            ctr = c0 + nK;
         }
-        // drain: the last one or two chunks
-        for (int kc = (nK >= 2 ? nK - 2 : 0); kc < nK; ++kc)
-            if (!tc_wait(&mbar[kc & 1], ph[kc & 1], status)) return false;
-        (void)issued;
-        return true;
+        const bool waited = tc::mbar_wait(&dbar, dph);
+        dph ^= 1u;
+        const bool bad = __syncthreads_or(!waited) || pfail;
+        tc::fence_after_sync();
+        if (bad && tid == 0) atomicOr(status, DPF_MMA_TIMEOUT);
+        return !bad;
     };
 
     // ---------------- forward
@@ -819,10 +898,6 @@ __global__ void __launch_bounds__(MXT, 1) k_fit_mx(DevModel m, MixedModel mx, in
             tc_sync();
         }
     }
-    if (!alive) {
-        tc::mbar_wait(&mbar[0], ph[0] ^ 1u);
-        tc::mbar_wait(&mbar[1], ph[1] ^ 1u);
-    }
     tc_sync();
     if (warp == 0) tc::tmem_dealloc(tbase, 256);
 }
@@ -927,7 +1002,7 @@ cudaError_t dp_launch_embed_bwd_mx(cudaStream_t st, const DevModel &m, const Mix
 cudaError_t dp_launch_fit_mx(cudaStream_t st, const DevModel &m, const MixedModel &mx, int N,
                              const NlistBuffers &nb, EvalBuffers eb, int32_t *status, int64_t *launches)
 {
-    const size_t smem = 2 * MXT * FIT_KC * 2 + 2 * 256 * FIT_KC * 2 + MXT * 256 * 2;
+    const size_t smem = FIT_NS * MXT * FIT_KC * 2 + FIT_NS * 256 * FIT_KC * 2 + MXT * 256 * 2;
     static bool configured = false;
     if (!configured) {
         cudaError_t e = cudaFuncSetAttribute(k_fit_mx, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -935,6 +1010,10 @@ cudaError_t dp_launch_fit_mx(cudaStream_t st, const DevModel &m, const MixedMode
         configured = true;
     }
     const int grid = (N + MXT - 1) / MXT + m.ntypes;
+    const int K1 = m.m2 * m.M;
+    k_d2bf<<<(grid * MXT * 32 + 255) / 256, 256, 0, st>>>(eb.D, K1, mx.fit_kp[0] / FIT_KC, nb.type_perm,
+                                                          nb.type_start, m.ntypes, mx.dtile);
+    *launches += 1;
     k_fit_mx<<<grid, MXT, smem, st>>>(m, mx, N, nb.type_perm, nb.type_start, eb.D, eb.Ei, eb.gD, eb.fit_t,
                                       eb.fit_h, status);
     *launches += 1;

@@ -50,8 +50,8 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 TRAFFIC = {
     # ncu --set full, one 12,288-atom water evaluation (bench.py --profile-eval 2):
     # dram__bytes_read.sum + dram__bytes_write.sum of the dominant kernel
-    "embed_bwd": {"bytes_per_launch": 206.358016e6 + 19.876096e6, "file": "embed.cu", "src_sha": "c982a146b11862b2"},
-    "embed_bwd_mx<25>": {"bytes_per_launch": 204.823552e6 + 17.918464e6, "file": "mixed.cu", "src_sha": "1d36586835464fdc"},
+    "embed_bwd": {"bytes_per_launch": 207.375104e6 + 19.777024e6, "file": "embed.cu", "src_sha": "07a9934264d6cc22"},
+    "embed_bwd_mx<25>": {"bytes_per_launch": 204.936448e6 + 17.953792e6, "file": "mixed.cu", "src_sha": "4fba8b950690f474"},
 }
 
 

@@ -143,6 +143,10 @@ struct dp_ctx {
     uint16_t *d_oz_w;
     int32_t *d_oz_e;
     int64_t oz_w_elems, oz_e_elems, oz_version;
+    // FP64 embedding forward with its last layer on the tensor cores: weight digits per net
+    bool use_ex;
+    unsigned char *d_ex_w;
+    int64_t ex_version;
     // mixed precision: BF16 / FP32 copies of the parameters
     MixedModel mx;
     float *d_p32;
@@ -520,6 +524,17 @@ dp_status ensure_oz(dp_ctx *c)
     return DP_OK;
 }
 
+dp_status ensure_ex(dp_ctx *c)
+{
+    if (c->ex_version == c->model->version) return DP_OK;
+    std::vector<unsigned char> w(dp_ex_bytes(c->m), 0);
+    dp_ex_split_weights(c->m, c->model->h_params, w.data());
+    DP_CUDA(cudaStreamSynchronize(c->stream), "embedding digits");
+    DP_CUDA(cudaMemcpy(c->d_ex_w, w.data(), w.size(), cudaMemcpyHostToDevice), "embedding digits");
+    c->ex_version = c->model->version;
+    return DP_OK;
+}
+
 dp_status enqueue_eval(dp_ctx *c, const double *coords, const int32_t *types, const Box3 &b, int64_t N,
                        int64_t nloc, double *energy, double *force, double *virial, double *atom_energy)
 {
@@ -530,12 +545,15 @@ dp_status enqueue_eval(dp_ctx *c, const double *coords, const int32_t *types, co
     const int n = (int)nloc;  // the centres
     if (n > 0) {
         if ((s = enqueue_format(c, coords, types, b, nloc))) return s;
+        if (!mixed && c->use_ex && (s = ensure_ex(c))) return s;
         {
             GroupTimer tm(c, G_EMBED_FWD);
-            e = mixed ? dp_launch_embed_fwd_mx(c->stream, c->m, c->mx, coords, types, b, n, c->fb, c->nb, c->eb,
-                                               c->num_sms, c->d_status, &c->launches)
-                      : dp_launch_embed_fwd(c->stream, c->m, coords, types, b, n, c->fb, c->nb, c->eb, c->num_sms,
-                                            &c->launches);
+            e = mixed       ? dp_launch_embed_fwd_mx(c->stream, c->m, c->mx, coords, types, b, n, c->fb, c->nb,
+                                                     c->eb, c->num_sms, c->d_status, &c->launches)
+                : c->use_ex ? dp_launch_embed_fwd_x(c->stream, c->m, c->d_ex_w, coords, types, b, n, c->fb, c->nb,
+                                                    c->eb, c->num_sms, c->d_status, &c->launches)
+                            : dp_launch_embed_fwd(c->stream, c->m, coords, types, b, n, c->fb, c->nb, c->eb,
+                                                  c->num_sms, &c->launches);
             if (e != cudaSuccess) return cuda_fail(e, "embed_fwd");
         }
         if (!mixed && c->use_oz && (s = ensure_oz(c))) return s;
@@ -754,7 +772,7 @@ void dp_ctx_free(dp_ctx *c)
                     c->d_energy, c->d_virial, c->md_force, c->ke_part, c->d_inv_mass_conv, c->d_mass,
                     c->eb.fit_t, c->eb.fit_h, c->d_p32, c->d_emb_ops, c->d_fit_fwd, c->d_fit_bwd,
                     c->pb.dT, c->pb.dD, c->pb.Db, c->pb.dDb, c->pb.fit_scr, c->pb.rowscr, c->pb.slices,
-                    c->d_oz_w, c->d_oz_e, c->ob.a, c->ob.aexp, c->ob.t, c->ob.h, c->ob.g, c->d_dtile};
+                    c->d_oz_w, c->d_oz_e, c->ob.a, c->ob.aexp, c->ob.t, c->ob.h, c->ob.g, c->d_dtile, c->d_ex_w};
     for (void *p : bufs) dev_free(p);
     delete c;
 }
@@ -824,6 +842,12 @@ dp_status dp_ctx_create(const dp_model *model, int64_t natoms_max, int32_t cand_
     }
     c->use_oz = false;
     c->oz_version = -1;
+    c->use_ex = false;
+    c->ex_version = -1;
+    if (precision == DP_PREC_FP64 && dp_ex_supported(c->m)) {
+        ALLOC(c->d_ex_w, dp_ex_bytes(c->m));
+        c->use_ex = true;
+    }
     if (precision == DP_PREC_FP64 && dp_oz_plan(c->m, c->oz, c->oz_w_elems, c->oz_e_elems)) {
         ALLOC(c->d_oz_w, (size_t)c->oz_w_elems);
         ALLOC(c->d_oz_e, (size_t)c->oz_e_elems);

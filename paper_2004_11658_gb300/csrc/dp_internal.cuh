@@ -263,6 +263,16 @@ void dp_oz_split_weights(const DevModel &m, const double *h_params, const OzMode
 cudaError_t dp_launch_fit_oz(cudaStream_t st, const DevModel &m, const OzModel &oz, const OzBuffers &ob, int N,
                              const NlistBuffers &nb, EvalBuffers eb, int32_t *status, int64_t *launches);
 
+// FP64 embedding forward with its last layer on the tensor cores by exact
+// splitting (csrc/embed_x.cu): 3-layer doubling nets with e1 in {16, 25, 32}.
+bool dp_ex_supported(const DevModel &m);
+size_t dp_ex_bytes(const DevModel &m);
+void dp_ex_split_weights(const DevModel &m, const double *h_params, unsigned char *out);
+cudaError_t dp_launch_embed_fwd_x(cudaStream_t st, const DevModel &m, const unsigned char *wx, const double *x,
+                                  const int32_t *types, Box3 box, int N, const FormatBuffers &fb,
+                                  const NlistBuffers &nb, EvalBuffers eb, int num_sms, int32_t *status,
+                                  int64_t *launches);
+
 // Mixed precision (BF16 tensor-core GEMMs, FP64 environment / contractions).
 cudaError_t dp_launch_embed_fwd_mx(cudaStream_t st, const DevModel &m, const MixedModel &mx, const double *x,
                                    const int32_t *types, Box3 box, int N, const FormatBuffers &fb,

@@ -1,0 +1,419 @@
+// embed_x.cu -- FP64 environment matrix, embedding net and descriptor
+// (Algorithm 2; Eqs. embedding, embedding-first, embedding-rest, descrpt)
+// with the widest embedding layer on the tensor cores at FP64 accuracy.
+//
+// The doubling embedding net (widths e1, 2e1, 4e1) costs 2 e1 (2 e1) + 2 (2 e1)(4 e1)
+// FLOP per neighbour row, four fifths of it in the last layer z2 = h1 W2.  Here
+// layers 0 and 1 run on the FP64 units (one row per lane, the 4 warps
+// splitting the columns, as in k_embed_fwd) and the last layer is an exact
+// product of digit expansions (as the fitting net's GEMMs, csrc/fit_oz.cu):
+//   h1 (|h1| < 2) -> S = 7 digits in base 2^8 of round(h1 2^55),
+//   W2 column f   -> 7 digits of round(W2[., f] 2^(56 - f_f)),  2^f_f > max |W2[., f]|,
+//   z2[f][row] = 2^(1 + f_f) sum_{g=2}^{8} 2^(-8 g) C_g,  C_g = sum_{s+t=g} A_s B_t,
+// with K = 2 e1 <= 64, so K 4^7 (S + 2) < 2^24: every partial sum of every C_g
+// is an integer the FP32 accumulators hold exactly.  The MMA is transposed:
+// M = 128 output features (the rows of W2^T), N = 32 neighbour rows, so in the
+// epilogue thread f owns feature f of the 32 rows: it adds the bias, applies the
+// FP64 tanh and the (h1, h1) skip, and accumulates its column of
+// T = R~^T G in registers.  One CTA (4 warps) per atom, persistent over the
+// type-sorted atoms; the current net's weight digits (7 x 128 x K2p BF16 and
+// the 128 column exponents) arrive by one bulk copy.  Bounded waits; on a
+// timeout the kernel sets DPF_MMA_TIMEOUT, frees its tensor memory and returns.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "dp_internal.cuh"
+#include "oz.cuh"
+#include "tc.cuh"
+
+namespace {
+
+constexpr int XS = 7;        // digits
+constexpr int XBETA = 8;     // digit width (bits)
+constexpr int XNR = 32;      // neighbour rows per MMA (N)
+constexpr int XM = 128;      // output features per MMA (M), 4 e1 <= 128
+constexpr int XT = 256;      // threads: 8 warps; in the epilogue warps w and w + 4 share TMEM lanes 32 (w % 4) ..
+constexpr int XGR = 512;     // rows of one neighbour block whose geometry is staged at once
+
+constexpr int k2p_of(int e1) { return (2 * e1 + 15) / 16 * 16; }
+// bytes of one net's weight block: digits [XS][128 x K2p] bf16, then 128 int32 exponents
+constexpr size_t net_bytes(int e1) { return (size_t)XS * XM * k2p_of(e1) * 2 + XM * 4; }
+
+__device__ __forceinline__ void bulk_g2s_x(void *dst, const void *src, uint32_t bytes, uint64_t *mbar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+            tc::smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(tc::smem_u32(mbar))
+        : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx_x(uint64_t *mbar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(tc::smem_u32(mbar)), "r"(bytes)
+                 : "memory");
+}
+
+// y[q] = sum_{g=2}^{8} C_g[q] 2^(8 (8 - g)) for the 16 columns at taddr (group g
+// at column offset (g - 2) * XNR): the group sums are integers below 2^24, so
+// they are combined exactly in two int64 Horner chains (g = 2..4 and g = 5..8,
+// below 2^41 and 2^49) and converted once: y = hi 2^32 + lo, one rounding.
+__device__ __forceinline__ void combine_groups(uint32_t taddr, double (&y)[16])
+{
+    static_assert(XS == 7 && XBETA == 8, "combine_groups assumes 7 digits of 8 bits");
+    long long hi[16], lo[16];
+#pragma unroll
+    for (int g = 2; g <= XS + 1; ++g) {
+        float v[16];
+        tc::tmem_ld16(taddr + (uint32_t)(g - 2) * XNR, v);
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+            const long long iv = (long long)__float2int_rn(v[q]);
+            if (g == 2) hi[q] = iv;
+            else if (g <= 4) hi[q] = (hi[q] << XBETA) + iv;
+            else if (g == 5) lo[q] = iv;
+            else lo[q] = (lo[q] << XBETA) + iv;
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < 16; ++q) y[q] = fma((double)hi[q], 4294967296.0, (double)lo[q]);
+}
+
+template <int E1>
+struct XShape {
+    static constexpr int E2 = 2 * E1, E3 = 4 * E1, K2p = k2p_of(E1);
+    static constexpr int LD0 = E1 + 1, LD1 = E2 + 1;
+    static constexpr size_t WD = net_bytes(E1);              // weight digits + exponents
+    static constexpr size_t BD = (size_t)XS * XNR * K2p * 2;  // row digits
+    // FP64 region: W1 (E1 x E2), w0, b0 (E1), b1 (E2), b2 (XM), H0, H1, Rt (XGR x 4), srow (XGR), Tsm (2 x 4 x XM)
+    static constexpr size_t F64 =
+        (size_t)E1 * E2 + 2 * E1 + E2 + XM + XNR * LD0 + XNR * LD1 + XGR * 4 + XGR + 8 * XM;
+    static constexpr size_t SMEM = WD + BD + F64 * 8;
+};
+
+template <int E1>
+__global__ void __launch_bounds__(XT, 1) k_embed_fwd_x(DevModel m, const unsigned char *__restrict__ wx,
+                                                       const double *__restrict__ x,
+                                                       const int32_t *__restrict__ types, Box3 box, int N,
+                                                       const int32_t *__restrict__ type_perm,
+                                                       const int32_t *__restrict__ nlist,
+                                                       const int32_t *__restrict__ nreal, double *__restrict__ Tout,
+                                                       double *__restrict__ Dout, int32_t *status)
+{
+    using X = XShape<E1>;
+    constexpr int E2 = X::E2, E3 = X::E3, K2p = X::K2p, LD0 = X::LD0, LD1 = X::LD1;
+    extern __shared__ __align__(1024) unsigned char smraw[];
+    unsigned char *Wd = smraw;                                   // weight digits, then exponents
+    const int *fexp = reinterpret_cast<const int *>(Wd + (size_t)XS * XM * K2p * 2);
+    unsigned char *Bd = Wd + X::WD;                              // row digits
+    double *W1s = reinterpret_cast<double *>(Bd + X::BD);
+    double *w0s = W1s + E1 * E2;
+    double *b0s = w0s + E1;
+    double *b1s = b0s + E1;
+    double *b2s = b1s + E2;
+    double *H0 = b2s + XM;
+    double *H1 = H0 + XNR * LD0;
+    double *Rga = H1 + XNR * LD1;   // environment rows of the block [XGR][4]
+    double *sga = Rga + XGR * 4;    // s of the block [XGR]
+    double *Tsm = sga + XGR;        // [2][4][XM]
+    __shared__ __align__(8) uint64_t mbar_w, mbar_m;
+    __shared__ uint32_t tslot;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int T = m.ntypes, nm = m.nm;
+
+    if (warp == 0) tc::tmem_alloc(&tslot, 256);
+    if (tid == 0) {
+        tc::mbar_init(&mbar_w, 1);
+        tc::mbar_init(&mbar_m, 1);
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tbase = tslot;
+    const uint32_t tlane = tbase + ((uint32_t)(32 * (warp & 3)) << 16);
+    const uint32_t idesc = tc::make_idesc_bf16(XM, XNR);
+    uint32_t ph_w = 0, ph_m = 0;
+    bool alive = true;
+    bool pend_w = false, pend_m = false;  // a copy or MMAs still in flight after a timeout
+    int staged = -1;
+    const int f = tid & (XM - 1);  // epilogue: this thread's output feature
+    const int half = tid >> 7;     // ... and half of the chunk's rows
+
+    for (int ii = blockIdx.x; ii < N && alive; ii += gridDim.x) {
+        const int i = type_perm[ii];
+        const int a = types[i];
+        const bool a_ok = (unsigned)a < (unsigned)T;
+        const double xi[3] = {x[3 * i], x[3 * i + 1], x[3 * i + 2]};
+        double tacc[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int b = 0; b < T && alive; ++b) {
+            const int nb = a_ok ? nreal[(size_t)i * T + b] : 0;
+            if (nb == 0) continue;
+            const int net = a * T + b;
+            if (net != staged) {
+                __syncthreads();
+                if (tid == 0) {
+                    mbar_expect_tx_x(&mbar_w, (uint32_t)X::WD);
+                    bulk_g2s_x(Wd, wx + (size_t)net * X::WD, (uint32_t)X::WD, &mbar_w);
+                }
+                const double *src = m.params + m.emb_base[net];
+                for (int q = tid; q < E1; q += XT) {
+                    w0s[q] = src[q];
+                    b0s[q] = src[E1 + q];
+                }
+                for (int q = tid; q < E1 * E2; q += XT) W1s[q] = src[2 * E1 + q];
+                for (int q = tid; q < E2; q += XT) b1s[q] = src[2 * E1 + E1 * E2 + q];
+                for (int q = tid; q < XM; q += XT)
+                    b2s[q] = q < E3 ? src[2 * E1 + E1 * E2 + E2 + E2 * E3 + q] : 0.0;
+                const bool ok = tc::mbar_wait(&mbar_w, ph_w);
+                ph_w ^= 1u;
+                if (__syncthreads_or(!ok)) {
+                    if (tid == 0) atomicOr(status, DPF_MMA_TIMEOUT);
+                    alive = false;
+                    pend_w = true;
+                    break;
+                }
+                staged = net;
+            }
+            const double cscale = f < E3 ? oz_pow2(1 + fexp[f] - XBETA * (XS + 1)) : 0.0;
+            for (int c0 = 0; c0 < nb && alive; c0 += XNR) {
+                const int nv = min(XNR, nb - c0);  // valid rows of the chunk
+                // geometry of the next XGR rows of the block, one row per thread
+                if (c0 % XGR == 0) {
+                    __syncthreads();
+                    for (int q = tid; q < XGR; q += XT) {
+                        const int r = c0 + q;
+                        double s = 0.0, R[4] = {0.0, 0.0, 0.0, 0.0};
+                        if (r < nb) {
+                            const int j = nlist[(size_t)i * nm + m.sel_off[b] + r];
+                            const double xj[3] = {x[3 * j], x[3 * j + 1], x[3 * j + 2]};
+                            double d[3], ds;
+                            const double rr = dp_pinned_dist(xi, xj, box, d);
+                            dp_switch(rr, m.rcut_smth, m.rcut, s, ds);
+                            const double inv = 1.0 / rr;
+                            R[0] = s;
+                            R[1] = s * d[0] * inv;
+                            R[2] = s * d[1] * inv;
+                            R[3] = s * d[2] * inv;
+                        }
+                        sga[q] = s;
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) Rga[q * 4 + c] = R[c];
+                    }
+                }
+                const double *srow = sga + (c0 % XGR);
+                const double *Rt = Rga + (c0 % XGR) * 4;
+                __syncthreads();
+                // layer 0: h0 = tanh(s w0 + b0), one row per lane, warps split the columns
+                {
+                    const double sv = srow[lane];
+                    for (int o = warp; o < E1; o += XT / 32) H0[lane * LD0 + o] = dp_tanh64(fma(sv, w0s[o], b0s[o]), m.tanh_tab);
+                }
+                __syncthreads();
+                // layer 1: h1 = (h0, h0) + tanh(h0 W1 + b1)
+                {
+                    const double *hr = H0 + lane * LD0;
+                    for (int o = warp; o < E2; o += XT / 32) {
+                        double z = b1s[o];
+#pragma unroll 5
+                        for (int q = 0; q < E1; ++q) z = fma(hr[q], W1s[q * E2 + o], z);
+                        H1[lane * LD1 + o] = hr[o < E1 ? o : o - E1] + dp_tanh64(z, m.tanh_tab);
+                    }
+                }
+                __syncthreads();
+                // digits of h1 (fixed scale: |h1| < 2), 8 columns per thread-iteration
+                for (int p = tid; p < XNR * (K2p / 8); p += XT) {
+                    const int row = p / (K2p / 8), k0 = (p % (K2p / 8)) * 8;
+                    long long I[8];
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        const double v = (k0 + q < E2) ? H1[row * LD1 + k0 + q] : 0.0;
+                        I[q] = __double2ll_rn(v * 36028797018963968.0);  // 2^55
+                    }
+                    const uint32_t ofs = tc::kmajor_offset(row, k0, K2p);
+                    for (int sd = XS - 1; sd >= 0; --sd) {
+                        int dg[8];
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) dg[q] = sd > 0 ? oz_digit_step(I[q], XBETA) : (int)I[q];
+                        uint4 u;
+                        u.x = (uint32_t)oz_bf16_int(dg[0]) | ((uint32_t)oz_bf16_int(dg[1]) << 16);
+                        u.y = (uint32_t)oz_bf16_int(dg[2]) | ((uint32_t)oz_bf16_int(dg[3]) << 16);
+                        u.z = (uint32_t)oz_bf16_int(dg[4]) | ((uint32_t)oz_bf16_int(dg[5]) << 16);
+                        u.w = (uint32_t)oz_bf16_int(dg[6]) | ((uint32_t)oz_bf16_int(dg[7]) << 16);
+                        *reinterpret_cast<uint4 *>(Bd + (size_t)sd * XNR * K2p * 2 + ofs) = u;
+                    }
+                }
+                tc::fence_proxy_async();
+                tc::fence_before_sync();
+                __syncthreads();
+                tc::fence_after_sync();
+                // z2^T (128 features x 32 rows) = W2^T digits x h1 digits, group g at columns (g - 2) * 32
+                if (tid == 0) {
+                    const uint32_t wa = tc::smem_u32(Wd), ba = tc::smem_u32(Bd);
+#pragma unroll
+                    for (int s = 1; s <= XS; ++s) {
+#pragma unroll
+                        for (int t = 1; t + s <= XS + 1; ++t) {
+#pragma unroll
+                            for (int kk = 0; kk < K2p / 16; ++kk) {
+                                const uint64_t ad = tc::make_desc(wa + (uint32_t)(s - 1) * XM * K2p * 2 + kk * 256, 128,
+                                                                  K2p * 16);
+                                const uint64_t bd = tc::make_desc(ba + (uint32_t)(t - 1) * XNR * K2p * 2 + kk * 256, 128,
+                                                                  K2p * 16);
+                                tc::mma_bf16(tbase + (uint32_t)(s + t - 2) * XNR, ad, bd, idesc, s > 1 || kk > 0);
+                            }
+                        }
+                    }
+                    tc::mma_commit(&mbar_m);
+                }
+                {
+                    const bool ok = tc::mbar_wait(&mbar_m, ph_m);
+                    ph_m ^= 1u;
+                    const bool bad = __syncthreads_or(!ok);
+                    tc::fence_after_sync();
+                    if (bad) {
+                        if (tid == 0) atomicOr(status, DPF_MMA_TIMEOUT);
+                        alive = false;
+                        pend_m = true;
+                        break;
+                    }
+                }
+                // epilogue: feature f of rows 16 half .. 16 half + 15 of the chunk
+                double y[16];
+                combine_groups(tlane + 16 * half, y);
+                if (f < E3) {
+                    const double bf = b2s[f];
+                    const int fs = f < E2 ? f : f - E2;
+#pragma unroll
+                    for (int qq = 0; qq < 16; ++qq) {
+                        const int q = 16 * half + qq;
+                        if (q < nv) {
+                            const double z = fma(y[qq], cscale, bf);
+                            const double G = H1[q * LD1 + fs] + dp_tanh64(z, m.tanh_tab);
+#pragma unroll
+                            for (int c = 0; c < 4; ++c) tacc[c] = fma(Rt[q * 4 + c], G, tacc[c]);
+                        }
+                    }
+                }
+                tc::fence_before_sync();
+                __syncthreads();
+                tc::fence_after_sync();
+            }
+        }
+        if (!alive) break;
+        // T (the two halves' partials summed, scaled) and D = T_<^T T
+        if (half == 1 && f < E3) {
+#pragma unroll
+            for (int c = 0; c < 4; ++c) Tsm[4 * XM + c * E3 + f] = tacc[c];
+        }
+        __syncthreads();
+        if (half == 0 && f < E3) {
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const double v = (tacc[c] + Tsm[4 * XM + c * E3 + f]) * m.desc_scale;
+                Tsm[c * E3 + f] = v;
+                Tout[(size_t)i * 4 * E3 + c * E3 + f] = v;
+            }
+        }
+        __syncthreads();
+        const int nd = m.m2 * E3;
+        for (int q = tid; q < nd; q += XT) {
+            const int a2 = q / E3, b2 = q - a2 * E3;
+            double acc = Tsm[a2] * Tsm[b2];
+            acc = fma(Tsm[E3 + a2], Tsm[E3 + b2], acc);
+            acc = fma(Tsm[2 * E3 + a2], Tsm[2 * E3 + b2], acc);
+            acc = fma(Tsm[3 * E3 + a2], Tsm[3 * E3 + b2], acc);
+            Dout[(size_t)i * nd + q] = acc;
+        }
+        __syncthreads();
+    }
+    // after a timeout: once more (bounded) for the copy or the MMAs still in flight
+    if (pend_w) tc::mbar_wait(&mbar_w, ph_w ^ 1u);
+    if (pend_m) tc::mbar_wait(&mbar_m, ph_m ^ 1u);
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tbase, 256);
+}
+
+template <int E1>
+cudaError_t launch_fwd_x(cudaStream_t st, const DevModel &m, const unsigned char *wx, const double *x,
+                         const int32_t *types, Box3 box, int N, const FormatBuffers &fb, const NlistBuffers &nb,
+                         EvalBuffers eb, int num_sms, int32_t *status)
+{
+    using X = XShape<E1>;
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e =
+            cudaFuncSetAttribute(k_embed_fwd_x<E1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)X::SMEM);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    int grid = num_sms;
+    if (grid > N) grid = N;
+    if (grid < 1) grid = 1;
+    k_embed_fwd_x<E1><<<grid, XT, X::SMEM, st>>>(m, wx, x, types, box, N, nb.type_perm, fb.nlist, fb.nreal, eb.T,
+                                                 eb.D, status);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+bool dp_ex_supported(const DevModel &m)
+{
+    if (m.n_emb != 3) return false;
+    const int e1 = m.emb[0];
+    if (e1 != 16 && e1 != 25 && e1 != 32) return false;
+    if (m.emb[1] != 2 * e1 || m.emb[2] != 4 * e1) return false;
+    return m.M == 4 * e1;
+}
+
+size_t dp_ex_bytes(const DevModel &m) { return (size_t)m.ntypes * m.ntypes * net_bytes(m.emb[0]); }
+
+void dp_ex_split_weights(const DevModel &m, const double *h_params, unsigned char *out)
+{
+    const int e1 = m.emb[0], e2 = 2 * e1, e3 = 4 * e1, K2p = k2p_of(e1);
+    const size_t nb = net_bytes(e1);
+    for (int net = 0; net < m.ntypes * m.ntypes; ++net) {
+        const double *W2 = h_params + m.emb_base[net] + 2 * e1 + e1 * e2 + e2;  // [e2][e3]
+        uint16_t *dig = reinterpret_cast<uint16_t *>(out + (size_t)net * nb);
+        int32_t *ex = reinterpret_cast<int32_t *>(out + (size_t)net * nb + (size_t)XS * XM * K2p * 2);
+        std::memset(out + (size_t)net * nb, 0, nb);
+        for (int f = 0; f < XM; ++f) {
+            double mx = 0.0;
+            if (f < e3)
+                for (int k = 0; k < e2; ++k) mx = std::max(mx, std::fabs(W2[(size_t)k * e3 + f]));
+            int ef = 0;
+            bool zero = !(mx > 0.0);
+            if (!zero) {
+                std::frexp(mx, &ef);
+                if (ef < XBETA * XS - 1020) zero = true;
+            }
+            if (zero) ef = 0;
+            ex[f] = ef;
+            const double scale = zero ? 0.0 : std::ldexp(1.0, XBETA * XS - ef);
+            for (int k = 0; k < K2p; ++k) {
+                long long I = (f < e3 && k < e2) ? std::llrint(W2[(size_t)k * e3 + f] * scale) : 0;
+                const uint32_t ofs = tc::kmajor_offset(f, k, K2p) / 2;
+                for (int sd = XS - 1; sd >= 0; --sd) {
+                    const int d = sd > 0 ? oz_digit_step(I, XBETA) : (int)I;
+                    dig[(size_t)sd * XM * K2p + ofs] = oz_bf16_int(d);
+                }
+            }
+        }
+    }
+}
+
+cudaError_t dp_launch_embed_fwd_x(cudaStream_t st, const DevModel &m, const unsigned char *wx, const double *x,
+                                  const int32_t *types, Box3 box, int N, const FormatBuffers &fb,
+                                  const NlistBuffers &nb, EvalBuffers eb, int num_sms, int32_t *status,
+                                  int64_t *launches)
+{
+    *launches += 1;
+    switch (m.emb[0]) {
+    case 16: return launch_fwd_x<16>(st, m, wx, x, types, box, N, fb, nb, eb, num_sms, status);
+    case 25: return launch_fwd_x<25>(st, m, wx, x, types, box, N, fb, nb, eb, num_sms, status);
+    case 32: return launch_fwd_x<32>(st, m, wx, x, types, box, N, fb, nb, eb, num_sms, status);
+    default: return cudaErrorInvalidValue;
+    }
+}

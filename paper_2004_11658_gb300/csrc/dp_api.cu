@@ -567,10 +567,12 @@ dp_status enqueue_eval(dp_ctx *c, const double *coords, const int32_t *types, co
         }
         {
             GroupTimer tm(c, G_EMBED_BWD);
-            e = mixed ? dp_launch_embed_bwd_mx(c->stream, c->m, c->mx, coords, types, b, n, c->fb, c->nb, c->eb,
-                                               c->num_sms, c->d_status, &c->launches)
-                      : dp_launch_embed_bwd(c->stream, c->m, coords, types, b, n, c->fb, c->nb, c->eb, c->num_sms,
-                                            &c->launches);
+            e = mixed       ? dp_launch_embed_bwd_mx(c->stream, c->m, c->mx, coords, types, b, n, c->fb, c->nb,
+                                                     c->eb, c->num_sms, c->d_status, &c->launches)
+                : c->use_ex ? dp_launch_embed_bwd_x(c->stream, c->m, c->d_ex_w, coords, types, b, n, c->fb, c->nb,
+                                                    c->eb, c->num_sms, c->d_status, &c->launches)
+                            : dp_launch_embed_bwd(c->stream, c->m, coords, types, b, n, c->fb, c->nb, c->eb,
+                                                  c->num_sms, &c->launches);
             if (e != cudaSuccess) return cuda_fail(e, "embed_bwd");
         }
     }

@@ -272,6 +272,10 @@ cudaError_t dp_launch_embed_fwd_x(cudaStream_t st, const DevModel &m, const unsi
                                   const int32_t *types, Box3 box, int N, const FormatBuffers &fb,
                                   const NlistBuffers &nb, EvalBuffers eb, int num_sms, int32_t *status,
                                   int64_t *launches);
+cudaError_t dp_launch_embed_bwd_x(cudaStream_t st, const DevModel &m, const unsigned char *wx, const double *x,
+                                  const int32_t *types, Box3 box, int N, const FormatBuffers &fb,
+                                  const NlistBuffers &nb, EvalBuffers eb, int num_sms, int32_t *status,
+                                  int64_t *launches);
 
 // Mixed precision (BF16 tensor-core GEMMs, FP64 environment / contractions).
 cudaError_t dp_launch_embed_fwd_mx(cudaStream_t st, const DevModel &m, const MixedModel &mx, const double *x,

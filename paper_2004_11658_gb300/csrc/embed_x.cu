@@ -357,6 +357,413 @@ cudaError_t launch_fwd_x(cudaStream_t st, const DevModel &m, const unsigned char
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- backward --
+//
+// k_embed_bwd_x recomputes G and its s-tangent dG/ds (G is never stored) with
+// the same split: layers 0 and 1 and their tangents on the FP64 units, the
+// last layer's two products z2 = h1 W2 and dz2 = dh1 W2 on the tensor cores
+// (h1 with the fixed scale 2^1, dh1 with a per-row power-of-two scale; the
+// two products run one after the other through the same digit buffer and
+// land in separate tensor-memory columns).  In the epilogue thread f forms
+// G[f] and dG[f] of its rows and the partials G gT[c][f], dG gT[c][f]; a warp
+// shuffle tree sums them over its 32 features, the four warps' sums are added
+// in fixed order, and warp 0 (one lane per row) applies the chain rule through
+// R~(r_ij) as k_embed_bwd does: pair gradients, the atom's own force and
+// virial parts.
+
+template <int E1>
+struct XBShape {
+    static constexpr int E2 = 2 * E1, E3 = 4 * E1, K2p = k2p_of(E1);
+    static constexpr int LD0 = E1 + 1, LD1 = E2 + 1;
+    static constexpr int GR = 64;  // rows whose geometry is staged at once
+    static constexpr size_t WD = net_bytes(E1);
+    static constexpr size_t BD = (size_t)XS * XNR * K2p * 2;
+    // FP64: W1, w0, b0, b1, b2, H0, dH0 (aliased by the reduction buffer), H1, dH1,
+    // geometry [GR][10], gT [4][XM]
+    static constexpr size_t H0SZ = (size_t)2 * XNR * LD0;
+    static constexpr size_t RED = (size_t)8 * 16 * 8;
+    static constexpr size_t F64 = (size_t)E1 * E2 + 2 * E1 + E2 + XM + (H0SZ > RED ? H0SZ : RED) +
+                                  2 * XNR * LD1 + GR * 10 + 4 * XM;
+    static constexpr size_t SMEM = WD + BD + F64 * 8 + XNR * 4;
+};
+
+template <int E1>
+__global__ void __launch_bounds__(XT, 1) k_embed_bwd_x(DevModel m, const unsigned char *__restrict__ wx,
+                                                       const double *__restrict__ x,
+                                                       const int32_t *__restrict__ types, Box3 box, int N,
+                                                       const int32_t *__restrict__ type_perm,
+                                                       const int32_t *__restrict__ nlist,
+                                                       const int32_t *__restrict__ nreal,
+                                                       const double *__restrict__ Tin, const double *__restrict__ gD,
+                                                       double *__restrict__ pair_g, double *__restrict__ f_own,
+                                                       double *__restrict__ vir_part, int32_t *status)
+{
+    using X = XBShape<E1>;
+    constexpr int E2 = X::E2, E3 = X::E3, K2p = X::K2p, LD0 = X::LD0, LD1 = X::LD1, GR = X::GR;
+    extern __shared__ __align__(1024) unsigned char smraw[];
+    unsigned char *Wd = smraw;
+    const int *fexp = reinterpret_cast<const int *>(Wd + (size_t)XS * XM * K2p * 2);
+    unsigned char *Bd = Wd + X::WD;
+    double *W1s = reinterpret_cast<double *>(Bd + X::BD);
+    double *w0s = W1s + E1 * E2;
+    double *b0s = w0s + E1;
+    double *b1s = b0s + E1;
+    double *b2s = b1s + E2;
+    double *H0 = b2s + XM;
+    double *dH0 = H0 + XNR * LD0;
+    double *red = H0;  // [8 warps][16 rows][8], used after layer 1 (aliases H0, dH0)
+    double *H1 = H0 + (X::H0SZ > X::RED ? X::H0SZ : X::RED);
+    double *dH1 = H1 + XNR * LD1;
+    double *geo = dH1 + XNR * LD1;  // [GR][10]: s, ds, R[4], d[3], r
+    double *gTs = geo + GR * 10;    // [4][XM]
+    int *erow = reinterpret_cast<int *>(gTs + 4 * XM);  // [XNR] tangent row exponents
+    __shared__ __align__(8) uint64_t mbar_w, mbar_m;
+    __shared__ uint32_t tslot;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int T = m.ntypes, nm = m.nm, m2 = m.m2;
+
+    if (warp == 0) tc::tmem_alloc(&tslot, 512);
+    if (tid == 0) {
+        tc::mbar_init(&mbar_w, 1);
+        tc::mbar_init(&mbar_m, 1);
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tbase = tslot;
+    const uint32_t tlane = tbase + ((uint32_t)(32 * (warp & 3)) << 16);
+    const uint32_t idesc = tc::make_idesc_bf16(XM, XNR);
+    uint32_t ph_w = 0, ph_m = 0;
+    bool alive = true, pend_w = false, pend_m = false;
+    int staged = -1;
+    const int f = tid & (XM - 1);
+    const int half = tid >> 7;
+
+    // z^T = W2^T digits x (row digits in Bd) into 7 groups at column base col0
+    auto mma_rows = [&](uint32_t col0) -> bool {
+        if (tid == 0) {
+            const uint32_t wa = tc::smem_u32(Wd), ba = tc::smem_u32(Bd);
+#pragma unroll
+            for (int s = 1; s <= XS; ++s)
+#pragma unroll
+                for (int t = 1; t + s <= XS + 1; ++t)
+#pragma unroll
+                    for (int kk = 0; kk < K2p / 16; ++kk)
+                        tc::mma_bf16(tbase + col0 + (uint32_t)(s + t - 2) * XNR,
+                                     tc::make_desc(wa + (uint32_t)(s - 1) * XM * K2p * 2 + kk * 256, 128, K2p * 16),
+                                     tc::make_desc(ba + (uint32_t)(t - 1) * XNR * K2p * 2 + kk * 256, 128, K2p * 16),
+                                     idesc, s > 1 || kk > 0);
+            tc::mma_commit(&mbar_m);
+        }
+        const bool ok = tc::mbar_wait(&mbar_m, ph_m);
+        ph_m ^= 1u;
+        const bool bad = __syncthreads_or(!ok);
+        tc::fence_after_sync();
+        if (bad) {
+            if (tid == 0) atomicOr(status, DPF_MMA_TIMEOUT);
+            pend_m = true;
+        }
+        return !bad;
+    };
+    // digits of the 32 x E2 rows of src (row scale 2^(56 - e_r), e_r from erow or fixed)
+    auto make_digits = [&](const double *src, bool fixed) {
+        for (int p = tid; p < XNR * (K2p / 8); p += XT) {
+            const int row = p / (K2p / 8), k0 = (p % (K2p / 8)) * 8;
+            const double sc = oz_pow2(XBETA * XS - (fixed ? 1 : erow[row]));
+            long long I[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) I[q] = (k0 + q < E2) ? __double2ll_rn(src[row * LD1 + k0 + q] * sc) : 0ll;
+            const uint32_t ofs = tc::kmajor_offset(row, k0, K2p);
+            for (int sd = XS - 1; sd >= 0; --sd) {
+                int dg[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) dg[q] = sd > 0 ? oz_digit_step(I[q], XBETA) : (int)I[q];
+                uint4 u;
+                u.x = (uint32_t)oz_bf16_int(dg[0]) | ((uint32_t)oz_bf16_int(dg[1]) << 16);
+                u.y = (uint32_t)oz_bf16_int(dg[2]) | ((uint32_t)oz_bf16_int(dg[3]) << 16);
+                u.z = (uint32_t)oz_bf16_int(dg[4]) | ((uint32_t)oz_bf16_int(dg[5]) << 16);
+                u.w = (uint32_t)oz_bf16_int(dg[6]) | ((uint32_t)oz_bf16_int(dg[7]) << 16);
+                *reinterpret_cast<uint4 *>(Bd + (size_t)sd * XNR * K2p * 2 + ofs) = u;
+            }
+        }
+        tc::fence_proxy_async();
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+    };
+
+    for (int ii = blockIdx.x; ii < N && alive; ii += gridDim.x) {
+        const int i = type_perm[ii];
+        const int a = types[i];
+        const double xi[3] = {x[3 * i], x[3 * i + 1], x[3 * i + 2]};
+        // gT[c][x] = scale ([x < M2] sum_b gD[x][b] T[c][b] + sum_{a<M2} gD[a][x] T[c][a])
+        {
+            double *Ts = H1;  // T of this atom, [4][E3]
+            for (int p = tid; p < 4 * E3; p += XT) Ts[p] = Tin[(size_t)i * 4 * E3 + p];
+            __syncthreads();
+            const double *g = gD + (size_t)i * m2 * E3;
+            for (int p = tid; p < 4 * E3; p += XT) {
+                const int cc = p / E3, xx = p - cc * E3;
+                double acc = 0.0;
+                if (xx < m2)
+                    for (int b2 = 0; b2 < E3; ++b2) acc = fma(g[xx * E3 + b2], Ts[cc * E3 + b2], acc);
+                for (int a2 = 0; a2 < m2; ++a2) acc = fma(g[a2 * E3 + xx], Ts[cc * E3 + a2], acc);
+                gTs[cc * XM + xx] = acc * m.desc_scale;
+            }
+            __syncthreads();
+        }
+        double gt[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) gt[c] = f < E3 ? gTs[c * XM + f] : 0.0;
+        double fo[3] = {0.0, 0.0, 0.0}, vir[9];
+#pragma unroll
+        for (int q = 0; q < 9; ++q) vir[q] = 0.0;
+
+        const bool a_ok = (unsigned)a < (unsigned)T;
+        for (int b = 0; b < T && alive; ++b) {
+            const int nb = a_ok ? nreal[(size_t)i * T + b] : 0;
+            if (nb == 0) continue;
+            const int net = a * T + b;
+            if (net != staged) {
+                __syncthreads();
+                if (tid == 0) {
+                    mbar_expect_tx_x(&mbar_w, (uint32_t)X::WD);
+                    bulk_g2s_x(Wd, wx + (size_t)net * X::WD, (uint32_t)X::WD, &mbar_w);
+                }
+                const double *src = m.params + m.emb_base[net];
+                for (int q = tid; q < E1; q += XT) {
+                    w0s[q] = src[q];
+                    b0s[q] = src[E1 + q];
+                }
+                for (int q = tid; q < E1 * E2; q += XT) W1s[q] = src[2 * E1 + q];
+                for (int q = tid; q < E2; q += XT) b1s[q] = src[2 * E1 + E1 * E2 + q];
+                for (int q = tid; q < XM; q += XT)
+                    b2s[q] = q < E3 ? src[2 * E1 + E1 * E2 + E2 + E2 * E3 + q] : 0.0;
+                const bool ok = tc::mbar_wait(&mbar_w, ph_w);
+                ph_w ^= 1u;
+                if (__syncthreads_or(!ok)) {
+                    if (tid == 0) atomicOr(status, DPF_MMA_TIMEOUT);
+                    alive = false;
+                    pend_w = true;
+                    break;
+                }
+                staged = net;
+            }
+            const int fx = f < E3 ? fexp[f] : 0;
+            for (int c0 = 0; c0 < nb && alive; c0 += XNR) {
+                const int nv = min(XNR, nb - c0);
+                if (c0 % GR == 0) {
+                    __syncthreads();
+                    for (int q = tid; q < GR; q += XT) {
+                        const int r = c0 + q;
+                        double *gq = geo + q * 10;
+                        double s = 0.0, ds = 0.0, d[3] = {0.0, 0.0, 0.0}, rr = 1.0;
+                        if (r < nb) {
+                            const int j = nlist[(size_t)i * nm + m.sel_off[b] + r];
+                            const double xj[3] = {x[3 * j], x[3 * j + 1], x[3 * j + 2]};
+                            rr = dp_pinned_dist(xi, xj, box, d);
+                            dp_switch(rr, m.rcut_smth, m.rcut, s, ds);
+                        }
+                        const double inv = 1.0 / rr;
+                        gq[0] = s;
+                        gq[1] = ds;
+                        gq[2] = s;
+                        gq[3] = s * d[0] * inv;
+                        gq[4] = s * d[1] * inv;
+                        gq[5] = s * d[2] * inv;
+                        gq[6] = d[0];
+                        gq[7] = d[1];
+                        gq[8] = d[2];
+                        gq[9] = rr;
+                    }
+                }
+                const double *gc = geo + (c0 % GR) * 10;  // this chunk's rows
+                __syncthreads();
+                // layer 0 and its tangent
+                {
+                    const double sv = gc[lane * 10];
+                    for (int o = warp; o < E1; o += XT / 32) {
+                        const double w0 = w0s[o];
+                        const double t = dp_tanh64(fma(sv, w0, b0s[o]), m.tanh_tab);
+                        H0[lane * LD0 + o] = t;
+                        dH0[lane * LD0 + o] = fma(-t, t, 1.0) * w0;
+                    }
+                }
+                __syncthreads();
+                // layer 1 and its tangent
+                {
+                    const double *hr = H0 + lane * LD0, *dhr = dH0 + lane * LD0;
+                    for (int o = warp; o < E2; o += XT / 32) {
+                        double z = b1s[o], dz = 0.0;
+#pragma unroll 5
+                        for (int q = 0; q < E1; ++q) {
+                            const double w = W1s[q * E2 + o];
+                            z = fma(hr[q], w, z);
+                            dz = fma(dhr[q], w, dz);
+                        }
+                        const double t = dp_tanh64(z, m.tanh_tab);
+                        const int os = o < E1 ? o : o - E1;
+                        H1[lane * LD1 + o] = hr[os] + t;
+                        dH1[lane * LD1 + o] = fma(fma(-t, t, 1.0), dz, dhr[os]);
+                    }
+                }
+                __syncthreads();
+                // tangent row exponents: 2^e > max_k |dh1[row][k]| (one warp per 8 rows, 4 lanes per row)
+                {
+                    const int row = tid >> 3, part = tid & 7;
+                    double mx = 0.0;
+                    if (row < XNR)
+                        for (int k = part; k < E2; k += 8) mx = fmax(mx, fabs(dH1[row * LD1 + k]));
+#pragma unroll
+                    for (int o = 4; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+                    if (row < XNR && part == 0) {
+                        // 2^e > max |dh1| (e >= -900 keeps every scale below a normal number; a zero row takes 0)
+                        int e = 0;
+                        if (mx > 0.0) {
+                            frexp(mx, &e);
+                            e = max(e, -900);
+                        }
+                        erow[row] = e;
+                    }
+                }
+                // value then tangent products, digits through the same buffer
+                make_digits(H1, true);
+                if (!mma_rows(0)) {
+                    alive = false;
+                    break;
+                }
+                make_digits(dH1, false);
+                if (!mma_rows(256)) {
+                    alive = false;
+                    break;
+                }
+                // epilogue: feature f of rows 16 half .. 16 half + 15
+                double yv[16], yt[16];
+                combine_groups(tlane + 16 * half, yv);
+                combine_groups(tlane + 256 + 16 * half, yt);
+                const double cv = oz_pow2(1 + fx - XBETA * (XS + 1));
+                const double bf = f < E3 ? b2s[f] : 0.0;
+                const int fs = f < E2 ? f : (f < E3 ? f - E2 : 0);
+                double *rw = red + (warp * 16) * 8;  // this warp's [16 rows][8]
+                // partials p[r][c] = G gT[c] (c < 4), dG gT[c - 4] for 4 rows at a time, summed over
+                // the warp's 32 features by a transposing shuffle tree (31 adds per lane): lane L ends
+                // with the sum of row L / 8, component L % 8
+#pragma unroll 1
+                for (int q4 = 0; q4 < 16; q4 += 4) {
+                    double p[32];
+#pragma unroll
+                    for (int r4 = 0; r4 < 4; ++r4) {
+                        const int qq = q4 + r4, q = 16 * half + qq;
+                        double G = 0.0, dG = 0.0;
+                        if (q < nv && f < E3) {
+                            const double t = dp_tanh64(fma(yv[qq], cv, bf), m.tanh_tab);
+                            G = H1[q * LD1 + fs] + t;
+                            const double dz2 = yt[qq] * oz_pow2(erow[q] + fx - XBETA * (XS + 1));
+                            dG = fma(fma(-t, t, 1.0), dz2, dH1[q * LD1 + fs]);
+                        }
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) {
+                            p[r4 * 8 + c] = G * gt[c];
+                            p[r4 * 8 + 4 + c] = dG * gt[c];
+                        }
+                    }
+#pragma unroll
+                    for (int w = 16, n = 16; w >= 1; w >>= 1, n >>= 1) {
+                        const bool up = (lane & w) != 0;
+#pragma unroll
+                        for (int k = 0; k < n; ++k) {
+                            const double send = up ? p[k] : p[n + k];
+                            const double keep = up ? p[n + k] : p[k];
+                            p[k] = keep + __shfl_xor_sync(0xffffffffu, send, w);
+                        }
+                    }
+                    rw[(q4 + (lane >> 3)) * 8 + (lane & 7)] = p[0];
+                }
+                __syncthreads();
+                // chain rule through R~(r_ij), one lane per row (warp 0)
+                if (warp == 0 && lane < nv) {
+                    const int q = lane, hq = q >> 4, qq = q & 15;
+                    double sa[8];
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) sa[c] = 0.0;
+                    for (int w = 4 * hq; w < 4 * hq + 4; ++w)
+#pragma unroll
+                        for (int c = 0; c < 8; ++c) sa[c] += red[(w * 16 + qq) * 8 + c];
+                    const double *gq = gc + q * 10;
+                    const double gs = gq[0], gds = gq[1], gd[3] = {gq[6], gq[7], gq[8]}, gr = gq[9];
+                    double gR0 = sa[0];
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) gR0 = fma(gq[2 + c], sa[4 + c], gR0);
+                    const double inv = 1.0 / gr;
+                    const double u[3] = {gd[0] * inv, gd[1] * inv, gd[2] * inv};
+                    const double dot = sa[1] * u[0] + sa[2] * u[1] + sa[3] * u[2];
+                    const double sr = gs * inv;
+                    const double coef = gR0 * gds + gds * dot - sr * dot;
+                    double gv[3];
+#pragma unroll
+                    for (int bb = 0; bb < 3; ++bb) gv[bb] = fma(u[bb], coef, sr * sa[1 + bb]);
+                    double *pg = pair_g + ((size_t)i * nm + m.sel_off[b] + c0 + q) * 3;
+                    pg[0] = gv[0];
+                    pg[1] = gv[1];
+                    pg[2] = gv[2];
+#pragma unroll
+                    for (int aa = 0; aa < 3; ++aa) {
+                        fo[aa] += gv[aa];
+#pragma unroll
+                        for (int bb = 0; bb < 3; ++bb) vir[aa * 3 + bb] -= gd[aa] * gv[bb];
+                    }
+                }
+                tc::fence_before_sync();
+                __syncthreads();
+                tc::fence_after_sync();
+            }
+        }
+        if (!alive) break;
+        if (warp == 0) {
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+#pragma unroll
+                for (int q = 0; q < 3; ++q) fo[q] += __shfl_xor_sync(0xffffffffu, fo[q], off);
+#pragma unroll
+                for (int q = 0; q < 9; ++q) vir[q] += __shfl_xor_sync(0xffffffffu, vir[q], off);
+            }
+            if (lane == 0) {
+#pragma unroll
+                for (int q = 0; q < 3; ++q) f_own[(size_t)i * 3 + q] = fo[q];
+#pragma unroll
+                for (int q = 0; q < 9; ++q) vir_part[(size_t)i * 9 + q] = vir[q];
+            }
+        }
+        __syncthreads();
+    }
+    if (pend_w) tc::mbar_wait(&mbar_w, ph_w ^ 1u);
+    if (pend_m) tc::mbar_wait(&mbar_m, ph_m ^ 1u);
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tbase, 512);
+}
+
+template <int E1>
+cudaError_t launch_bwd_x(cudaStream_t st, const DevModel &m, const unsigned char *wx, const double *x,
+                         const int32_t *types, Box3 box, int N, const FormatBuffers &fb, const NlistBuffers &nb,
+                         EvalBuffers eb, int num_sms, int32_t *status)
+{
+    using X = XBShape<E1>;
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e =
+            cudaFuncSetAttribute(k_embed_bwd_x<E1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)X::SMEM);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    int grid = num_sms;
+    if (grid > N) grid = N;
+    if (grid < 1) grid = 1;
+    k_embed_bwd_x<E1><<<grid, XT, X::SMEM, st>>>(m, wx, x, types, box, N, nb.type_perm, fb.nlist, fb.nreal, eb.T,
+                                                 eb.gD, eb.pair_g, eb.f_own, eb.vir_part, status);
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 bool dp_ex_supported(const DevModel &m)
@@ -401,6 +808,20 @@ void dp_ex_split_weights(const DevModel &m, const double *h_params, unsigned cha
                 }
             }
         }
+    }
+}
+
+cudaError_t dp_launch_embed_bwd_x(cudaStream_t st, const DevModel &m, const unsigned char *wx, const double *x,
+                                  const int32_t *types, Box3 box, int N, const FormatBuffers &fb,
+                                  const NlistBuffers &nb, EvalBuffers eb, int num_sms, int32_t *status,
+                                  int64_t *launches)
+{
+    *launches += 1;
+    switch (m.emb[0]) {
+    case 16: return launch_bwd_x<16>(st, m, wx, x, types, box, N, fb, nb, eb, num_sms, status);
+    case 25: return launch_bwd_x<25>(st, m, wx, x, types, box, N, fb, nb, eb, num_sms, status);
+    case 32: return launch_bwd_x<32>(st, m, wx, x, types, box, N, fb, nb, eb, num_sms, status);
+    default: return cudaErrorInvalidValue;
     }
 }
 

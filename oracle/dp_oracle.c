@@ -139,9 +139,9 @@ static double orc_norm(const double d[3])
 }
 
 /* s(r) = w(r)/r with w a smooth gate: 1 below rs, 0 from rc on, and in
- * between w = u^3(-6u^2 + 15u - 10) + 1, u = (r - rs)/(rc - rs).  The paper
- * (Sec. 2) fixes only that w decays smoothly from 1 to 0 at rc.  Also returns
- * ds/dr. */
+ * between w = u^3(-6u^2 + 15u - 10) + 1, u = (r - rs)/(rc - rs).  Sec. 2
+ * asks only for a gate that goes smoothly from 1 to 0 at rc; this quintic is
+ * the reading taken here.  Also returns ds/dr. */
 int orc_switch(double r, double rs, double rc, double *s, double *ds)
 {
     if (r < rs) {

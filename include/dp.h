@@ -80,12 +80,15 @@ typedef struct dp_model dp_model;
 typedef struct dp_ctx dp_ctx;
 
 /* Precision modes of a context. */
-#define DP_PREC_FP64  0   /* every step with float64 accuracy; the fitting-net
-                             GEMMs run on the tensor cores as exact products of
-                             BF16 digit expansions of the FP64 operands (every
-                             partial sum an integer below 2^24, held exactly by
-                             the FP32 accumulators), the rest on the FP64 units
-                             (fitting widths <= 256; otherwise as FP64_SIMT) */
+#define DP_PREC_FP64  0   /* every step with float64 accuracy; the dense products
+                             (the fitting-net GEMMs and, for 3-layer doubling
+                             embedding nets with s_1 in {16, 25, 32}, the last
+                             embedding layer and its s-tangent) run on the tensor
+                             cores as exact products of BF16 digit expansions of
+                             the FP64 operands (every partial sum an integer
+                             below 2^24, held exactly by the FP32 accumulators),
+                             the rest on the FP64 units; other shapes run as
+                             FP64_SIMT */
 #define DP_PREC_FP64_SIMT 2  /* every step in float64 on the FP64 units */
 #define DP_PREC_MIXED 1   /* embedding- and fitting-net GEMMs on the tensor cores
                              (BF16 operands, FP32 accumulation, FP32 tanh); the

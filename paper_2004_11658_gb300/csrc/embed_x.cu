@@ -84,7 +84,8 @@ __device__ __forceinline__ void combine_groups(uint32_t taddr, double (&y)[16])
 template <int E1>
 struct XShape {
     static constexpr int E2 = 2 * E1, E3 = 4 * E1, K2p = k2p_of(E1);
-    static constexpr int LD0 = E1 + 1, LD1 = E2 + 1;
+    // odd row strides (in doubles): one row per lane reads without bank conflicts
+    static constexpr int LD0 = (E1 % 2) ? E1 + 2 : E1 + 1, LD1 = (E2 % 2) ? E2 + 2 : E2 + 1;
     static constexpr size_t WD = net_bytes(E1);              // weight digits + exponents
     static constexpr size_t BD = (size_t)XS * XNR * K2p * 2;  // row digits
     // FP64 region: W1 (E1 x E2), w0, b0 (E1), b1 (E2), b2 (XM), H0, H1, Rt (XGR x 4), srow (XGR), Tsm (2 x 4 x XM)
@@ -224,7 +225,7 @@ __global__ void __launch_bounds__(XT, 1) k_embed_fwd_x(DevModel m, const unsigne
                 __syncthreads();
                 // digits of h1 (fixed scale: |h1| < 2), 8 columns per thread-iteration
                 for (int p = tid; p < XNR * (K2p / 8); p += XT) {
-                    const int row = p / (K2p / 8), k0 = (p % (K2p / 8)) * 8;
+                    const int row = p % XNR, k0 = (p / XNR) * 8;  // lanes on consecutive rows
                     long long I[8];
 #pragma unroll
                     for (int q = 0; q < 8; ++q) {
@@ -374,16 +375,18 @@ cudaError_t launch_fwd_x(cudaStream_t st, const DevModel &m, const unsigned char
 template <int E1>
 struct XBShape {
     static constexpr int E2 = 2 * E1, E3 = 4 * E1, K2p = k2p_of(E1);
-    static constexpr int LD0 = E1 + 1, LD1 = E2 + 1;
+    // odd row strides (in doubles): one row per lane reads without bank conflicts
+    static constexpr int LD0 = (E1 % 2) ? E1 + 2 : E1 + 1, LD1 = (E2 % 2) ? E2 + 2 : E2 + 1;
     static constexpr int GR = 64;  // rows whose geometry is staged at once
+    static constexpr int GS = 11;  // doubles per staged row
     static constexpr size_t WD = net_bytes(E1);
     static constexpr size_t BD = (size_t)XS * XNR * K2p * 2;
     // FP64: W1, w0, b0, b1, b2, H0, dH0 (aliased by the reduction buffer), H1, dH1,
-    // geometry [GR][10], gT [4][XM]
+    // geometry [GR][GS] (10 values, odd stride), gT [4][XM]
     static constexpr size_t H0SZ = (size_t)2 * XNR * LD0;
     static constexpr size_t RED = (size_t)8 * 16 * 8;
     static constexpr size_t F64 = (size_t)E1 * E2 + 2 * E1 + E2 + XM + (H0SZ > RED ? H0SZ : RED) +
-                                  2 * XNR * LD1 + GR * 10 + 4 * XM;
+                                  2 * XNR * LD1 + GR * GS + 4 * XM;
     static constexpr size_t SMEM = WD + BD + F64 * 8 + XNR * 4;
 };
 
@@ -399,7 +402,7 @@ __global__ void __launch_bounds__(XT, 1) k_embed_bwd_x(DevModel m, const unsigne
                                                        double *__restrict__ vir_part, int32_t *status)
 {
     using X = XBShape<E1>;
-    constexpr int E2 = X::E2, E3 = X::E3, K2p = X::K2p, LD0 = X::LD0, LD1 = X::LD1, GR = X::GR;
+    constexpr int E2 = X::E2, E3 = X::E3, K2p = X::K2p, LD0 = X::LD0, LD1 = X::LD1, GR = X::GR, GS = X::GS;
     extern __shared__ __align__(1024) unsigned char smraw[];
     unsigned char *Wd = smraw;
     const int *fexp = reinterpret_cast<const int *>(Wd + (size_t)XS * XM * K2p * 2);
@@ -414,8 +417,8 @@ __global__ void __launch_bounds__(XT, 1) k_embed_bwd_x(DevModel m, const unsigne
     double *red = H0;  // [8 warps][16 rows][8], used after layer 1 (aliases H0, dH0)
     double *H1 = H0 + (X::H0SZ > X::RED ? X::H0SZ : X::RED);
     double *dH1 = H1 + XNR * LD1;
-    double *geo = dH1 + XNR * LD1;  // [GR][10]: s, ds, R[4], d[3], r
-    double *gTs = geo + GR * 10;    // [4][XM]
+    double *geo = dH1 + XNR * LD1;  // [GR][GS]: s, ds, R[4], d[3], r
+    double *gTs = geo + GR * GS;    // [4][XM]
     int *erow = reinterpret_cast<int *>(gTs + 4 * XM);  // [XNR] tangent row exponents
     __shared__ __align__(8) uint64_t mbar_w, mbar_m;
     __shared__ uint32_t tslot;
@@ -468,7 +471,7 @@ __global__ void __launch_bounds__(XT, 1) k_embed_bwd_x(DevModel m, const unsigne
     // digits of the 32 x E2 rows of src (row scale 2^(56 - e_r), e_r from erow or fixed)
     auto make_digits = [&](const double *src, bool fixed) {
         for (int p = tid; p < XNR * (K2p / 8); p += XT) {
-            const int row = p / (K2p / 8), k0 = (p % (K2p / 8)) * 8;
+            const int row = p % XNR, k0 = (p / XNR) * 8;  // lanes on consecutive rows
             const double sc = oz_pow2(XBETA * XS - (fixed ? 1 : erow[row]));
             long long I[8];
 #pragma unroll
@@ -556,7 +559,7 @@ __global__ void __launch_bounds__(XT, 1) k_embed_bwd_x(DevModel m, const unsigne
                     __syncthreads();
                     for (int q = tid; q < GR; q += XT) {
                         const int r = c0 + q;
-                        double *gq = geo + q * 10;
+                        double *gq = geo + q * GS;
                         double s = 0.0, ds = 0.0, d[3] = {0.0, 0.0, 0.0}, rr = 1.0;
                         if (r < nb) {
                             const int j = nlist[(size_t)i * nm + m.sel_off[b] + r];
@@ -577,11 +580,11 @@ __global__ void __launch_bounds__(XT, 1) k_embed_bwd_x(DevModel m, const unsigne
                         gq[9] = rr;
                     }
                 }
-                const double *gc = geo + (c0 % GR) * 10;  // this chunk's rows
+                const double *gc = geo + (c0 % GR) * GS;  // this chunk's rows
                 __syncthreads();
                 // layer 0 and its tangent
                 {
-                    const double sv = gc[lane * 10];
+                    const double sv = gc[lane * GS];
                     for (int o = warp; o < E1; o += XT / 32) {
                         const double w0 = w0s[o];
                         const double t = dp_tanh64(fma(sv, w0, b0s[o]), m.tanh_tab);
@@ -689,7 +692,7 @@ __global__ void __launch_bounds__(XT, 1) k_embed_bwd_x(DevModel m, const unsigne
                     for (int w = 4 * hq; w < 4 * hq + 4; ++w)
 #pragma unroll
                         for (int c = 0; c < 8; ++c) sa[c] += red[(w * 16 + qq) * 8 + c];
-                    const double *gq = gc + q * 10;
+                    const double *gq = gc + q * GS;
                     const double gs = gq[0], gds = gq[1], gd[3] = {gq[6], gq[7], gq[8]}, gr = gq[9];
                     double gR0 = sa[0];
 #pragma unroll

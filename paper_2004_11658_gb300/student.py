@@ -200,6 +200,57 @@ def force_errors(desc, params, frames, which, precision=dp.DP_PREC_FP64):
                 atom_err_p50=float(p50), atom_err_p90=float(p90), atom_err_p99=float(p99))
 
 
+class FastPathMD:
+    """Velocity-Verlet MD on the student (the fast path, mixed precision by
+    default) with the FP64 full model as its judge and fallback: every
+    `check_every` steps the full model evaluates the current configuration;
+    when the student's force RMSE against it exceeds `tol` (eV/A) the run
+    continues on the full model from that configuration and velocity.
+
+    run() advances coords/vel in place and returns the list of checks
+    (step, force RMSE, max per-atom force error, on which model the run goes
+    on) and the step at which it switched (None if it never did)."""
+
+    def __init__(self, full_model, student_model, natoms_max, tol=1e-3, check_every=10,
+                 precision=dp.DP_PREC_MIXED):
+        self.fast = dp.Context(student_model, natoms_max, precision=precision)
+        self.full = dp.Context(full_model, natoms_max)
+        self.judge = dp.Context(full_model, natoms_max)
+        self.tol = float(tol)
+        self.check_every = int(check_every)
+        self.on_full = False
+        self.switched_at = None
+
+    def _check(self, x, t, box):
+        dp.dp_build_nlist(self.judge, x, t, box, 0.0)
+        ref = dp.dp_eval(self.judge, x, t, box)["force"].clone()
+        dp.dp_build_nlist(self.fast, x, t, box, 0.0)
+        f = dp.dp_eval(self.fast, x, t, box)["force"]
+        d = (f - ref).double()
+        return float(d.pow(2).mean().sqrt()), float(d.norm(dim=1).max())
+
+    def run(self, x, v, t, box, masses, dt, nsteps, rebuild_every=10, skin=2.0):
+        checks = []
+        done = 0
+        while done < nsteps:
+            n = min(self.check_every, nsteps - done)
+            ctx = self.full if self.on_full else self.fast
+            dp.dp_md_step(ctx, x, v, t, box, masses, dt, n, rebuild_every=rebuild_every, skin=skin)
+            done += n
+            if not self.on_full:
+                rmse, worst = self._check(x, t, box)
+                if rmse > self.tol:
+                    self.on_full = True
+                    self.switched_at = done
+                    dp.dp_md_reset(self.full)  # forces of the current configuration on the next step
+                else:
+                    # the check rebuilt the student's lists; its next step recomputes its forces
+                    dp.dp_md_reset(self.fast)
+                checks.append(dict(step=done, force_rmse=rmse, max_atom_err=worst,
+                                   model="full" if self.on_full else "student"))
+        return checks, self.switched_at
+
+
 def main(argv=None):
     """Trains the water student on teacher trajectories of the 12,288-atom
     box and writes its parameters (float32 .npy) and a JSON summary."""

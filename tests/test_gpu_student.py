@@ -95,3 +95,44 @@ def test_student_training_reduces_force_error(frames, synth):
     assert np.isfinite(hist[-1]["loss"])
     assert after["force_rmse"] < 0.7 * before["force_rmse"]
     assert abs(mixed["force_rmse"] - after["force_rmse"]) < 1e-3
+
+
+def test_fast_path_with_full_model_fallback(synth):
+    """The trained student runs MD as the fast path; the FP64 full model
+    judges it every 5 steps.  With a loose tolerance the run stays on the
+    student; with a tight one it switches at the first check and continues
+    exactly as a full-model run started from that configuration."""
+    import os
+    from paper_2004_11658_gb300 import dp, student
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    path = os.path.join(os.path.dirname(student.__file__), "data", "student_water12288.npy")
+    Ps = np.load(path).astype(np.float64)
+    w = synth.workload("water192")
+    N = len(w["coords"])
+    full = dp.Model(w["model"], synth.model_params(w["model"], 0))
+    stud = dp.Model(synth.WATER_STUDENT, Ps)
+    m = np.array(w["masses"])[w["types"]]
+    v0 = synth.maxwell_velocities(m, 300.0, seed=2)
+    t = torch.tensor(w["types"], device="cuda")
+    kw = dict(rebuild_every=10, skin=0.2)
+
+    x = torch.tensor(w["coords"], device="cuda")
+    v = torch.tensor(v0, device="cuda")
+    loose = student.FastPathMD(full, stud, N, tol=1.0, check_every=5)
+    checks, sw = loose.run(x, v, t, w["box"], w["masses"], 0.5, 20, **kw)
+    print("loose:", checks)
+    assert sw is None and len(checks) == 4
+    assert all(c["model"] == "student" and c["force_rmse"] < 1.0 for c in checks)
+
+    x = torch.tensor(w["coords"], device="cuda")
+    v = torch.tensor(v0, device="cuda")
+    tight = student.FastPathMD(full, stud, N, tol=0.0, check_every=5)
+    # first 5 steps on the student, then the switch
+    checks, sw = tight.run(x, v, t, w["box"], w["masses"], 0.5, 5, **kw)
+    assert sw == 5 and checks[-1]["model"] == "full"
+    xs, vs = x.clone(), v.clone()
+    tight.run(x, v, t, w["box"], w["masses"], 0.5, 10, **kw)
+    ref = dp.Context(full, N)
+    dp.dp_md_step(ref, xs, vs, t, w["box"], w["masses"], 0.5, 10, **kw)
+    assert torch.equal(x, xs) and torch.equal(v, vs)

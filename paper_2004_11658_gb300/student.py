@@ -24,7 +24,7 @@ from . import dp, synth
 def generate_frames(teacher_desc, teacher_params, workload, n_traj=20, frames_per_traj=50, stride=2,
                     T0=300.0, dt=0.5, seed0=100, device="cuda"):
     """Frames from n_traj teacher trajectories (different Maxwell seeds), one
-    frame every `stride` MD steps (20 x 50 frames at stride 2: twenty 100-step
+    frame every `stride` MD steps (20 x 50 frames at stride 3: twenty 150-step
     NVE runs of the starting configuration), labelled by the FP64 teacher.
     Returns dict(coords [F,N,3], energy [F], force [F,N,3]) on the device."""
     w = workload
@@ -262,13 +262,14 @@ def main(argv=None):
     ap.add_argument("--minutes", type=float, default=15.0, help="training wall time")
     ap.add_argument("--trajectories", type=int, default=20)
     ap.add_argument("--frames", type=int, default=50, help="frames per trajectory")
+    ap.add_argument("--stride", type=int, default=3, help="MD steps between frames")
     ap.add_argument("--seed", type=int, default=7)
     a = ap.parse_args(argv)
     w = synth.workload("water12288")
     teacher = w["model"]
     t0 = time.time()
     fr = generate_frames(teacher, synth.model_params(teacher, 0), w, n_traj=a.trajectories,
-                         frames_per_traj=a.frames)
+                         frames_per_traj=a.frames, stride=a.stride)
     t_gen = time.time() - t0
     nf = fr["coords"].shape[0]
     ntrain = nf - a.frames  # the last trajectory is held out
@@ -279,7 +280,7 @@ def main(argv=None):
     S = WATER_STUDENT_DESC
     P, hist = train(S, train_fr, 10 ** 9, seed=a.seed, time_limit_s=60.0 * a.minutes, log_every=50)
     res = dict(desc={k: list(v) if isinstance(v, tuple) else v for k, v in S.items()},
-               frames=nf, train_frames=ntrain, held_out_frames=len(held), generate_s=t_gen,
+               frames=nf, train_frames=ntrain, held_out_frames=len(held), stride=a.stride, generate_s=t_gen,
                steps=hist[-1]["step"] + 1, history=hist,
                held_out_fp64=force_errors(S, P, fr, held),
                held_out_mixed=force_errors(S, P, fr, held, precision=dp.DP_PREC_MIXED))

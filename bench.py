@@ -249,17 +249,17 @@ def mixed_kernel_flops(desc, rows, natoms):
     }
 
 
-def _accuracy(dp, ctx, judge, x, t, box):
-    """Forces, energy and virial of ctx against the judge context (FP64 full
+def _accuracy(dp, ctx, refc, x, t, box):
+    """Forces, energy and virial of ctx against the reference context (FP64 full
     model) on the configuration x: RMSE per component, per-atom |dF|
     percentiles, energy error per atom, virial error relative to its max."""
     import torch
     N = x.shape[0]
     dp.dp_build_nlist(ctx, x, t, box, SKIN)
-    dp.dp_build_nlist(judge, x, t, box, SKIN)
+    dp.dp_build_nlist(refc, x, t, box, SKIN)
     a = dp.dp_eval(ctx, x, t, box)
     a = {k: v.clone() for k, v in a.items() if torch.is_tensor(v)}
-    b = dp.dp_eval(judge, x, t, box)
+    b = dp.dp_eval(refc, x, t, box)
     dF = (a["force"] - b["force"]).double()
     rmse = float(dF.pow(2).mean().sqrt())
     frms = float(b["force"].pow(2).mean().sqrt())
@@ -272,7 +272,7 @@ def _accuracy(dp, ctx, judge, x, t, box):
             "virial_rel_err": float((a["virial"] - b["virial"]).abs().max() / b["virial"].abs().max())}
 
 
-def measure_mode(args, dp, w, run_desc, run_P, judge_model, v0, dev, world, flush, dtype):
+def measure_mode(args, dp, w, run_desc, run_P, ref_model, v0, dev, world, flush, dtype):
     """MD with another model or precision on the same workload: throughput,
     per-kernel times, roofline of the dominant kernel, and accuracy against
     the FP64 full model on the first and on the last configuration."""
@@ -280,11 +280,11 @@ def measure_mode(args, dp, w, run_desc, run_P, judge_model, v0, dev, world, flus
     N = len(v0)
     model = dp.Model(run_desc, run_P)
     ctx = dp.Context(model, N, precision=dp.DP_PREC_MIXED)
-    judge = dp.Context(judge_model, N)
+    refc = dp.Context(ref_model, N)
     x = torch.tensor(w["coords"], dtype=torch.float64, device=dev)
     v = torch.tensor(v0, dtype=torch.float64, device=dev)
     t = torch.tensor(w["types"], dtype=torch.int32, device=dev)
-    acc_first = _accuracy(dp, ctx, judge, x, t, w["box"])
+    acc_first = _accuracy(dp, ctx, refc, x, t, w["box"])
     th = torch.empty((MD_PER_STEP, 4), dtype=torch.float64, device=dev)
 
     def step():
@@ -317,7 +317,7 @@ def measure_mode(args, dp, w, run_desc, run_P, judge_model, v0, dev, world, flus
     total_ms = float(tmax.item())
     nl, nr, _ = dp.dp_format_nlist(ctx, x, t, w["box"], check=False)
     rows = int(nr.sum().item())
-    acc_last = _accuracy(dp, ctx, judge, x, t, w["box"])
+    acc_last = _accuracy(dp, ctx, refc, x, t, w["box"])
     fl = mixed_kernel_flops(run_desc, rows, N)
     groups = {g: {"ms": ms, "launches": n} for g, (ms, n) in kt.items() if n > 0}
     dom = max(groups, key=lambda g: groups[g]["ms"])

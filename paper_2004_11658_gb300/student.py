@@ -202,7 +202,7 @@ def force_errors(desc, params, frames, which, precision=dp.DP_PREC_FP64):
 
 class FastPathMD:
     """Velocity-Verlet MD on the student (the fast path, mixed precision by
-    default) with the FP64 full model as its judge and fallback: every
+    default) with the FP64 full model as its reference and fallback: every
     `check_every` steps the full model evaluates the current configuration;
     when the student's force RMSE against it exceeds `tol` (eV/A) the run
     continues on the full model from that configuration and velocity.
@@ -215,15 +215,15 @@ class FastPathMD:
                  precision=dp.DP_PREC_MIXED):
         self.fast = dp.Context(student_model, natoms_max, precision=precision)
         self.full = dp.Context(full_model, natoms_max)
-        self.judge = dp.Context(full_model, natoms_max)
+        self.refc = dp.Context(full_model, natoms_max)
         self.tol = float(tol)
         self.check_every = int(check_every)
         self.on_full = False
         self.switched_at = None
 
     def _check(self, x, t, box):
-        dp.dp_build_nlist(self.judge, x, t, box, 0.0)
-        ref = dp.dp_eval(self.judge, x, t, box)["force"].clone()
+        dp.dp_build_nlist(self.refc, x, t, box, 0.0)
+        ref = dp.dp_eval(self.refc, x, t, box)["force"].clone()
         dp.dp_build_nlist(self.fast, x, t, box, 0.0)
         f = dp.dp_eval(self.fast, x, t, box)["force"]
         d = (f - ref).double()

@@ -99,7 +99,7 @@ def test_student_training_reduces_force_error(frames, synth):
 
 def test_fast_path_with_full_model_fallback(synth):
     """The trained student runs MD as the fast path; the FP64 full model
-    judges it every 5 steps.  With a loose tolerance the run stays on the
+    checks it every 5 steps.  With a loose tolerance the run stays on the
     student; with a tight one it switches at the first check and continues
     exactly as a full-model run started from that configuration."""
     import os

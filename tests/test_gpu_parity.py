@@ -114,10 +114,18 @@ def test_eval_with_skin_list_matches(dp, oracle, synth):
     assert max(rel_errors(g, o)) < TOL
 
 
-@pytest.mark.parametrize("variant", ["student", "unscaled"])
+@pytest.mark.parametrize("variant", ["student", "unscaled", "e1_20", "fit_200"])
 def test_model_variants(dp, oracle, synth, variant):
+    """Other net shapes: the student widths; the unscaled descriptor; an
+    embedding net (20, 40, 80) that the tensor-core embedding kernels do not
+    take (FP64-unit embedding kernels with the tensor-core fitting net); a
+    fitting net of width 200 (column chunks with a ragged last one)."""
     if variant == "student":
         desc = synth.WATER_STUDENT
+    elif variant == "e1_20":
+        desc = dict(synth.WATER_MODEL, emb=(20, 40, 80))
+    elif variant == "fit_200":
+        desc = dict(synth.WATER_MODEL, fit=(200, 200))
     else:
         desc = dict(synth.WATER_MODEL, desc_scale_nm=0)
     w, d, P, o = oracle_eval(oracle, synth, "water192", desc=desc)

@@ -1,24 +1,26 @@
 // embed_x.cu -- FP64 environment matrix, embedding net and descriptor
 // (Algorithm 2; Eqs. embedding, embedding-first, embedding-rest, descrpt)
-// with the widest embedding layer on the tensor cores at FP64 accuracy.
+// with the embedding net's dense layers on the tensor cores at FP64 accuracy.
 //
 // The doubling embedding net (widths e1, 2e1, 4e1) costs 2 e1 (2 e1) + 2 (2 e1)(4 e1)
-// FLOP per neighbour row, four fifths of it in the last layer z2 = h1 W2.  Here
-// layers 0 and 1 run on the FP64 units (one row per lane, the 4 warps
-// splitting the columns, as in k_embed_fwd) and the last layer is an exact
-// product of digit expansions (as the fitting net's GEMMs, csrc/fit_oz.cu):
-//   h1 (|h1| < 2) -> S = 7 digits in base 2^8 of round(h1 2^55),
-//   W2 column f   -> 7 digits of round(W2[., f] 2^(56 - f_f)),  2^f_f > max |W2[., f]|,
-//   z2[f][row] = 2^(1 + f_f) sum_{g=2}^{8} 2^(-8 g) C_g,  C_g = sum_{s+t=g} A_s B_t,
-// with K = 2 e1 <= 64, so K 4^7 (S + 2) < 2^24: every partial sum of every C_g
-// is an integer the FP32 accumulators hold exactly.  The MMA is transposed:
-// M = 128 output features (the rows of W2^T), N = 32 neighbour rows, so in the
-// epilogue thread f owns feature f of the 32 rows: it adds the bias, applies the
-// FP64 tanh and the (h1, h1) skip, and accumulates its column of
-// T = R~^T G in registers.  One CTA (4 warps) per atom, persistent over the
-// type-sorted atoms; the current net's weight digits (7 x 128 x K2p BF16 and
-// the 128 column exponents) arrive by one bulk copy.  Bounded waits; on a
-// timeout the kernel sets DPF_MMA_TIMEOUT, frees its tensor memory and returns.
+// FLOP per neighbour row.  Layer 0 (1 -> e1) runs on the FP64 units (one row
+// per lane, the warps splitting the columns); the last layer, and layer 1 where
+// its weight digits fit in shared memory (e1 <= 25), are exact products of
+// digit expansions (as the fitting net's GEMMs, csrc/fit_oz.cu):
+//   h (|h| < 2)   -> S = 7 digits in base 2^8 of round(h 2^55),
+//   W column f    -> 7 digits of round(W[., f] 2^(56 - f_f)),  2^f_f > max |W[., f]|,
+//   z[f][row] = 2^(1 + f_f) sum_{g=2}^{8} 2^(-8 g) C_g,  C_g = sum_{s+t=g} A_s B_t,
+// with K <= 64, so K 4^7 (S + 2) < 2^24: every partial sum of every C_g is an
+// integer the FP32 accumulators hold exactly.  The MMAs are transposed: M = the
+// output features (the rows of W^T; 128 for the last layer, 64 for layer 1),
+// N = 32 neighbour rows.  In the last layer's epilogue thread f owns feature f
+// of the 32 rows: it adds the bias, applies the FP64 tanh and the (h1, h1) skip,
+// and accumulates its column of T = R~^T G in registers; layer 1's epilogue
+// (an M = 64 accumulator: 16 lanes of each warp's quarter) writes h1 back as
+// FP64 rows.  One CTA (8 warps) per atom, persistent over the type-sorted
+// atoms; the current net's weight digits and column exponents arrive by one
+// bulk copy.  Bounded waits; on a timeout the kernel sets DPF_MMA_TIMEOUT,
+// frees its tensor memory and returns.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -37,9 +39,19 @@ constexpr int XM = 128;      // output features per MMA (M), 4 e1 <= 128
 constexpr int XT = 256;      // threads: 8 warps; in the epilogue warps w and w + 4 share TMEM lanes 32 (w % 4) ..
 constexpr int XGR = 512;     // rows of one neighbour block whose geometry is staged at once
 
+constexpr int XM1 = 64;      // output features of the layer-1 MMA (M), 2 e1 <= 64
+
 constexpr int k2p_of(int e1) { return (2 * e1 + 15) / 16 * 16; }
-// bytes of one net's weight block: digits [XS][128 x K2p] bf16, then 128 int32 exponents
-constexpr size_t net_bytes(int e1) { return (size_t)XS * XM * k2p_of(e1) * 2 + XM * 4; }
+constexpr int k1p_of(int e1) { return (e1 + 15) / 16 * 16; }
+// layer 1 (e1 -> 2 e1) on the tensor cores as well: where its weight digits fit
+// in shared memory next to the backward kernel's buffers
+constexpr bool l1tc_of(int e1) { return e1 <= 25; }
+// bytes of the last layer's weights: digits [XS][128 x K2p] bf16, then 128 int32 exponents
+constexpr size_t w2_bytes(int e1) { return (size_t)XS * XM * k2p_of(e1) * 2 + XM * 4; }
+// bytes of layer 1's weights: digits [XS][64 x K1p] bf16, then 64 int32 exponents
+constexpr size_t w1_bytes(int e1) { return l1tc_of(e1) ? (size_t)XS * XM1 * k1p_of(e1) * 2 + XM1 * 4 : 0; }
+// bytes of one net's weight block: the last layer's part, then layer 1's
+constexpr size_t net_bytes(int e1) { return w2_bytes(e1) + w1_bytes(e1); }
 
 __device__ __forceinline__ void bulk_g2s_x(void *dst, const void *src, uint32_t bytes, uint64_t *mbar)
 {
@@ -81,17 +93,44 @@ __device__ __forceinline__ void combine_groups(uint32_t taddr, double (&y)[16])
     for (int q = 0; q < 16; ++q) y[q] = fma((double)hi[q], 4294967296.0, (double)lo[q]);
 }
 
+// combine_groups for an M = 64 accumulator: the 8 columns that tc::tmem_ld16x2_8
+// (second half 16 columns on) gives this thread.
+__device__ __forceinline__ void combine_groups8(uint32_t taddr, double (&y)[8])
+{
+    long long hi[8], lo[8];
+#pragma unroll
+    for (int g = 2; g <= XS + 1; ++g) {
+        float v[8];
+        tc::tmem_ld16x2_8<16>(taddr + (uint32_t)(g - 2) * XNR, v);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const long long iv = (long long)__float2int_rn(v[q]);
+            if (g == 2) hi[q] = iv;
+            else if (g <= 4) hi[q] = (hi[q] << XBETA) + iv;
+            else if (g == 5) lo[q] = iv;
+            else lo[q] = (lo[q] << XBETA) + iv;
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) y[q] = fma((double)hi[q], 4294967296.0, (double)lo[q]);
+}
+
 template <int E1>
 struct XShape {
-    static constexpr int E2 = 2 * E1, E3 = 4 * E1, K2p = k2p_of(E1);
+    static constexpr int E2 = 2 * E1, E3 = 4 * E1, K2p = k2p_of(E1), K1p = k1p_of(E1);
+    static constexpr bool L1 = l1tc_of(E1);  // layer 1 on the tensor cores
     // odd row strides (in doubles): one row per lane reads without bank conflicts
     static constexpr int LD0 = (E1 % 2) ? E1 + 2 : E1 + 1, LD1 = (E2 % 2) ? E2 + 2 : E2 + 1;
-    static constexpr size_t WD = net_bytes(E1);              // weight digits + exponents
+    static constexpr size_t WD = net_bytes(E1);              // weight digits + exponents (both layers)
+    static constexpr size_t NB = net_bytes(E1);              // stride of the nets' weight blocks
     static constexpr size_t BD = (size_t)XS * XNR * K2p * 2;  // row digits
-    // FP64 region: W1 (E1 x E2), w0, b0 (E1), b1 (E2), b2 (XM), H0, H1, Rt (XGR x 4), srow (XGR), Tsm (2 x 4 x XM)
+    // FP64 region: W1 (E1 x E2, SIMT layer 1 only), w0, b0 (E1), b1 (E2), b2 (XM), H0, H1,
+    // Rt (XGR x 4), srow (XGR), Tsm (2 x 4 x XM)
     static constexpr size_t F64 =
-        (size_t)E1 * E2 + 2 * E1 + E2 + XM + XNR * LD0 + XNR * LD1 + XGR * 4 + XGR + 8 * XM;
+        (L1 ? 0 : (size_t)E1 * E2) + 2 * E1 + E2 + XM + XNR * LD0 + XNR * LD1 + XGR * 4 + XGR + 8 * XM;
     static constexpr size_t SMEM = WD + BD + F64 * 8;
+    static_assert(!L1 || (XS * XNR * K1p * 2 <= BD && E2 <= XM1), "layer 1's digits use the row-digit buffer");
+    static_assert(SMEM + 1024 <= 232448, "dynamic plus static shared memory above the 227 KB opt-in limit");
 };
 
 template <int E1>
@@ -104,13 +143,16 @@ __global__ void __launch_bounds__(XT, 1) k_embed_fwd_x(DevModel m, const unsigne
                                                        double *__restrict__ Dout, int32_t *status)
 {
     using X = XShape<E1>;
-    constexpr int E2 = X::E2, E3 = X::E3, K2p = X::K2p, LD0 = X::LD0, LD1 = X::LD1;
+    constexpr int E2 = X::E2, E3 = X::E3, K2p = X::K2p, K1p = X::K1p, LD0 = X::LD0, LD1 = X::LD1;
+    constexpr bool L1 = X::L1;
     extern __shared__ __align__(1024) unsigned char smraw[];
     unsigned char *Wd = smraw;                                   // weight digits, then exponents
     const int *fexp = reinterpret_cast<const int *>(Wd + (size_t)XS * XM * K2p * 2);
+    unsigned char *Wd1 = Wd + w2_bytes(E1);                      // layer 1's weight digits (L1)
+    const int *fexp1 = reinterpret_cast<const int *>(Wd1 + (size_t)XS * XM1 * K1p * 2);
     unsigned char *Bd = Wd + X::WD;                              // row digits
-    double *W1s = reinterpret_cast<double *>(Bd + X::BD);
-    double *w0s = W1s + E1 * E2;
+    double *W1s = reinterpret_cast<double *>(Bd + X::BD);       // SIMT layer 1 only
+    double *w0s = W1s + (L1 ? 0 : E1 * E2);
     double *b0s = w0s + E1;
     double *b1s = b0s + E1;
     double *b2s = b1s + E2;
@@ -156,14 +198,15 @@ __global__ void __launch_bounds__(XT, 1) k_embed_fwd_x(DevModel m, const unsigne
                 __syncthreads();
                 if (tid == 0) {
                     mbar_expect_tx_x(&mbar_w, (uint32_t)X::WD);
-                    bulk_g2s_x(Wd, wx + (size_t)net * X::WD, (uint32_t)X::WD, &mbar_w);
+                    bulk_g2s_x(Wd, wx + (size_t)net * X::NB, (uint32_t)X::WD, &mbar_w);
                 }
                 const double *src = m.params + m.emb_base[net];
                 for (int q = tid; q < E1; q += XT) {
                     w0s[q] = src[q];
                     b0s[q] = src[E1 + q];
                 }
-                for (int q = tid; q < E1 * E2; q += XT) W1s[q] = src[2 * E1 + q];
+                if constexpr (!L1)
+                    for (int q = tid; q < E1 * E2; q += XT) W1s[q] = src[2 * E1 + q];
                 for (int q = tid; q < E2; q += XT) b1s[q] = src[2 * E1 + E1 * E2 + q];
                 for (int q = tid; q < XM; q += XT)
                     b2s[q] = q < E3 ? src[2 * E1 + E1 * E2 + E2 + E2 * E3 + q] : 0.0;
@@ -213,7 +256,80 @@ __global__ void __launch_bounds__(XT, 1) k_embed_fwd_x(DevModel m, const unsigne
                 }
                 __syncthreads();
                 // layer 1: h1 = (h0, h0) + tanh(h0 W1 + b1)
-                {
+                if constexpr (L1) {
+                    // digits of h0 (fixed scale: |h0| <= 1), then z1^T (64 features x 32 rows)
+                    for (int p = tid; p < XNR * (K1p / 8); p += XT) {
+                        const int row = p % XNR, k0 = (p / XNR) * 8;
+                        long long I[8];
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) {
+                            const double v = (k0 + q < E1) ? H0[row * LD0 + k0 + q] : 0.0;
+                            I[q] = __double2ll_rn(v * 36028797018963968.0);  // 2^55
+                        }
+                        const uint32_t ofs = tc::kmajor_offset(row, k0, K1p);
+                        for (int sd = XS - 1; sd >= 0; --sd) {
+                            int dg[8];
+#pragma unroll
+                            for (int q = 0; q < 8; ++q) dg[q] = sd > 0 ? oz_digit_step(I[q], XBETA) : (int)I[q];
+                            uint4 u;
+                            u.x = (uint32_t)oz_bf16_int(dg[0]) | ((uint32_t)oz_bf16_int(dg[1]) << 16);
+                            u.y = (uint32_t)oz_bf16_int(dg[2]) | ((uint32_t)oz_bf16_int(dg[3]) << 16);
+                            u.z = (uint32_t)oz_bf16_int(dg[4]) | ((uint32_t)oz_bf16_int(dg[5]) << 16);
+                            u.w = (uint32_t)oz_bf16_int(dg[6]) | ((uint32_t)oz_bf16_int(dg[7]) << 16);
+                            *reinterpret_cast<uint4 *>(Bd + (size_t)sd * XNR * K1p * 2 + ofs) = u;
+                        }
+                    }
+                    tc::fence_proxy_async();
+                    tc::fence_before_sync();
+                    __syncthreads();
+                    tc::fence_after_sync();
+                    if (tid == 0) {
+                        const uint32_t wa = tc::smem_u32(Wd1), ba = tc::smem_u32(Bd);
+                        const uint32_t idesc1 = tc::make_idesc_bf16(XM1, XNR);
+#pragma unroll
+                        for (int s = 1; s <= XS; ++s)
+#pragma unroll
+                            for (int t = 1; t + s <= XS + 1; ++t)
+#pragma unroll
+                                for (int kk = 0; kk < K1p / 16; ++kk)
+                                    tc::mma_bf16(
+                                        tbase + (uint32_t)(s + t - 2) * XNR,
+                                        tc::make_desc(wa + (uint32_t)(s - 1) * XM1 * K1p * 2 + kk * 256, 128, K1p * 16),
+                                        tc::make_desc(ba + (uint32_t)(t - 1) * XNR * K1p * 2 + kk * 256, 128, K1p * 16),
+                                        idesc1, s > 1 || kk > 0);
+                        tc::mma_commit(&mbar_m);
+                    }
+                    {
+                        const bool ok = tc::mbar_wait(&mbar_m, ph_m);
+                        ph_m ^= 1u;
+                        const bool bad = __syncthreads_or(!ok);
+                        tc::fence_after_sync();
+                        if (bad) {
+                            if (tid == 0) atomicOr(status, DPF_MMA_TIMEOUT);
+                            alive = false;
+                            pend_m = true;
+                            break;
+                        }
+                    }
+                    // epilogue: the warp's TMEM quarter holds features 16 (warp % 4) .. + 15 in
+                    // its first 16 lanes; lanes < 16 take rows 0..15, the others rows 16..31,
+                    // and warps w, w + 4 take 8 of them each
+                    const int f1 = 16 * (warp & 3) + (lane & 15);
+                    const int r0 = 16 * (lane >> 4) + 8 * (warp >> 2);
+                    double y1[8];
+                    combine_groups8(tlane + 8 * (uint32_t)(warp >> 2), y1);
+                    if (f1 < E2) {
+                        const double cv1 = oz_pow2(1 + fexp1[f1] - XBETA * (XS + 1));
+                        const double bb = b1s[f1];
+                        const int os = f1 < E1 ? f1 : f1 - E1;
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) {
+                            const int row = r0 + j;
+                            H1[row * LD1 + f1] = H0[row * LD0 + os] + dp_tanh64(fma(y1[j], cv1, bb), m.tanh_tab);
+                        }
+                    }
+                    tc::fence_before_sync();
+                } else {
                     const double *hr = H0 + lane * LD0;
                     for (int o = warp; o < E2; o += XT / 32) {
                         double z = b1s[o];
@@ -361,33 +477,40 @@ cudaError_t launch_fwd_x(cudaStream_t st, const DevModel &m, const unsigned char
 // ---------------------------------------------------------------- backward --
 //
 // k_embed_bwd_x recomputes G and its s-tangent dG/ds (G is never stored) with
-// the same split: layers 0 and 1 and their tangents on the FP64 units, the
-// last layer's two products z2 = h1 W2 and dz2 = dh1 W2 on the tensor cores
-// (h1 with the fixed scale 2^1, dh1 with a per-row power-of-two scale; the
-// two products run one after the other through the same digit buffer and
-// land in separate tensor-memory columns).  In the epilogue thread f forms
-// G[f] and dG[f] of its rows and the partials G gT[c][f], dG gT[c][f]; a warp
-// shuffle tree sums them over its 32 features, the four warps' sums are added
-// in fixed order, and warp 0 (one lane per row) applies the chain rule through
-// R~(r_ij) as k_embed_bwd does: pair gradients, the atom's own force and
-// virial parts.
+// the same split: layer 0 and its tangent on the FP64 units; layer 1's
+// products z1 = h0 W1 and dz1 = dh0 W1 (e1 <= 25; else on the FP64 units) and
+// the last layer's z2 = h1 W2 and dz2 = dh1 W2 on the tensor cores (values
+// with the fixed scale 2^1, tangents with a per-row power-of-two scale; a
+// value and its tangent land in separate tensor-memory columns).  In the last
+// layer's epilogue thread f forms G[f] and dG[f] of its rows and the partials
+// G gT[c][f], dG gT[c][f]; a warp shuffle tree sums them over its 32 features,
+// the four warps' sums are added in fixed order, and warp 0 (one lane per row)
+// applies the chain rule through R~(r_ij) as k_embed_bwd does: pair gradients,
+// the atom's own force and virial parts.
 
 template <int E1>
 struct XBShape {
-    static constexpr int E2 = 2 * E1, E3 = 4 * E1, K2p = k2p_of(E1);
+    static constexpr int E2 = 2 * E1, E3 = 4 * E1, K2p = k2p_of(E1), K1p = k1p_of(E1);
+    static constexpr bool L1 = l1tc_of(E1);  // layer 1 on the tensor cores
     // odd row strides (in doubles): one row per lane reads without bank conflicts
     static constexpr int LD0 = (E1 % 2) ? E1 + 2 : E1 + 1, LD1 = (E2 % 2) ? E2 + 2 : E2 + 1;
     static constexpr int GR = 64;  // rows whose geometry is staged at once
     static constexpr int GS = 11;  // doubles per staged row
-    static constexpr size_t WD = net_bytes(E1);
+    static constexpr size_t WD = net_bytes(E1);  // both layers' weight digits + exponents
+    static constexpr size_t NB = net_bytes(E1);
     static constexpr size_t BD = (size_t)XS * XNR * K2p * 2;
-    // FP64: W1, w0, b0, b1, b2, H0, dH0 (aliased by the reduction buffer), H1, dH1,
-    // geometry [GR][GS] (10 values, odd stride), gT [4][XM]
+    // FP64: W1 (SIMT layer 1 only), w0, b0, b1, b2, H0, dH0 (aliased by the reduction
+    // buffer), H1, dH1, geometry [GR][GS] (10 values, odd stride), gT [4][XM]
     static constexpr size_t H0SZ = (size_t)2 * XNR * LD0;
     static constexpr size_t RED = (size_t)8 * 16 * 8;
-    static constexpr size_t F64 = (size_t)E1 * E2 + 2 * E1 + E2 + XM + (H0SZ > RED ? H0SZ : RED) +
+    static constexpr size_t F64 = (L1 ? 0 : (size_t)E1 * E2) + 2 * E1 + E2 + XM + (H0SZ > RED ? H0SZ : RED) +
                                   2 * XNR * LD1 + GR * GS + 4 * XM;
-    static constexpr size_t SMEM = WD + BD + F64 * 8 + XNR * 4;
+    // + two [XNR] int32 row exponents (layer 2's and layer 1's tangent rows)
+    static constexpr size_t SMEM = WD + BD + F64 * 8 + 2 * XNR * 4;
+    static_assert(GR % XNR == 0 && GR <= XT, "geometry is staged one row per thread, whole chunks at a time");
+    static_assert(!L1 || (2 * XS * XNR * K1p * 2 <= BD && E2 <= XM1),
+                  "layer 1's value and tangent digits share the row-digit buffer");
+    static_assert(SMEM + 1024 <= 232448, "dynamic plus static shared memory above the 227 KB opt-in limit");
 };
 
 template <int E1>
@@ -402,13 +525,17 @@ __global__ void __launch_bounds__(XT, 1) k_embed_bwd_x(DevModel m, const unsigne
                                                        double *__restrict__ vir_part, int32_t *status)
 {
     using X = XBShape<E1>;
-    constexpr int E2 = X::E2, E3 = X::E3, K2p = X::K2p, LD0 = X::LD0, LD1 = X::LD1, GR = X::GR, GS = X::GS;
+    constexpr int E2 = X::E2, E3 = X::E3, K2p = X::K2p, K1p = X::K1p, LD0 = X::LD0, LD1 = X::LD1, GR = X::GR,
+                  GS = X::GS;
+    constexpr bool L1 = X::L1;
     extern __shared__ __align__(1024) unsigned char smraw[];
     unsigned char *Wd = smraw;
     const int *fexp = reinterpret_cast<const int *>(Wd + (size_t)XS * XM * K2p * 2);
+    unsigned char *Wd1 = Wd + w2_bytes(E1);  // layer 1's weight digits (L1)
+    const int *fexp1 = reinterpret_cast<const int *>(Wd1 + (size_t)XS * XM1 * K1p * 2);
     unsigned char *Bd = Wd + X::WD;
-    double *W1s = reinterpret_cast<double *>(Bd + X::BD);
-    double *w0s = W1s + E1 * E2;
+    double *W1s = reinterpret_cast<double *>(Bd + X::BD);  // SIMT layer 1 only
+    double *w0s = W1s + (L1 ? 0 : E1 * E2);
     double *b0s = w0s + E1;
     double *b1s = b0s + E1;
     double *b2s = b1s + E2;
@@ -420,6 +547,7 @@ __global__ void __launch_bounds__(XT, 1) k_embed_bwd_x(DevModel m, const unsigne
     double *geo = dH1 + XNR * LD1;  // [GR][GS]: s, ds, R[4], d[3], r
     double *gTs = geo + GR * GS;    // [4][XM]
     int *erow = reinterpret_cast<int *>(gTs + 4 * XM);  // [XNR] tangent row exponents
+    int *erow0 = erow + XNR;                            // [XNR] the same for layer 1's input (L1)
     __shared__ __align__(8) uint64_t mbar_w, mbar_m;
     __shared__ uint32_t tslot;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -494,6 +622,69 @@ __global__ void __launch_bounds__(XT, 1) k_embed_bwd_x(DevModel m, const unsigne
         __syncthreads();
         tc::fence_after_sync();
     };
+    // layer 1: digits of the 32 x E1 rows of H0 (fixed scale 2^55) at Bd and of dH0
+    // (row scale 2^(56 - erow0)) after them
+    auto make_digits1 = [&]() {
+        constexpr int NP = XNR * (K1p / 8);
+        for (int p = tid; p < 2 * NP; p += XT) {
+            const int which = p / NP, pp = p - which * NP;
+            const int row = pp % XNR, k0 = (pp / XNR) * 8;
+            const double *src = which ? dH0 : H0;
+            const double sc = oz_pow2(XBETA * XS - (which ? erow0[row] : 1));
+            long long I[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) I[q] = (k0 + q < E1) ? __double2ll_rn(src[row * LD0 + k0 + q] * sc) : 0ll;
+            const uint32_t ofs = tc::kmajor_offset(row, k0, K1p);
+            unsigned char *dst = Bd + (size_t)which * XS * XNR * K1p * 2;
+            for (int sd = XS - 1; sd >= 0; --sd) {
+                int dg[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) dg[q] = sd > 0 ? oz_digit_step(I[q], XBETA) : (int)I[q];
+                uint4 u;
+                u.x = (uint32_t)oz_bf16_int(dg[0]) | ((uint32_t)oz_bf16_int(dg[1]) << 16);
+                u.y = (uint32_t)oz_bf16_int(dg[2]) | ((uint32_t)oz_bf16_int(dg[3]) << 16);
+                u.z = (uint32_t)oz_bf16_int(dg[4]) | ((uint32_t)oz_bf16_int(dg[5]) << 16);
+                u.w = (uint32_t)oz_bf16_int(dg[6]) | ((uint32_t)oz_bf16_int(dg[7]) << 16);
+                *reinterpret_cast<uint4 *>(dst + (size_t)sd * XNR * K1p * 2 + ofs) = u;
+            }
+        }
+        tc::fence_proxy_async();
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+    };
+    // z1^T = W1^T digits x row digits (M = 64): value into 7 groups at column 0,
+    // tangent at column 256
+    auto mma_l1 = [&]() -> bool {
+        if (tid == 0) {
+            const uint32_t wa = tc::smem_u32(Wd1), ba = tc::smem_u32(Bd);
+            const uint32_t idesc1 = tc::make_idesc_bf16(XM1, XNR);
+#pragma unroll
+            for (int v = 0; v < 2; ++v)
+#pragma unroll
+                for (int s = 1; s <= XS; ++s)
+#pragma unroll
+                    for (int t = 1; t + s <= XS + 1; ++t)
+#pragma unroll
+                        for (int kk = 0; kk < K1p / 16; ++kk)
+                            tc::mma_bf16(
+                                tbase + (uint32_t)v * 256 + (uint32_t)(s + t - 2) * XNR,
+                                tc::make_desc(wa + (uint32_t)(s - 1) * XM1 * K1p * 2 + kk * 256, 128, K1p * 16),
+                                tc::make_desc(ba + (uint32_t)(v * XS + t - 1) * XNR * K1p * 2 + kk * 256, 128,
+                                              K1p * 16),
+                                idesc1, s > 1 || kk > 0);
+            tc::mma_commit(&mbar_m);
+        }
+        const bool ok = tc::mbar_wait(&mbar_m, ph_m);
+        ph_m ^= 1u;
+        const bool bad = __syncthreads_or(!ok);
+        tc::fence_after_sync();
+        if (bad) {
+            if (tid == 0) atomicOr(status, DPF_MMA_TIMEOUT);
+            pend_m = true;
+        }
+        return !bad;
+    };
 
     for (int ii = blockIdx.x; ii < N && alive; ii += gridDim.x) {
         const int i = type_perm[ii];
@@ -531,14 +722,15 @@ __global__ void __launch_bounds__(XT, 1) k_embed_bwd_x(DevModel m, const unsigne
                 __syncthreads();
                 if (tid == 0) {
                     mbar_expect_tx_x(&mbar_w, (uint32_t)X::WD);
-                    bulk_g2s_x(Wd, wx + (size_t)net * X::WD, (uint32_t)X::WD, &mbar_w);
+                    bulk_g2s_x(Wd, wx + (size_t)net * X::NB, (uint32_t)X::WD, &mbar_w);
                 }
                 const double *src = m.params + m.emb_base[net];
                 for (int q = tid; q < E1; q += XT) {
                     w0s[q] = src[q];
                     b0s[q] = src[E1 + q];
                 }
-                for (int q = tid; q < E1 * E2; q += XT) W1s[q] = src[2 * E1 + q];
+                if constexpr (!L1)
+                    for (int q = tid; q < E1 * E2; q += XT) W1s[q] = src[2 * E1 + q];
                 for (int q = tid; q < E2; q += XT) b1s[q] = src[2 * E1 + E1 * E2 + q];
                 for (int q = tid; q < XM; q += XT)
                     b2s[q] = q < E3 ? src[2 * E1 + E1 * E2 + E2 + E2 * E3 + q] : 0.0;
@@ -594,7 +786,55 @@ __global__ void __launch_bounds__(XT, 1) k_embed_bwd_x(DevModel m, const unsigne
                 }
                 __syncthreads();
                 // layer 1 and its tangent
-                {
+                if constexpr (L1) {
+                    // tangent row exponents of layer 1's input: 2^e > max_k |dh0[row][k]|
+                    {
+                        const int row = tid >> 3, part = tid & 7;
+                        double mx = 0.0;
+                        if (row < XNR)
+                            for (int k = part; k < E1; k += 8) mx = fmax(mx, fabs(dH0[row * LD0 + k]));
+#pragma unroll
+                        for (int o = 4; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+                        if (row < XNR && part == 0) {
+                            int e = 0;
+                            if (mx > 0.0) {
+                                frexp(mx, &e);
+                                e = max(e, -900);
+                            }
+                            erow0[row] = e;
+                        }
+                    }
+                    __syncthreads();
+                    make_digits1();
+                    if (!mma_l1()) {
+                        alive = false;
+                        break;
+                    }
+                    // epilogue: the warp's TMEM quarter holds features 16 (warp % 4) .. + 15 in
+                    // its first 16 lanes; lanes < 16 take rows 0..15, the others rows 16..31,
+                    // and warps w, w + 4 take 8 of them each
+                    const int f1 = 16 * (warp & 3) + (lane & 15);
+                    const int r0 = 16 * (lane >> 4) + 8 * (warp >> 2);
+                    const uint32_t ta = tlane + 8 * (uint32_t)(warp >> 2);
+                    double y1[8], dy1[8];
+                    combine_groups8(ta, y1);
+                    combine_groups8(ta + 256, dy1);
+                    if (f1 < E2) {
+                        const int fx1 = fexp1[f1];
+                        const double cv1 = oz_pow2(1 + fx1 - XBETA * (XS + 1));
+                        const double bb = b1s[f1];
+                        const int os = f1 < E1 ? f1 : f1 - E1;
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) {
+                            const int row = r0 + j;
+                            const double t = dp_tanh64(fma(y1[j], cv1, bb), m.tanh_tab);
+                            const double dz = dy1[j] * oz_pow2(erow0[row] + fx1 - XBETA * (XS + 1));
+                            H1[row * LD1 + f1] = H0[row * LD0 + os] + t;
+                            dH1[row * LD1 + f1] = fma(fma(-t, t, 1.0), dz, dH0[row * LD0 + os]);
+                        }
+                    }
+                    tc::fence_before_sync();
+                } else {
                     const double *hr = H0 + lane * LD0, *dhr = dH0 + lane * LD0;
                     for (int o = warp; o < E2; o += XT / 32) {
                         double z = b1s[o], dz = 0.0;
@@ -780,36 +1020,50 @@ bool dp_ex_supported(const DevModel &m)
 
 size_t dp_ex_bytes(const DevModel &m) { return (size_t)m.ntypes * m.ntypes * net_bytes(m.emb[0]); }
 
+// Digits of the columns of W [K][F] (row-major) as the rows of an Mrows x Kp
+// K-major operand: row f holds column f of W scaled by 2^(56 - e_f), 2^e_f > max |W[., f]|
+// (e_f = 0 and zero digits for an all-zero or too small column).
+static void split_columns(const double *W, int K, int F, int Mrows, int Kp, uint16_t *dig, int32_t *ex)
+{
+    for (int f = 0; f < Mrows; ++f) {
+        double mx = 0.0;
+        if (f < F)
+            for (int k = 0; k < K; ++k) mx = std::max(mx, std::fabs(W[(size_t)k * F + f]));
+        int ef = 0;
+        bool zero = !(mx > 0.0);
+        if (!zero) {
+            std::frexp(mx, &ef);
+            if (ef < XBETA * XS - 1020) zero = true;
+        }
+        if (zero) ef = 0;
+        ex[f] = ef;
+        const double scale = zero ? 0.0 : std::ldexp(1.0, XBETA * XS - ef);
+        for (int k = 0; k < Kp; ++k) {
+            long long I = (f < F && k < K) ? std::llrint(W[(size_t)k * F + f] * scale) : 0;
+            const uint32_t ofs = tc::kmajor_offset(f, k, Kp) / 2;
+            for (int sd = XS - 1; sd >= 0; --sd) {
+                const int d = sd > 0 ? oz_digit_step(I, XBETA) : (int)I;
+                dig[(size_t)sd * Mrows * Kp + ofs] = oz_bf16_int(d);
+            }
+        }
+    }
+}
+
 void dp_ex_split_weights(const DevModel &m, const double *h_params, unsigned char *out)
 {
-    const int e1 = m.emb[0], e2 = 2 * e1, e3 = 4 * e1, K2p = k2p_of(e1);
+    const int e1 = m.emb[0], e2 = 2 * e1, e3 = 4 * e1, K2p = k2p_of(e1), K1p = k1p_of(e1);
     const size_t nb = net_bytes(e1);
     for (int net = 0; net < m.ntypes * m.ntypes; ++net) {
-        const double *W2 = h_params + m.emb_base[net] + 2 * e1 + e1 * e2 + e2;  // [e2][e3]
-        uint16_t *dig = reinterpret_cast<uint16_t *>(out + (size_t)net * nb);
-        int32_t *ex = reinterpret_cast<int32_t *>(out + (size_t)net * nb + (size_t)XS * XM * K2p * 2);
-        std::memset(out + (size_t)net * nb, 0, nb);
-        for (int f = 0; f < XM; ++f) {
-            double mx = 0.0;
-            if (f < e3)
-                for (int k = 0; k < e2; ++k) mx = std::max(mx, std::fabs(W2[(size_t)k * e3 + f]));
-            int ef = 0;
-            bool zero = !(mx > 0.0);
-            if (!zero) {
-                std::frexp(mx, &ef);
-                if (ef < XBETA * XS - 1020) zero = true;
-            }
-            if (zero) ef = 0;
-            ex[f] = ef;
-            const double scale = zero ? 0.0 : std::ldexp(1.0, XBETA * XS - ef);
-            for (int k = 0; k < K2p; ++k) {
-                long long I = (f < e3 && k < e2) ? std::llrint(W2[(size_t)k * e3 + f] * scale) : 0;
-                const uint32_t ofs = tc::kmajor_offset(f, k, K2p) / 2;
-                for (int sd = XS - 1; sd >= 0; --sd) {
-                    const int d = sd > 0 ? oz_digit_step(I, XBETA) : (int)I;
-                    dig[(size_t)sd * XM * K2p + ofs] = oz_bf16_int(d);
-                }
-            }
+        unsigned char *blk = out + (size_t)net * nb;
+        std::memset(blk, 0, nb);
+        const double *W1 = h_params + m.emb_base[net] + 2 * e1;  // [e1][e2]
+        const double *W2 = W1 + e1 * e2 + e2;                    // [e2][e3]
+        split_columns(W2, e2, e3, XM, K2p, reinterpret_cast<uint16_t *>(blk),
+                      reinterpret_cast<int32_t *>(blk + (size_t)XS * XM * K2p * 2));
+        if (l1tc_of(e1)) {
+            unsigned char *b1 = blk + w2_bytes(e1);
+            split_columns(W1, e1, e2, XM1, K1p, reinterpret_cast<uint16_t *>(b1),
+                          reinterpret_cast<int32_t *>(b1 + (size_t)XS * XM1 * K1p * 2));
         }
     }
 }

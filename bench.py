@@ -50,7 +50,7 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 TRAFFIC = {
     # ncu --set full, one 12,288-atom water evaluation (bench.py --profile-eval 2):
     # dram__bytes_read.sum + dram__bytes_write.sum of the dominant kernel
-    "embed_bwd": {"bytes_per_launch": 206.536704e6 + 22.095360e6, "file": "embed_x.cu", "src_sha": "c3be755e30744d24"},
+    "embed_bwd": {"bytes_per_launch": 206.658048e6 + 21.853696e6, "file": "embed_x.cu", "src_sha": "2d054be16c9e9e06"},
     "embed_bwd_mx<25>": {"bytes_per_launch": 204.936448e6 + 17.953792e6, "file": "mixed.cu", "src_sha": "f7e14a0339b2fab3"},
 }
 
@@ -445,8 +445,8 @@ def run_ours(args, rank, world, local_rank):
         roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
                 "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
                 "peak_source": "FP64 pipe: 152 SMs x 2 FMA/clk x 2 FLOP x 2.07 GHz (nominal 1.25 TFLOP/s)",
-                "note": "algorithmic FP64 FLOPs; the last embedding layer's products run on the tensor cores "
-                        "by exact splitting (FP64 accuracy), the rest on the FP64 pipe",
+                "note": "algorithmic FP64 FLOPs; the embedding net's dense layers (layer 1 and the last) run "
+                        "on the tensor cores by exact splitting (FP64 accuracy), the rest on the FP64 pipe",
                 "flops_per_launch": flops[dom], "rows_per_launch": rows}
     th_all = torch.stack(thermo_all).cpu().numpy().reshape(-1, 4)
     etot = th_all[:, 0] + th_all[:, 1]

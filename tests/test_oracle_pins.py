@@ -452,6 +452,58 @@ def test_md_time_reversible(oracle, synth):
     np.testing.assert_allclose(-v2, v0, atol=1e-10)
 
 
+# Unit conversions from the SI definitions (amu, eV, k_B exact in the 2019 SI
+# or CODATA 2018), independent of the oracle's own constants.
+_AMU_KG = 1.66053906660e-27
+_EV_J = 1.602176634e-19
+_KB_J = 1.380649e-23
+_AMU_A2_FS2_IN_EV = _AMU_KG * 1e10 / _EV_J       # 1 amu (A/fs)^2 in eV
+_ACC_A_FS2 = _EV_J / 1e-10 / _AMU_KG * 1e-20     # 1 eV/A/amu in A/fs^2
+
+
+def test_md_one_step_is_velocity_verlet(oracle, synth):
+    """One step from (x0, v0): x1 = x0 + dt v0 + dt^2/2 a0, v1 = v0 + dt/2 (a0 + a1),
+    a = F/m in A/fs^2, F from the evaluator at x0 and x1 (Sec. 4)."""
+    w = synth.workload("water192")
+    P = synth.model_params(w["model"], 0)
+    m = np.array(w["masses"])[w["types"]]
+    v0 = synth.maxwell_velocities(m, 300.0, seed=5)
+    dt = 0.5
+    x1, v1, f1, _, _ = oracle.md(w["model"], P, w["coords"], v0, w["types"], w["box"], w["masses"], dt, 1,
+                                 rebuild_every=1, skin=0.0)
+    f0 = oracle.evaluate(w["model"], P, w["coords"], w["types"], w["box"])["force"]
+    a0 = f0 / m[:, None] * _ACC_A_FS2
+    x1_ref = np.mod(w["coords"] + dt * v0 + 0.5 * dt * dt * a0, w["box"])
+    d = x1 - x1_ref
+    d -= w["box"] * np.round(d / w["box"])
+    assert np.abs(d).max() < 1e-12
+    f1_ref = oracle.evaluate(w["model"], P, x1, w["types"], w["box"])["force"]
+    np.testing.assert_allclose(f1, f1_ref, rtol=0, atol=1e-13 * np.abs(f1_ref).max())
+    v1_ref = v0 + 0.5 * dt * (a0 + f1_ref / m[:, None] * _ACC_A_FS2)
+    np.testing.assert_allclose(v1, v1_ref, rtol=0, atol=1e-12 * np.abs(v1_ref).max())
+
+
+def test_md_thermo_definitions(oracle, synth):
+    """thermo = (E_pot, E_kin, T, P) of the configuration after the step:
+    E_kin = sum m v^2 / 2, T = 2 E_kin / ((3N - 3) k_B), P = (2 E_kin + tr Xi) / (3V)."""
+    w = synth.workload("water192")
+    P = synth.model_params(w["model"], 0)
+    m = np.array(w["masses"])[w["types"]]
+    v0 = synth.maxwell_velocities(m, 300.0, seed=6)
+    x, v, _, th, _ = oracle.md(w["model"], P, w["coords"], v0, w["types"], w["box"], w["masses"], 0.5, 3,
+                               rebuild_every=1, skin=0.0)
+    out = oracle.evaluate(w["model"], P, x, w["types"], w["box"])
+    n = len(m)
+    ke = 0.5 * float((m[:, None] * v * v).sum()) * _AMU_A2_FS2_IN_EV
+    temp = 2.0 * ke / ((3 * n - 3) * _KB_J / _EV_J)
+    vol = float(np.prod(w["box"]))
+    pres = (2.0 * ke + float(np.trace(np.asarray(out["virial"]).reshape(3, 3)))) / (3.0 * vol)
+    assert th[-1, 0] == pytest.approx(out["energy"], rel=1e-13)
+    assert th[-1, 1] == pytest.approx(ke, rel=1e-9)
+    assert th[-1, 2] == pytest.approx(temp, rel=1e-9)
+    assert th[-1, 3] == pytest.approx(pres, rel=1e-9)
+
+
 # ------------------------------------------------------- parameter gradient --
 
 def _phi(oracle, desc, P, w, cE, lam):

@@ -43,13 +43,15 @@ constexpr int XM1 = 64;      // output features of the layer-1 MMA (M), 2 e1 <= 
 
 constexpr int k2p_of(int e1) { return (2 * e1 + 15) / 16 * 16; }
 constexpr int k1p_of(int e1) { return (e1 + 15) / 16 * 16; }
-// layer 1 (e1 -> 2 e1) on the tensor cores as well: where its weight digits fit
-// in shared memory next to the backward kernel's buffers
-constexpr bool l1tc_of(int e1) { return e1 <= 25; }
+// layer 1 (e1 -> 2 e1) on the tensor cores as well, where its weight digits fit
+// in shared memory next to each kernel's buffers: the forward kernel for every
+// supported width, the backward kernel (more FP64 rows) up to e1 = 25
+constexpr bool l1fwd_of(int e1) { return e1 <= 32; }
+constexpr bool l1bwd_of(int e1) { return e1 <= 25; }
 // bytes of the last layer's weights: digits [XS][128 x K2p] bf16, then 128 int32 exponents
 constexpr size_t w2_bytes(int e1) { return (size_t)XS * XM * k2p_of(e1) * 2 + XM * 4; }
 // bytes of layer 1's weights: digits [XS][64 x K1p] bf16, then 64 int32 exponents
-constexpr size_t w1_bytes(int e1) { return l1tc_of(e1) ? (size_t)XS * XM1 * k1p_of(e1) * 2 + XM1 * 4 : 0; }
+constexpr size_t w1_bytes(int e1) { return l1fwd_of(e1) ? (size_t)XS * XM1 * k1p_of(e1) * 2 + XM1 * 4 : 0; }
 // bytes of one net's weight block: the last layer's part, then layer 1's
 constexpr size_t net_bytes(int e1) { return w2_bytes(e1) + w1_bytes(e1); }
 
@@ -118,7 +120,7 @@ __device__ __forceinline__ void combine_groups8(uint32_t taddr, double (&y)[8])
 template <int E1>
 struct XShape {
     static constexpr int E2 = 2 * E1, E3 = 4 * E1, K2p = k2p_of(E1), K1p = k1p_of(E1);
-    static constexpr bool L1 = l1tc_of(E1);  // layer 1 on the tensor cores
+    static constexpr bool L1 = l1fwd_of(E1);  // layer 1 on the tensor cores
     // odd row strides (in doubles): one row per lane reads without bank conflicts
     static constexpr int LD0 = (E1 % 2) ? E1 + 2 : E1 + 1, LD1 = (E2 % 2) ? E2 + 2 : E2 + 1;
     static constexpr size_t WD = net_bytes(E1);              // weight digits + exponents (both layers)
@@ -491,12 +493,13 @@ cudaError_t launch_fwd_x(cudaStream_t st, const DevModel &m, const unsigned char
 template <int E1>
 struct XBShape {
     static constexpr int E2 = 2 * E1, E3 = 4 * E1, K2p = k2p_of(E1), K1p = k1p_of(E1);
-    static constexpr bool L1 = l1tc_of(E1);  // layer 1 on the tensor cores
+    static constexpr bool L1 = l1bwd_of(E1);  // layer 1 on the tensor cores
     // odd row strides (in doubles): one row per lane reads without bank conflicts
     static constexpr int LD0 = (E1 % 2) ? E1 + 2 : E1 + 1, LD1 = (E2 % 2) ? E2 + 2 : E2 + 1;
     static constexpr int GR = 64;  // rows whose geometry is staged at once
     static constexpr int GS = 11;  // doubles per staged row
-    static constexpr size_t WD = net_bytes(E1);  // both layers' weight digits + exponents
+    // weight digits + exponents copied: the last layer's, and layer 1's (L1)
+    static constexpr size_t WD = w2_bytes(E1) + (L1 ? w1_bytes(E1) : 0);
     static constexpr size_t NB = net_bytes(E1);
     static constexpr size_t BD = (size_t)XS * XNR * K2p * 2;
     // FP64: W1 (SIMT layer 1 only), w0, b0, b1, b2, H0, dH0 (aliased by the reduction
@@ -1060,7 +1063,7 @@ void dp_ex_split_weights(const DevModel &m, const double *h_params, unsigned cha
         const double *W2 = W1 + e1 * e2 + e2;                    // [e2][e3]
         split_columns(W2, e2, e3, XM, K2p, reinterpret_cast<uint16_t *>(blk),
                       reinterpret_cast<int32_t *>(blk + (size_t)XS * XM * K2p * 2));
-        if (l1tc_of(e1)) {
+        if (w1_bytes(e1) > 0) {
             unsigned char *b1 = blk + w2_bytes(e1);
             split_columns(W1, e1, e2, XM1, K1p, reinterpret_cast<uint16_t *>(b1),
                           reinterpret_cast<int32_t *>(b1 + (size_t)XS * XM1 * K1p * 2));

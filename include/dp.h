@@ -83,9 +83,9 @@ typedef struct dp_ctx dp_ctx;
 #define DP_PREC_FP64  0   /* every step with float64 accuracy; the dense products
                              (the fitting-net GEMMs and, for 3-layer doubling
                              embedding nets with s_1 in {16, 25, 32}, the last
-                             embedding layer and its s-tangent, and layer 1 with,
-                             for s_1 <= 25, its s-tangent) run on the tensor
-                             cores as exact products of BF16 digit expansions of
+                             embedding layer and layer 1 with their s-tangents)
+                             run on the tensor cores as exact products of BF16
+                             digit expansions of
                              the FP64 operands (every partial sum an integer
                              below 2^24, held exactly by the FP32 accumulators),
                              the rest on the FP64 units; other shapes run as

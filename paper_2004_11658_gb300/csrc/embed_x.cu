@@ -44,10 +44,9 @@ constexpr int XM1 = 64;      // output features of the layer-1 MMA (M), 2 e1 <= 
 constexpr int k2p_of(int e1) { return (2 * e1 + 15) / 16 * 16; }
 constexpr int k1p_of(int e1) { return (e1 + 15) / 16 * 16; }
 // layer 1 (e1 -> 2 e1) on the tensor cores as well, where its weight digits fit
-// in shared memory next to each kernel's buffers: the forward kernel for every
-// supported width, the backward kernel (more FP64 rows) up to e1 = 25
+// in shared memory next to each kernel's buffers (both kernels, every supported width)
 constexpr bool l1fwd_of(int e1) { return e1 <= 32; }
-constexpr bool l1bwd_of(int e1) { return e1 <= 25; }
+constexpr bool l1bwd_of(int e1) { return e1 <= 32; }
 // bytes of the last layer's weights: digits [XS][128 x K2p] bf16, then 128 int32 exponents
 constexpr size_t w2_bytes(int e1) { return (size_t)XS * XM * k2p_of(e1) * 2 + XM * 4; }
 // bytes of layer 1's weights: digits [XS][64 x K1p] bf16, then 64 int32 exponents
@@ -503,11 +502,13 @@ struct XBShape {
     static constexpr size_t NB = net_bytes(E1);
     static constexpr size_t BD = (size_t)XS * XNR * K2p * 2;
     // FP64: W1 (SIMT layer 1 only), w0, b0, b1, b2, H0, dH0 (aliased by the reduction
-    // buffer), H1, dH1, geometry [GR][GS] (10 values, odd stride), gT [4][XM]
+    // buffer), H1, dH1 (aliased by gT [4][XM] in each atom's prologue), geometry [GR][GS]
+    // (10 values, odd stride)
     static constexpr size_t H0SZ = (size_t)2 * XNR * LD0;
     static constexpr size_t RED = (size_t)8 * 16 * 8;
     static constexpr size_t F64 = (L1 ? 0 : (size_t)E1 * E2) + 2 * E1 + E2 + XM + (H0SZ > RED ? H0SZ : RED) +
-                                  2 * XNR * LD1 + GR * GS + 4 * XM;
+                                  2 * XNR * LD1 + GR * GS;
+    static_assert(4 * XM <= XNR * LD1 && 4 * E3 <= XNR * LD1, "T and gT fit in the h1 and dh1 rows");
     // + two [XNR] int32 row exponents (layer 2's and layer 1's tangent rows)
     static constexpr size_t SMEM = WD + BD + F64 * 8 + 2 * XNR * 4;
     static_assert(GR % XNR == 0 && GR <= XT, "geometry is staged one row per thread, whole chunks at a time");
@@ -548,8 +549,10 @@ __global__ void __launch_bounds__(XT, 1) k_embed_bwd_x(DevModel m, const unsigne
     double *H1 = H0 + (X::H0SZ > X::RED ? X::H0SZ : X::RED);
     double *dH1 = H1 + XNR * LD1;
     double *geo = dH1 + XNR * LD1;  // [GR][GS]: s, ds, R[4], d[3], r
-    double *gTs = geo + GR * GS;    // [4][XM]
-    int *erow = reinterpret_cast<int *>(gTs + 4 * XM);  // [XNR] tangent row exponents
+    // gT [4][XM] of the atom: written and read into registers in the atom's prologue,
+    // before the first chunk writes dh1
+    double *gTs = dH1;
+    int *erow = reinterpret_cast<int *>(geo + GR * GS);  // [XNR] tangent row exponents
     int *erow0 = erow + XNR;                            // [XNR] the same for layer 1's input (L1)
     __shared__ __align__(8) uint64_t mbar_w, mbar_m;
     __shared__ uint32_t tslot;

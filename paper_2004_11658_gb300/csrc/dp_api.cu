@@ -143,7 +143,7 @@ struct dp_ctx {
     uint16_t *d_oz_w;
     int32_t *d_oz_e;
     int64_t oz_w_elems, oz_e_elems, oz_version;
-    // FP64 embedding forward with its last layer on the tensor cores: weight digits per net
+    // FP64 embedding kernels with layers 1 and 2 on the tensor cores: weight digits per net
     bool use_ex;
     unsigned char *d_ex_w;
     int64_t ex_version;

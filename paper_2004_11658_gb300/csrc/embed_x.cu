@@ -4,9 +4,8 @@
 //
 // The doubling embedding net (widths e1, 2e1, 4e1) costs 2 e1 (2 e1) + 2 (2 e1)(4 e1)
 // FLOP per neighbour row.  Layer 0 (1 -> e1) runs on the FP64 units (one row
-// per lane, the warps splitting the columns); the last layer, and layer 1 where
-// its weight digits fit in shared memory (e1 <= 25), are exact products of
-// digit expansions (as the fitting net's GEMMs, csrc/fit_oz.cu):
+// per lane, the warps splitting the columns); layer 1 and the last layer are
+// exact products of digit expansions (as the fitting net's GEMMs, csrc/fit_oz.cu):
 //   h (|h| < 2)   -> S = 7 digits in base 2^8 of round(h 2^55),
 //   W column f    -> 7 digits of round(W[., f] 2^(56 - f_f)),  2^f_f > max |W[., f]|,
 //   z[f][row] = 2^(1 + f_f) sum_{g=2}^{8} 2^(-8 g) C_g,  C_g = sum_{s+t=g} A_s B_t,
@@ -479,10 +478,10 @@ cudaError_t launch_fwd_x(cudaStream_t st, const DevModel &m, const unsigned char
 //
 // k_embed_bwd_x recomputes G and its s-tangent dG/ds (G is never stored) with
 // the same split: layer 0 and its tangent on the FP64 units; layer 1's
-// products z1 = h0 W1 and dz1 = dh0 W1 (e1 <= 25; else on the FP64 units) and
-// the last layer's z2 = h1 W2 and dz2 = dh1 W2 on the tensor cores (values
-// with the fixed scale 2^1, tangents with a per-row power-of-two scale; a
-// value and its tangent land in separate tensor-memory columns).  In the last
+// products z1 = h0 W1 and dz1 = dh0 W1 and the last layer's z2 = h1 W2 and
+// dz2 = dh1 W2 on the tensor cores (values with the fixed scale 2^1, tangents
+// with a per-row power-of-two scale; a value and its tangent land in separate
+// tensor-memory columns).  In the last
 // layer's epilogue thread f forms G[f] and dG[f] of its rows and the partials
 // G gT[c][f], dG gT[c][f]; a warp shuffle tree sums them over its 32 features,
 // the four warps' sums are added in fixed order, and warp 0 (one lane per row)

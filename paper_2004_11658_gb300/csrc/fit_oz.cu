@@ -24,11 +24,11 @@
 // K-major layout of the MMA A operand (16-column chunks).  The weights'
 // digits are made once on the host.  k_oz_gemm: one CTA per (tile, 32-column
 // chunk of Y); one thread streams the digit chunks of A and W with bulk copies
-// (cp.async.bulk, 3-stage ring on mbarriers) and issues S(S+1)/2 MMAs of
-// 128 x 32 x 16 per chunk into S group accumulators in tensor memory; the
-// epilogue (4 warps, one row per thread) combines the groups in FP64 and
-// applies the layer's bias, tanh and skip (forward) or the skip gradient
-// (backward).  Every wait is bounded; on a timeout the kernel sets
+// (cp.async.bulk, a 2- to 4-stage ring on mbarriers) and issues S(S+1)/2 MMAs
+// of 128 x 32 x 16 per chunk into S group accumulators in tensor memory; the
+// epilogue (4 warps, one row per thread) combines the groups exactly in int64,
+// converts once (one rounding) and applies the layer's bias, tanh and skip
+// (forward) or the skip gradient (backward).  Every wait is bounded; on a timeout the kernel sets
 // DPF_MMA_TIMEOUT, waits for its copies and MMAs, frees tensor memory and
 // returns.
 #include <algorithm>
@@ -315,37 +315,51 @@ __global__ void __launch_bounds__(DP_OZ_TILE, 1) k_oz_gemm(OzGemmArgs p)
         const int r = tid;
         const int i = r < T.cnt ? p.type_perm[T.first + r] : -1;
         const uint32_t tl_lane = tbase + ((uint32_t)(32 * warp) << 16);
-        double y[DP_OZ_NC];
+        // y = sum_{g=2}^{S+1} C_g 2^(beta (S + 1 - g)): the group sums are integers
+        // below 2^24, combined exactly in two int64 Horner chains (the H groups of
+        // largest scale, then the rest; each chain below 2^(25 + beta (H - 1)) <= 2^53
+        // for every (beta, S) of oz_beta) and converted once: y = hi 2^(beta (S - H)) + lo.
+        // Then y 2^escale = sum_g C_g 2^(-beta g).  Sixteen columns at a time.
+        constexpr int H = (S + 1) / 2;
+        const long long sh = 1ll << g.beta;
+        const double chi = oz_pow2(g.beta * (S - H));
+        const int escale = -g.beta * (S + 1);
+        const int er = i >= 0 ? p.aexp[(size_t)tl * DP_OZ_TILE + r] : 0;
+#pragma unroll 1
+        for (int h = 0; h < 2; ++h) {
+            long long hi[16], lo[16];
+            __syncwarp();  // the loads below are warp-wide; the previous half's stores diverge
 #pragma unroll
-        for (int n = 0; n < DP_OZ_NC; ++n) y[n] = 0.0;
-        // groups from the smallest scale up
-        for (int gg = S + 1; gg >= 2; --gg) {
-            float v0[16], v1[16];
-            tc::tmem_ld16(tl_lane + (uint32_t)(gg - 2) * DP_OZ_NC, v0);
-            tc::tmem_ld16(tl_lane + (uint32_t)(gg - 2) * DP_OZ_NC + 16, v1);
-            const double c = oz_pow2(-g.beta * gg);
+            for (int gg = 2; gg <= S + 1; ++gg) {
+                float v[16];
+                tc::tmem_ld16(tl_lane + (uint32_t)(gg - 2) * DP_OZ_NC + 16 * h, v);
 #pragma unroll
-            for (int n = 0; n < 16; ++n) {
-                y[n] = fma((double)v0[n], c, y[n]);
-                y[16 + n] = fma((double)v1[n], c, y[16 + n]);
+                for (int n = 0; n < 16; ++n) {
+                    const long long iv = (long long)__float2int_rn(v[n]);
+                    if (gg == 2) hi[n] = iv;
+                    else if (gg <= H + 1) hi[n] = hi[n] * sh + iv;
+                    else if (gg == H + 2) lo[n] = iv;
+                    else lo[n] = lo[n] * sh + iv;
+                }
             }
-        }
-        if (i >= 0) {
-            const int er = p.aexp[(size_t)tl * DP_OZ_TILE + r];
-            const int *fe = fe_s;
-            const int n0 = nchunk * DP_OZ_NC;
+            if (i < 0) continue;
+            const int c0 = 16 * h;                       // first column of this half in the chunk
+            const int n0 = nchunk * DP_OZ_NC + c0;       // ... and in Y
+            const int *fe = fe_s + c0;
+            const double *bs = bias_s + c0;
             double *ho = p.hout + (size_t)i * p.ldo;
             if (p.epi == 0) {
-                const double *hi = p.hin + (size_t)i * p.ldh;
+                const double *hin = p.hin + (size_t)i * p.ldh;
                 double *to = p.tout + (size_t)i * p.ldo;
 #pragma unroll
-                for (int n = 0; n < DP_OZ_NC; ++n) {
+                for (int n = 0; n < 16; ++n) {
                     const int col = n0 + n;
                     if (col < g.N) {
-                        const double z = ldexp(y[n], er + fe[n]) + bias_s[n];
+                        const double y = fma((double)hi[n], chi, (double)lo[n]);
+                        const double z = ldexp(y, er + fe[n] + escale) + bs[n];
                         const double t = dp_tanh64(z, p.tanh_tab);
                         const double sk =
-                            p.skip == 2 ? hi[col % p.skip_in] : (p.skip == 1 ? hi[col] : 0.0);
+                            p.skip == 2 ? hin[col % p.skip_in] : (p.skip == 1 ? hin[col] : 0.0);
                         to[col] = t;
                         ho[col] = sk + t;
                     }
@@ -353,10 +367,10 @@ __global__ void __launch_bounds__(DP_OZ_TILE, 1) k_oz_gemm(OzGemmArgs p)
             } else {
                 const double *gh = p.gbc[T.a] != nullptr ? p.gbc[T.a] : p.hin + (size_t)i * p.ldh;
 #pragma unroll
-                for (int n = 0; n < DP_OZ_NC; ++n) {
+                for (int n = 0; n < 16; ++n) {
                     const int q = n0 + n;
                     if (q < g.N) {
-                        double v = ldexp(y[n], er + fe[n]);
+                        double v = ldexp(fma((double)hi[n], chi, (double)lo[n]), er + fe[n] + escale);
                         if (p.skip == 1) v += gh[q];
                         else if (p.skip == 2) v += gh[q] + gh[q + p.skip_in];
                         ho[q] = v;

@@ -214,6 +214,13 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t *mbar, uint32_t bytes)
                  : "memory");
 }
 
+// y 2^e: one multiplication while 2^e is a normal number (exact, or rounded
+// once when the product is subnormal, as ldexp rounds it), ldexp otherwise
+__device__ __forceinline__ double scale2(double y, int e)
+{
+    return (e >= -1022 && e <= 1023) ? y * oz_pow2(e) : ldexp(y, e);
+}
+
 template <int S>
 __global__ void __launch_bounds__(DP_OZ_TILE, 1) k_oz_gemm(OzGemmArgs p)
 {
@@ -355,8 +362,8 @@ __global__ void __launch_bounds__(DP_OZ_TILE, 1) k_oz_gemm(OzGemmArgs p)
                 for (int n = 0; n < 16; ++n) {
                     const int col = n0 + n;
                     if (col < g.N) {
-                        const double y = fma((double)hi[n], chi, (double)lo[n]);
-                        const double z = ldexp(y, er + fe[n] + escale) + bs[n];
+                        const double z =
+                            scale2(fma((double)hi[n], chi, (double)lo[n]), er + fe[n] + escale) + bs[n];
                         const double t = dp_tanh64(z, p.tanh_tab);
                         const double sk =
                             p.skip == 2 ? hin[col % p.skip_in] : (p.skip == 1 ? hin[col] : 0.0);
@@ -370,7 +377,7 @@ __global__ void __launch_bounds__(DP_OZ_TILE, 1) k_oz_gemm(OzGemmArgs p)
                 for (int n = 0; n < 16; ++n) {
                     const int q = n0 + n;
                     if (q < g.N) {
-                        double v = ldexp(fma((double)hi[n], chi, (double)lo[n]), er + fe[n] + escale);
+                        double v = scale2(fma((double)hi[n], chi, (double)lo[n]), er + fe[n] + escale);
                         if (p.skip == 1) v += gh[q];
                         else if (p.skip == 2) v += gh[q] + gh[q + p.skip_in];
                         ho[q] = v;

@@ -51,8 +51,8 @@ TRAFFIC = {
     # ncu (--set full, or the two DRAM metrics alone) on one 12,288-atom water
     # evaluation (bench.py --profile-eval 2): dram__bytes_read.sum +
     # dram__bytes_write.sum of the dominant kernel
-    "embed_bwd": {"bytes_per_launch": 206.746112e6 + 21.276672e6, "file": "embed_x.cu", "src_sha": "d8075d8840f6fec3"},
-    "embed_bwd_mx<25>": {"bytes_per_launch": 204.936448e6 + 17.953792e6, "file": "mixed.cu", "src_sha": "f7e14a0339b2fab3"},
+    "embed_bwd": {"bytes_per_launch": 206.746112e6 + 21.276672e6, "file": "embed_x.cu", "src_sha": "8c4c5603a99cc6ec"},
+    "embed_bwd_mx<25>": {"bytes_per_launch": 204.936448e6 + 17.953792e6, "file": "mixed.cu", "src_sha": "97f3fe1bf34f81b7"},
 }
 
 

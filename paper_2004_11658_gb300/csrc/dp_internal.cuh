@@ -107,7 +107,7 @@ cudaError_t dp_tanh_setup(const double **table);
 __device__ __forceinline__ double dp_tanh64(double x, const double *__restrict__ tab)
 {
     const double ax = fabs(x);
-    // |x| >= 19.125: tanh = +-1 to double precision (1 - tanh(19.125) < 2^-55)
+    // |x| >= 19.125: +-1 is tanh correctly rounded (1 - tanh(19.125) < 2^-54)
     const long long bits = __double_as_longlong(ax);
     if (bits >= 0x4033200000000000ll) return bits > 0x7ff0000000000000ll ? x : copysign(1.0, x);  // NaN stays NaN
     // k = round(20 |x|) from the low bits of 20|x| + 1.5 * 2^52

@@ -3,7 +3,8 @@
 // tanh(|x|) on [0, 19.125) is split into intervals of width 1/20; on interval
 // k (centre c_k = k/20, k = round(20 |x|)) it is the degree-8 Taylor polynomial
 //   sum_n a_{k,n} t^n,  t = |x| - c_k,  |t| <= 1/40,
-// and tanh(|x|) = 1 beyond (1 - tanh(19.125) < 2^-55).  The coefficients come
+// and tanh(|x|) = 1 beyond (1 - tanh(19.125) < 2^-54, below half the spacing
+// of the doubles under 1, so 1 is tanh correctly rounded).  The coefficients come
 // from the derivatives of tanh, which are polynomials in T = tanh:
 //   d/dx P(T) = P'(T) (1 - T^2),   a_{k,n} = P_n(tanh(c_k)) / n!,
 // so each interval needs only tanh(c_k).  The Taylor remainder is bounded by

@@ -175,7 +175,8 @@ dp_status dp_format_nlist(dp_ctx *ctx, const double *coords, const int32_t *type
                           const double box[9], int64_t N, int32_t *nlist, int32_t *nreal);
 
 /* The FP64 tanh used by the FP64 kernels (piecewise degree-8 Taylor
- * polynomials of tanh on intervals of width 1/20, |error| < 1e-16 absolute),
+ * polynomials of tanh on intervals of width 1/20: truncation below 1e-16,
+ * |error| with FP64 rounding below 4e-16 absolute),
  * exposed so that its accuracy can be checked: y[i] = tanh(x[i]) for n device
  * doubles, on stream (NULL = legacy default); returns after the stream has
  * finished.  The paper's nets use tanh as their activation (Eqs.

@@ -22,3 +22,33 @@ def test_reference_arm_json_line():
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
     assert d["config"]["workload"] == "water192"
+
+
+def _bench_module():
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("bench_under_test", os.path.join(ROOT, "bench.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+def test_roofline_flop_counts_per_unit():
+    """The roofline's algorithmic FLOPs per unit, worked out by hand from the
+    nets of Sec. 4 (water: embedding 25-50-100, M2 = 16, fitting 240 x 3;
+    copper: embedding 32-64-128): multiply-add = 2, tanh not counted."""
+    from paper_2004_11658_gb300 import synth
+    b = _bench_module()
+    w = synth.WATER_MODEL
+    # one embedding pass per row: 2 (25 + 25*50 + 50*100)
+    assert b.emb_row_flops(w) == 12550
+    # fitting per atom: 2 (1600*240 + 240*240 + 240*240 + 240)
+    assert b.fit_atom_flops(w) == 998880
+    one_row = b.kernel_flops(w, rows=1, natoms=0)
+    one_atom = b.kernel_flops(w, rows=0, natoms=1)
+    assert one_row["embed_fwd"] == 12550 + 8 * 100          # + T = R~^T G
+    assert one_row["embed_bwd"] == 26700                    # G and dG/ds, two 4 x M contractions
+    assert one_atom["embed_fwd"] == 8 * 16 * 100            # D = T_<^T T
+    assert one_atom["embed_bwd"] == 25600                   # gT
+    assert one_atom["fit"] == 2 * 998880                    # forward and backward to D
+    cu = synth.CU_MODEL
+    assert b.kernel_flops(cu, rows=1, natoms=0)["embed_bwd"] == 43136

@@ -1,7 +1,7 @@
 """Spatial domain decomposition (Sec. 3.1, Remark 4) on the CPU: slabs with
 ghost shells, forward and reverse halos and the energy/virial all-reduce,
 with the oracle's sub-region evaluation, against the oracle on the whole
-periodic system; one slab per gloo rank for two ranks."""
+periodic system; one slab per gloo rank for two and three ranks."""
 import os
 
 import numpy as np
@@ -85,7 +85,10 @@ def _rank_main(rank, world, port, desc, P, coords, types, box, cap, out_dir):
         dist.destroy_process_group()
 
 
-def test_gloo_two_slabs(oracle, synth, tmp_path):
+@pytest.mark.parametrize("world", [2, 3])
+def test_gloo_slabs(oracle, synth, tmp_path, world):
+    """One slab per gloo rank; with three ranks on the 18.6 A box every rank
+    exchanges halos with both others."""
     import torch.multiprocessing as mp
     w = _case(synth, "water648")
     desc = w["model"]
@@ -93,11 +96,12 @@ def test_gloo_two_slabs(oracle, synth, tmp_path):
     N = len(w["coords"])
     ref = oracle.evaluate(desc, P, w["coords"], w["types"], w["box"])
     cap = oracle.default_cap(desc, w["box"], N, 0.0)
-    port = 29500 + (os.getpid() % 2000)
-    mp.start_processes(_rank_main, args=(2, port, desc, P, w["coords"], w["types"], w["box"], cap, str(tmp_path)),
-                       nprocs=2, start_method="spawn", join=True)
+    port = 29500 + (os.getpid() % 2000) + 10 * world
+    mp.start_processes(_rank_main, args=(world, port, desc, P, w["coords"], w["types"], w["box"], cap,
+                                         str(tmp_path)),
+                       nprocs=world, start_method="spawn", join=True)
     F = np.zeros((N, 3))
-    for r in range(2):
+    for r in range(world):
         d = np.load(tmp_path / f"rank{r}.npz")
         assert float(d["E"]) == pytest.approx(ref["energy"], rel=1e-12)
         assert np.abs(d["V"] - ref["virial"]).max() < 1e-11 * np.abs(ref["virial"]).max()

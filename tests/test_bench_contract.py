@@ -52,3 +52,18 @@ def test_roofline_flop_counts_per_unit():
     assert one_atom["fit"] == 2 * 998880                    # forward and backward to D
     cu = synth.CU_MODEL
     assert b.kernel_flops(cu, rows=1, natoms=0)["embed_bwd"] == 43136
+
+
+def test_reference_arm_under_torchrun_two_ranks():
+    """Launched as the multi-GPU bench is (torchrun, two ranks): rank 0 alone
+    prints the reference line, the other rank exits 0 without work."""
+    port = 29600 + (os.getpid() % 1000)
+    r = subprocess.run([sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
+                        "--master-addr", "127.0.0.1", "--master-port", str(port), os.path.join(ROOT, "bench.py"),
+                        "--impl", "reference", "--gpus", "2", "--workload", "water192", "--steps", "1",
+                        "--warmup", "1"], capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0

@@ -11,6 +11,7 @@
  *
  *   orc_switch      s(r) = w(r)/r                          Sec. 2 (env. matrix)
  *   orc_candidates  brute-force neighbour candidates with skin   Sec. 3.2.2, Sec. 4
+ *   orc_candidates_cells  the same candidates from a cell list  Sec. 3.2.2, Sec. 4
  *   orc_format      formatted neighbour list                Algorithm 1 + Sec. 3.2.2 text
  *   orc_eval        env. matrix (Alg. 2), embedding net (Eqs. embedding,
  *                   embedding-first, embedding-rest), descriptor (Eq. descrpt),
@@ -186,6 +187,118 @@ int64_t orc_candidates(int64_t N, const double *x, const double *box, double rli
         ncand[i] = n;
     }
     return over;
+}
+
+/* Cell-list neighbour candidates (Sec. 3.2.2 builds the list from cells;
+ * Sec. 4 adds the skin): the same set as orc_candidates, in the same
+ * increasing-j order, for the centres 0..ncentre-1.  The box is cut into
+ * n_a = floor(L_a / rlist) cells per axis (slightly fewer when L_a / rlist is
+ * an integer, so that every cell edge exceeds rlist by a margin larger than the
+ * rounding of the cell index); a neighbour within rlist then lies in one of
+ * the 27 cells around the centre's cell, each visited once since n_a >= 3.
+ * Distances use the same minimum-image arithmetic as the brute-force build, so
+ * the two sets agree bit for bit.  Returns -1 (nothing written) when an axis
+ * has fewer than 3 cells; otherwise the number of centres whose list was cut
+ * at cap. */
+static int orc_cmp_i32(const void *a, const void *b)
+{
+    int32_t x = *(const int32_t *)a, y = *(const int32_t *)b;
+    return (x > y) - (x < y);
+}
+
+int64_t orc_candidates_cells(int64_t N, int64_t ncentre, const double *x, const double *box, double rlist,
+                             int32_t cap, int32_t *ncand, int32_t *cand)
+{
+    int nc[3];
+    for (int a = 0; a < 3; ++a) {
+        nc[a] = (int)floor(box[a] / rlist * (1.0 - 1e-9));
+        if (nc[a] < 3) return -1;
+    }
+    const int64_t ncell = (int64_t)nc[0] * nc[1] * nc[2];
+    int64_t *cell_of = malloc(sizeof(int64_t) * (size_t)(N > 0 ? N : 1));
+    int64_t *start = calloc((size_t)ncell + 1, sizeof(int64_t));
+    int64_t *fill = malloc(sizeof(int64_t) * (size_t)ncell);
+    int32_t *members = malloc(sizeof(int32_t) * (size_t)(N > 0 ? N : 1));
+    /* cell of every atom, from its position wrapped into [0, L) */
+    for (int64_t i = 0; i < N; ++i) {
+        int64_t c = 0;
+        for (int a = 0; a < 3; ++a) {
+            double v = x[3 * i + a] - box[a] * floor(x[3 * i + a] / box[a]);
+            int k = (int)floor(v / box[a] * nc[a]);
+            if (k < 0) k = 0;
+            if (k >= nc[a]) k = nc[a] - 1;
+            c = c * nc[a] + k;
+        }
+        cell_of[i] = c;
+        start[c + 1]++;
+    }
+    for (int64_t c = 0; c < ncell; ++c) start[c + 1] += start[c];
+    for (int64_t c = 0; c < ncell; ++c) fill[c] = start[c];
+    for (int64_t i = 0; i < N; ++i) members[fill[cell_of[i]]++] = (int32_t)i;   /* increasing i per cell */
+    int64_t over = 0;
+#pragma omp parallel reduction(+ : over)
+    {
+        int64_t bufcap = 1024;
+        int32_t *buf = malloc(sizeof(int32_t) * (size_t)bufcap);
+#pragma omp for schedule(dynamic, 64)
+        for (int64_t i = 0; i < ncentre; ++i) {
+            int64_t c = cell_of[i];
+            int ci[3];
+            ci[2] = (int)(c % nc[2]);
+            ci[1] = (int)((c / nc[2]) % nc[1]);
+            ci[0] = (int)(c / ((int64_t)nc[1] * nc[2]));
+            int64_t n = 0;
+            for (int d0 = -1; d0 <= 1; ++d0)
+                for (int d1 = -1; d1 <= 1; ++d1)
+                    for (int d2 = -1; d2 <= 1; ++d2) {
+                        int k0 = (ci[0] + d0 + nc[0]) % nc[0];
+                        int k1 = (ci[1] + d1 + nc[1]) % nc[1];
+                        int k2 = (ci[2] + d2 + nc[2]) % nc[2];
+                        int64_t cc = ((int64_t)k0 * nc[1] + k1) * nc[2] + k2;
+                        for (int64_t q = start[cc]; q < start[cc + 1]; ++q) {
+                            int32_t j = members[q];
+                            if (j == i) continue;
+                            double d[3];
+                            orc_min_image(box, x + 3 * i, x + 3 * (int64_t)j, d);
+                            if (orc_norm(d) <= rlist) {
+                                if (n == bufcap) {
+                                    bufcap *= 2;
+                                    buf = realloc(buf, sizeof(int32_t) * (size_t)bufcap);
+                                }
+                                buf[n++] = j;
+                            }
+                        }
+                    }
+            qsort(buf, (size_t)n, sizeof(int32_t), orc_cmp_i32);
+            int64_t keep = n < cap ? n : cap;
+            for (int64_t k = 0; k < keep; ++k) cand[i * cap + k] = buf[k];
+            if (n > cap) over += 1;
+            ncand[i] = (int32_t)keep;
+        }
+        free(buf);
+    }
+    free(cell_of); free(start); free(fill); free(members);
+    return over;
+}
+
+/* Candidates of every atom: the cell list when each axis has at least 3
+ * cells, brute force otherwise (both give the same list). */
+static int64_t orc_candidates_any(int64_t N, const double *x, const double *box, double rlist, int32_t cap,
+                                  int32_t *ncand, int32_t *cand)
+{
+    int64_t r = orc_candidates_cells(N, N, x, box, rlist, cap, ncand, cand);
+    if (r >= 0) return r;
+    return orc_candidates(N, x, box, rlist, cap, ncand, cand);
+}
+
+/* Number of OpenMP threads the oracle uses from now on (n >= 1). */
+void orc_set_num_threads(int n)
+{
+#ifdef _OPENMP
+    if (n >= 1) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
 }
 
 /* ------------------------------------------------------------- Algorithm 1 */
@@ -606,7 +719,7 @@ static void orc_wrap(double *x, int64_t N, const double *box)
 #define ORC_KB 8.617333262e-5         /* eV/K */
 
 /* Velocity-Verlet NVE (Sec. 4): half kick, drift, wrap, candidate rebuild every
- * `rebuild_every` steps (brute force, rcut + skin), Algorithm 1 every step,
+ * `rebuild_every` steps (cell list, or brute force in small boxes; rcut + skin), Algorithm 1 every step,
  * force evaluation, half kick.  thermo[s] = (E_pot, E_kin, T, P) after step s
  * (eV, eV, K, eV/A^3), P = (2 E_kin + tr Xi) / (3V).  force (N x 3, in/out)
  * holds F(x) of the input coordinates when *have_force != 0, and is computed
@@ -629,7 +742,7 @@ int64_t orc_md(const int32_t *idesc, const double *ddesc, const double *params, 
     int64_t status = 0;
     double E = 0.0, V[9];
     const double vol = box[0] * box[1] * box[2];
-    if (orc_candidates(N, x, box, m.rcut + skin, cap, ncand, cand)) { status = -3; goto done; }
+    if (orc_candidates_any(N, x, box, m.rcut + skin, cap, ncand, cand)) { status = -3; goto done; }
     memcpy(xref, x, sizeof(double) * 3 * (size_t)N);
     if (!*have_force) {
         orc_format(N, x, types, box, ncand, cand, cap, T, m.sel, m.rcut, nlist, nreal, ovf);
@@ -655,7 +768,7 @@ int64_t orc_md(const int32_t *idesc, const double *ddesc, const double *params, 
             }
         }
         if (rebuild) {
-            if (orc_candidates(N, x, box, m.rcut + skin, cap, ncand, cand)) { status = -3; goto done; }
+            if (orc_candidates_any(N, x, box, m.rcut + skin, cap, ncand, cand)) { status = -3; goto done; }
             memcpy(xref, x, sizeof(double) * 3 * (size_t)N);
         }
         orc_format(N, x, types, box, ncand, cand, cap, T, m.sel, m.rcut, nlist, nreal, ovf);

@@ -48,6 +48,10 @@ def lib():
             L.orc_nparams.restype = ctypes.c_long
             L.orc_candidates.argtypes = [ctypes.c_int64, _d, _d, ctypes.c_double, ctypes.c_int32, _i32, _i32]
             L.orc_candidates.restype = ctypes.c_int64
+            L.orc_candidates_cells.argtypes = [ctypes.c_int64, ctypes.c_int64, _d, _d, ctypes.c_double,
+                                               ctypes.c_int32, _i32, _i32]
+            L.orc_candidates_cells.restype = ctypes.c_int64
+            L.orc_set_num_threads.argtypes = [ctypes.c_int]
             L.orc_format.argtypes = [ctypes.c_int64, _d, _i32, _d, _i32, _i32, ctypes.c_int32,
                                      ctypes.c_int32, _i32, ctypes.c_double, _i32, _i32, _i64]
             L.orc_eval.argtypes = [_i32, _d, _d, ctypes.c_int64, _d, _i32, _d, _i32, _d, _d, _d, _d, _d]
@@ -93,12 +97,30 @@ def switch(r, rs, rc):
     return s.value, ds.value
 
 
-def candidates(coords, box, rlist, cap):
+def set_num_threads(n):
+    """OpenMP threads of every later oracle call."""
+    lib().orc_set_num_threads(int(n))
+
+
+def candidates(coords, box, rlist, cap, method="auto", ncentre=None):
+    """Neighbour candidates within rlist, increasing j per centre.
+
+    method: "brute" (O(N^2)), "cells" (cell list; needs >= 3 cells per axis),
+    "auto" (cells where possible).  ncentre: only centres [0, ncentre) are
+    built (cell list only); the other rows are left empty."""
     x = np.ascontiguousarray(coords, dtype=np.float64)
     N = len(x)
+    nc = N if ncentre is None else int(ncentre)
     ncand = np.zeros(N, dtype=np.int32)
     cand = np.full((N, cap), -1, dtype=np.int32)
     b = np.ascontiguousarray(box, dtype=np.float64)
+    if method in ("auto", "cells"):
+        over = lib().orc_candidates_cells(N, nc, _p(x, _d), _p(b, _d), float(rlist), int(cap), _p(ncand, _i32),
+                                          _p(cand, _i32))
+        if over >= 0:
+            return ncand, cand, int(over)
+        if method == "cells" or nc != N:
+            raise ValueError("cell list needs at least 3 cells per axis (box edge >= 3 rlist)")
     over = lib().orc_candidates(N, _p(x, _d), _p(b, _d), float(rlist), int(cap), _p(ncand, _i32), _p(cand, _i32))
     return ncand, cand, int(over)
 

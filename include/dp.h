@@ -118,6 +118,27 @@ int64_t dp_model_nparams(const dp_model_desc *desc);
  * current CUDA device).  *out is owned by the caller; free with dp_model_free. */
 dp_status dp_model_create(const dp_model_desc *desc, const double *params, int64_t nparams,
                           dp_model **out);
+/* Seeded model (the paper's models are trained, Sec. 2 and Sec. 4, and no
+ * trained model is available, so weights are drawn from a seed).  Element k
+ * of the flat parameter vector (layout of dp_model_nparams) is
+ *     scale * n_k,
+ * with n_k the k-th standard normal of one stream: splitmix64 outputs
+ * z_i = mix(seed + i * 0x9E3779B97F4A7C15), i = 1, 2, ... (Steele, Lea and
+ * Flood, 2014), uniforms u1 = ((z_{2p+1} >> 11) + 1) * 2^-53 in (0, 1] and
+ * u2 = (z_{2p+2} >> 11) * 2^-53 in [0, 1), and Box-Muller:
+ * n_{2p} = sqrt(-2 ln u1) cos(2 pi u2), n_{2p+1} = sqrt(-2 ln u1) sin(2 pi u2).
+ * Scales: every weight matrix n / sqrt(fan_in + fan_out) (embedding layer 0:
+ * fan_in 1), the first fitting layer's weights then times fit_in_gain; every
+ * hidden bias n; output weights (out_scale * n) / sqrt(f_last + 1); b_out 0.
+ * dp_model_params_from_seed writes the nparams host doubles of params (nparams
+ * must equal dp_model_nparams(desc)); dp_model_from_seed creates the model
+ * directly (as dp_model_create).  The values are reproducible on every
+ * machine whose libm gives the same log, sin and cos. */
+dp_status dp_model_params_from_seed(const dp_model_desc *desc, uint64_t seed, double fit_in_gain,
+                                    double out_scale, double *params, int64_t nparams);
+dp_status dp_model_from_seed(const dp_model_desc *desc, uint64_t seed, double fit_in_gain,
+                             double out_scale, dp_model **out);
+
 /* Load / save the binary model file: "DPGB300M" magic, uint32 version 1,
  * the descriptor fields as little-endian int32/float64 in declaration order,
  * int64 nparams, nparams float64.  DP_ERR_FILE on a short or corrupt file. */

@@ -591,6 +591,69 @@ dp_status enqueue_eval(dp_ctx *c, const double *coords, const int32_t *types, co
     return DP_OK;
 }
 
+// ------------------------------------------------------------ seeded weights
+// The paper's models are trained (Sec. 2) and none is shipped, so models are
+// drawn from a seed.  Element k of the flat parameter vector takes the k-th
+// standard normal of one stream: splitmix64 (Steele, Lea and Flood, 2014; its
+// i-th output mixes seed + i * 0x9E3779B97F4A7C15, i = 1, 2, ...) gives 53-bit
+// uniforms, and the Box-Muller transform turns outputs (2p+1, 2p+2) into the
+// normals 2p (cosine branch) and 2p+1 (sine branch).
+uint64_t splitmix64_at(uint64_t seed, uint64_t i)
+{
+    uint64_t z = seed + i * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+double seeded_normal(uint64_t seed, int64_t k)
+{
+    const uint64_t p = (uint64_t)k >> 1;
+    const double u1 = (double)((splitmix64_at(seed, 2 * p + 1) >> 11) + 1) * 0x1p-53;   // (0, 1]
+    const double u2 = (double)(splitmix64_at(seed, 2 * p + 2) >> 11) * 0x1p-53;         // [0, 1)
+    const double r = std::sqrt(-2.0 * std::log(u1));
+    const double th = 6.283185307179586 * u2;
+    return (k & 1) ? r * std::sin(th) : r * std::cos(th);
+}
+
+// Walks the flat layout of dp_model_nparams and writes every element.
+void fill_seeded(const dp_model_desc &d, uint64_t seed, double fit_in_gain, double out_scale, double *P)
+{
+    int64_t k = 0;
+    auto weights = [&](int64_t n, int fan_in, int fan_out, double gain) {
+        const double den = std::sqrt((double)(fan_in + fan_out));
+        for (int64_t q = 0; q < n; ++q, ++k) {
+            double w = seeded_normal(seed, k) / den;
+            if (gain != 1.0) w = w * gain;
+            P[k] = w;
+        }
+    };
+    auto biases = [&](int64_t n) {
+        for (int64_t q = 0; q < n; ++q, ++k) P[k] = seeded_normal(seed, k);
+    };
+    const int T = d.ntypes, M = d.emb[d.n_emb - 1];
+    for (int a = 0; a < T; ++a)
+        for (int b = 0; b < T; ++b) {
+            int prev = 1;
+            for (int l = 0; l < d.n_emb; ++l) {
+                weights((int64_t)prev * d.emb[l], prev, d.emb[l], 1.0);
+                biases(d.emb[l]);
+                prev = d.emb[l];
+            }
+        }
+    for (int a = 0; a < T; ++a) {
+        int prev = d.m2 * M;
+        for (int l = 0; l < d.n_fit; ++l) {
+            weights((int64_t)prev * d.fit[l], prev, d.fit[l], l == 0 ? fit_in_gain : 1.0);
+            biases(d.fit[l]);
+            prev = d.fit[l];
+        }
+        const double den = std::sqrt((double)(prev + 1));
+        for (int q = 0; q < prev; ++q, ++k) P[k] = (out_scale * seeded_normal(seed, k)) / den;
+        P[k++] = 0.0;   // b_out
+    }
+}
+
 }  // namespace
 
 // Lets other translation units (the no-allocation entry point) report errors
@@ -755,6 +818,38 @@ dp_status dp_model_load(const char *path, dp_model **out)
     std::free(buf);
     if (s == DP_ERR_ARG) return fail(DP_ERR_FILE, std::string("corrupt parameters in ") + path);
     return s;
+}
+
+dp_status dp_model_params_from_seed(const dp_model_desc *desc, uint64_t seed, double fit_in_gain,
+                                    double out_scale, double *params, int64_t nparams)
+{
+    dp_status s = check_desc(desc);
+    if (s) return s;
+    if (!params) return fail(DP_ERR_ARG, "params is NULL");
+    const int64_t need = desc_nparams(*desc);
+    if (nparams != need) return fail(DP_ERR_ARG, "nparams does not match the descriptor (" + std::to_string(need) + ")");
+    if (!std::isfinite(fit_in_gain) || !std::isfinite(out_scale))
+        return fail(DP_ERR_ARG, "fit_in_gain and out_scale must be finite");
+    fill_seeded(*desc, seed, fit_in_gain, out_scale, params);
+    return DP_OK;
+}
+
+dp_status dp_model_from_seed(const dp_model_desc *desc, uint64_t seed, double fit_in_gain, double out_scale,
+                             dp_model **out)
+{
+    if (!out) return fail(DP_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    dp_status s = check_desc(desc);
+    if (s) return s;
+    const int64_t n = desc_nparams(*desc);
+    std::vector<double> P;
+    try {
+        P.resize((size_t)n);
+    } catch (...) {
+        return fail(DP_ERR_NOMEM, "host allocation failed");
+    }
+    if ((s = dp_model_params_from_seed(desc, seed, fit_in_gain, out_scale, P.data(), n))) return s;
+    return dp_model_create(desc, P.data(), n, out);
 }
 
 void dp_ctx_free(dp_ctx *c)

@@ -105,6 +105,12 @@ def lib():
             L.dp_model_set_params.argtypes = [_vp, _vp, _i64]
             L.dp_tanh_f64.restype = _i32
             L.dp_tanh_f64.argtypes = [_vp, _vp, _i64, _vp]
+            L.dp_model_params_from_seed.restype = _i32
+            L.dp_model_params_from_seed.argtypes = [ctypes.POINTER(dp_model_desc), ctypes.c_uint64, _dbl, _dbl,
+                                                    _vp, _i64]
+            L.dp_model_from_seed.restype = _i32
+            L.dp_model_from_seed.argtypes = [ctypes.POINTER(dp_model_desc), ctypes.c_uint64, _dbl, _dbl,
+                                             ctypes.POINTER(_vp)]
             L.dp_format_nlist_noalloc.restype = _i32
             L.dp_format_nlist_noalloc.argtypes = [ctypes.POINTER(dp_model_desc), _vp, _vp, _vp, _i64, _dbl,
                                                   _vp, _vp, _vp]
@@ -164,6 +170,24 @@ def _dev(t, dtype, shape=None, name="tensor"):
     return ctypes.c_void_p(t.data_ptr())
 
 
+def _seed_gains(desc, fit_in_gain, out_scale):
+    g = float(desc.get("fit_in_gain", 300.0) if fit_in_gain is None else fit_in_gain)
+    o = float(desc.get("out_scale", 0.02) if out_scale is None else out_scale)
+    return g, o
+
+
+def dp_model_params_from_seed(desc, seed, fit_in_gain=None, out_scale=None):
+    """Seeded flat parameter vector (host float64 numpy) of dp_model_params_from_seed."""
+    g, o = _seed_gains(desc, fit_in_gain, out_scale)
+    c = make_desc(desc)
+    n = dp_model_nparams(c)
+    if n < 0:
+        raise DPError(DP_ERR_ARG, "invalid descriptor")
+    P = np.empty(n, dtype=np.float64)
+    _check(lib().dp_model_params_from_seed(ctypes.byref(c), int(seed), g, o, P.ctypes.data_as(_vp), n))
+    return P
+
+
 class Model:
     """dp_model handle (parameters live on the current CUDA device)."""
 
@@ -177,6 +201,17 @@ class Model:
             _check(lib().dp_model_create(ctypes.byref(self.desc_c), p.ctypes.data_as(_vp), len(p),
                                          ctypes.byref(self._h)))
         self.desc = desc
+
+    @classmethod
+    def from_seed(cls, desc, seed, fit_in_gain=None, out_scale=None):
+        """dp_model_from_seed; the gains default to desc's own (as synth.model_params)."""
+        g, o = _seed_gains(desc, fit_in_gain, out_scale)
+        c = make_desc(desc)
+        h = _vp()
+        _check(lib().dp_model_from_seed(ctypes.byref(c), int(seed), g, o, ctypes.byref(h)))
+        m = cls(desc=desc, _handle=h)
+        m.desc_c = c
+        return m
 
     @classmethod
     def load(cls, path, desc=None):

@@ -14,8 +14,9 @@ equilibrated configuration or trained model is available, so:
   deg) with a uniformly random orientation (unit quaternion from 4 normals);
   atoms ordered O,H,H per molecule, types O=0, H=1;
 * copper: FCC cells with Gaussian jitter of 1% of the lattice constant;
-* weights: every linear layer W ~ N(0, 1/(fan_in+fan_out)), b ~ N(0, 1); the
-  first fitting layer is multiplied by 300, the output layer by 0.02 (zero bias);
+* weights: every linear layer W ~ N(0, 1/(fan_in+fan_out)), b ~ N(0, 1), drawn
+  from one seeded splitmix64 / Box-Muller stream; the first fitting layer is
+  multiplied by a gain, the output layer by a scale (zero bias), both per model;
 * velocities: Maxwell-Boltzmann at T0, centre-of-mass momentum removed, then
   rescaled to exactly T0 with 3N-3 degrees of freedom.
 
@@ -31,6 +32,8 @@ Model parameter layout (flat float64 vector, the one format both sides read):
 """
 from __future__ import annotations
 
+import math
+
 import numpy as np
 
 # Physical constants for the velocity draw (units: A, fs, eV, amu, K).
@@ -40,12 +43,16 @@ MASS = {"O": 15.999, "H": 1.008, "Cu": 63.546}
 
 # ---------------------------------------------------------------- models ----
 
+# fit_in_gain / out_scale: the seeded weights' first-fitting-layer gain and
+# output scale (model_params); they give RMS forces of ~7e-3 eV/A on both the
+# water and the copper boxes (the nearly symmetric FCC environments cancel
+# most of a copper atom's force, so copper's output scale is larger).
 WATER_MODEL = dict(ntypes=2, sel=(46, 92), rcut=6.0, rcut_smth=0.5,
                    emb=(25, 50, 100), m2=16, fit=(240, 240, 240),
-                   desc_scale_nm=1)
+                   desc_scale_nm=1, fit_in_gain=300.0, out_scale=0.04)
 CU_MODEL = dict(ntypes=1, sel=(512,), rcut=8.0, rcut_smth=2.0,
                 emb=(32, 64, 128), m2=16, fit=(240, 240, 240),
-                desc_scale_nm=1)
+                desc_scale_nm=1, fit_in_gain=300.0, out_scale=8.0)
 WATER_STUDENT = dict(WATER_MODEL, emb=(16, 32, 64))
 
 
@@ -78,37 +85,89 @@ def n_params(desc):
     return int(sum(int(np.prod(s)) for _, s in layer_shapes(desc)))
 
 
-def model_params(desc, seed=0, fit_in_gain=300.0, out_scale=0.02):
+_SM64_GAMMA = np.uint64(0x9E3779B97F4A7C15)
+_SM64_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_SM64_M2 = np.uint64(0x94D049BB133111EB)
+
+
+def splitmix64(seed, i):
+    """Outputs i (uint64 array, i >= 1) of splitmix64 seeded with `seed`
+    (Steele, Lea and Flood, 2014): mix(seed + i * gamma), arithmetic mod 2^64."""
+    z = np.uint64(seed) + np.asarray(i, dtype=np.uint64) * _SM64_GAMMA
+    z = (z ^ (z >> np.uint64(30))) * _SM64_M1
+    z = (z ^ (z >> np.uint64(27))) * _SM64_M2
+    return z ^ (z >> np.uint64(31))
+
+
+def seeded_normals(seed, n):
+    """The first n standard normals of the seeded stream: outputs (2p+1, 2p+2)
+    of splitmix64 give u1 = ((z >> 11) + 1) 2^-53 in (0, 1] and
+    u2 = (z >> 11) 2^-53 in [0, 1); Box-Muller gives normal 2p =
+    sqrt(-2 ln u1) cos(2 pi u2) and normal 2p+1 = sqrt(-2 ln u1) sin(2 pi u2).
+    The transcendental functions are the C library's (math module), element by
+    element, so that the values equal those of a C implementation using the
+    same libm bit for bit."""
+    npair = (int(n) + 1) // 2
+    with np.errstate(over="ignore"):
+        z = splitmix64(seed, np.arange(1, 2 * npair + 1, dtype=np.uint64))
+    u1 = ((z[0::2] >> np.uint64(11)) + np.uint64(1)).astype(np.float64) * 2.0 ** -53
+    u2 = (z[1::2] >> np.uint64(11)).astype(np.float64) * 2.0 ** -53
+    out = np.empty(2 * npair)
+    two_pi = 6.283185307179586
+    log, sqrt, cos, sin = math.log, math.sqrt, math.cos, math.sin
+    for p, (a, b) in enumerate(zip(u1.tolist(), u2.tolist())):
+        r = sqrt(-2.0 * log(a))
+        th = two_pi * b
+        out[2 * p] = r * cos(th)
+        out[2 * p + 1] = r * sin(th)
+    return out[:n]
+
+
+def model_params(desc, seed=0, fit_in_gain=None, out_scale=None):
     """Seeded weights in the flat layout.  No trained model exists; these
     stand in for one (same architecture as the paper's models, Sec. 4).
 
-    The first fitting layer is multiplied by ``fit_in_gain``: with the 1/N_m
-    descriptor scale the descriptor entries are ~1e-3, and the gain brings
-    that layer's pre-activations to O(1).  The output layer is scaled by
-    ``out_scale`` (0.02), which gives RMS forces of ~0.01 eV/A on the water
-    boxes.  The random landscape has no physical repulsion and slowly draws
-    atoms together; at this scale a 300 K NVE run of the 12,288-atom box
-    stays below ~330 K and within sel for 300 steps of 0.5 fs, while 5x
-    larger forces heat it past 700 K and overflow sel in ~230 steps."""
+    Element k of the flat vector is scale_k * n_k with n_k the k-th normal of
+    ``seeded_normals(seed, .)`` (the generator of the C ABI's
+    dp_model_params_from_seed, value for value): weight matrices
+    n / sqrt(fan_in + fan_out), the first fitting layer's then times
+    ``fit_in_gain``; hidden biases n; output weights
+    (out_scale * n) / sqrt(f_last + 1); output bias 0.
 
-    rng = np.random.default_rng(seed)
-    parts = []
-    for name, shape in layer_shapes(desc):
+    The gains default to the model's own (``desc["fit_in_gain"]``,
+    ``desc["out_scale"]``).  The first fitting layer's gain brings its
+    pre-activations to O(1) (with the 1/N_m scale the descriptor entries are
+    ~1e-3).  The output scale sets the force scale: RMS forces of ~0.01 eV/A
+    on the water and copper boxes.  The random landscape has no physical
+    repulsion and slowly draws atoms together, so much larger forces heat an
+    NVE run quickly."""
+    if fit_in_gain is None:
+        fit_in_gain = desc.get("fit_in_gain", 300.0)
+    if out_scale is None:
+        out_scale = desc.get("out_scale", 0.02)
+    shapes = layer_shapes(desc)
+    n = sum(int(np.prod(s)) for _, s in shapes)
+    z = seeded_normals(seed, n)
+    P = np.empty(n)
+    k = 0
+    for name, shape in shapes:
+        m = int(np.prod(shape))
         kind = name.split(".")[1]
-        if kind.startswith("W"):
-            fan_in = shape[0] if len(shape) == 2 else 1
-            fan_out = shape[-1]
-            w = rng.standard_normal(shape).ravel() / np.sqrt(fan_in + fan_out)
-            if name.startswith("fit") and kind == "W1":
-                w = w * fit_in_gain
-            parts.append(w)
-        elif kind == "wo":
-            parts.append(out_scale * rng.standard_normal(shape) / np.sqrt(shape[0] + 1))
+        seg = z[k:k + m]
+        if kind == "wo":
+            P[k:k + m] = (out_scale * seg) / math.sqrt(shape[0] + 1)
         elif kind == "bo":
-            parts.append(np.zeros(shape))
+            P[k:k + m] = 0.0
+        elif kind.startswith("W"):
+            fan_in = shape[0] if len(shape) == 2 else 1
+            w = seg / math.sqrt(fan_in + shape[-1])
+            if name.startswith("fit") and kind == "W1" and fit_in_gain != 1.0:
+                w = w * fit_in_gain
+            P[k:k + m] = w
         else:
-            parts.append(rng.standard_normal(shape))
-    return np.ascontiguousarray(np.concatenate(parts), dtype=np.float64)
+            P[k:k + m] = seg
+        k += m
+    return np.ascontiguousarray(P, dtype=np.float64)
 
 
 # --------------------------------------------------------------- systems ----

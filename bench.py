@@ -1,18 +1,26 @@
 #!/usr/bin/env python
 """Benchmark: Deep Potential MD throughput (atom-steps/s) on GB300.
 
-Workload (default): 4,096 H2O = 12,288 atoms in a 49.7 A periodic box, the
+Workload (default): 131,072 H2O = 393,216 atoms in a 157.6 A periodic box, the
 water model (se_a, rcut 6 A, rcut_smth 0.5 A, sel 46/92, embedding 25-50-100,
 M2 = 16, fitting 240-240-240, seeded FP64 weights), velocity Verlet at
 dt = 0.5 fs from 300 K, candidates with a 2 A skin rebuilt every 10 steps.
-One benchmark step = 10 MD steps = one rebuild period, so every step runs
-the whole path: candidate build, Algorithm 1, environment matrix, embedding,
-descriptor, fitting, backward, ProdForce/ProdVirial, energy sum, integrator.
+One benchmark step = one MD step of the whole box (every tenth step includes
+the candidate rebuild, so any 10 consecutive steps run every row of the path:
+candidate build, Algorithm 1, environment matrix, embedding, descriptor,
+fitting, backward, ProdForce/ProdVirial, energy sum, integrator).  The
+12,288-atom box (--workload water12288) and copper run 10 MD steps per
+benchmark step.
 
-Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle
-on the same system instead (one MD step per benchmark step).
-Multi-GPU (--gpus N under torchrun): N independent replicas, one per GPU
-(the path has no exchange step on one box); value sums all ranks.
+Modes beside the FP64 path: mixed precision (full model) and the student
+model as the fast path with the FP64 full model as its periodic judge and
+fallback; each reports its force error against the FP64 full model at the
+start and at the end of a 100-step trajectory (200 for copper).
+
+Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle on
+a bounded sample of the same workload instead.  Multi-GPU (--gpus N under
+torchrun): N independent replicas, one per GPU (the path has no exchange step
+on one box); value sums all ranks.
 """
 from __future__ import annotations
 
@@ -20,6 +28,7 @@ import argparse
 import hashlib
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -33,27 +42,37 @@ if ROOT not in sys.path:
 import numpy as np  # noqa: E402
 
 METRIC = "atom-steps/s"
-MD_PER_STEP = 10
-DT_FS = 0.5
-# MD conditions per workload: (dt in fs, T0 in K); the copper box runs at 1 fs and 330 K
-MD_CONDITIONS = {"cu32000": (1.0, 330.0)}
 SKIN = 2.0
-T0 = 300.0
+REBUILD_EVERY = 10
 L2_BYTES = 129 * 1024 * 1024
+DEFAULT_WORKLOAD = "water393216"
+
+# Per workload: MD steps per benchmark step, dt (fs), T0 (K), length of the
+# trajectory on which each mode's accuracy is reported (MD steps), and the
+# centres of the oracle's bounded sample per MD step (all cores, one core).
+WORKLOADS = {
+    "water393216": dict(md_per_step=1, dt=0.5, T0=300.0, traj=100, sample=8192, sample_1core=1024),
+    "water12288": dict(md_per_step=10, dt=0.5, T0=300.0, traj=100, sample=12288, sample_1core=1024),
+    "cu32000": dict(md_per_step=10, dt=1.0, T0=330.0, traj=200, sample=4096, sample_1core=512),
+    "water192": dict(md_per_step=1, dt=0.5, T0=300.0, traj=20, sample=192, sample_1core=192),
+}
 
 # FP64 pipe peak of a GB300: 152 SMs x 2 FP64 FMA/clk/SM x 2 FLOP x 2.07 GHz.
 # The per-SM rate is the one that reproduces the nominal 1.25 TFLOP/s.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+FORCE_RMSE_TARGET = 1e-3   # eV/A, against the FP64 full model
 
-# DRAM bytes per launch of the dominant kernel from one ncu capture;
-# reported only while the kernel source is the one captured.
+# Per-kernel counters from one ncu capture, reported only while the kernel
+# source is the one captured (hash of the .cu file and the shared header):
+#   bytes_per_launch  dram__bytes_read.sum + dram__bytes_write.sum
+#   fp64_flop_per_row 2 x dfma + dadd + dmul thread instructions
+#                     (smsp__sass_thread_inst_executed_op_d{fma,add,mul}_pred_on.sum)
+#                     per real neighbour row
 TRAFFIC = {
-    # ncu (--set full, or the two DRAM metrics alone) on one 12,288-atom water
-    # evaluation (bench.py --profile-eval 2): dram__bytes_read.sum +
-    # dram__bytes_write.sum of the dominant kernel
     "embed_bwd": {"bytes_per_launch": 206.746112e6 + 21.276672e6, "file": "embed_x.cu", "src_sha": "8c4c5603a99cc6ec"},
     "embed_bwd_mx<25>": {"bytes_per_launch": 204.936448e6 + 17.953792e6, "file": "mixed.cu", "src_sha": "97f3fe1bf34f81b7"},
 }
+FP64_ISSUED = {}
 
 
 def parse():
@@ -62,7 +81,7 @@ def parse():
     p.add_argument("--steps", type=int, default=10)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--workload", default="water12288")
+    p.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision measurement")
@@ -108,6 +127,20 @@ def kernel_flops(desc, rows, natoms):
         "embed_bwd": rows * (2 * g + 16 * M) + natoms * 16 * m2 * M,
         "fit": natoms * 2 * fit_atom_flops(desc),
     }
+
+
+def digit_mma_flops_bwd(desc, nreal):
+    """Tensor-core FLOPs the FP64 embedding backward kernel issues per launch
+    (k_embed_bwd_x, doubling nets with e1 <= 32): for every chunk of up to 32
+    rows of one atom's type block, the last layer's value and tangent
+    products, 28 digit pairs x ceil(2 e1 / 16) MMAs of M = 128, N = 32,
+    K = 16 each, and layer 1's, 28 x ceil(e1 / 16) MMAs of M = 64 each.
+    nreal: [N, ntypes] real rows per type block."""
+    e1 = desc["emb"][0]
+    k2p, k1p = -(-2 * e1 // 16), -(-e1 // 16)
+    chunks = int(np.ceil(np.asarray(nreal, dtype=np.int64) / 32.0).sum())
+    per_chunk = 2 * 28 * (k2p * 2 * 128 * 32 * 16 + k1p * 2 * 64 * 32 * 16)
+    return chunks * per_chunk
 
 
 class ClockSampler:
@@ -173,9 +206,85 @@ def source_sha(fn):
     return h.hexdigest()[:16]
 
 
-# ------------------------------------------------------------ reference --
+def _counter(table, key):
+    tr = table.get(key)
+    return tr if tr and tr.get("src_sha") == source_sha(tr["file"]) else None
+
+
+def workload_config(name, w, world):
+    """The config block both arms print (same keys, same values)."""
+    wl = WORKLOADS[name]
+    desc = w["model"]
+    return {"workload": name, "atoms": int(len(w["coords"])), "md_steps_per_step": wl["md_per_step"],
+            "dt_fs": wl["dt"], "skin": SKIN, "rebuild_every": REBUILD_EVERY, "T0_K": wl["T0"],
+            "model": "se_a %s %s / M2 %d / fit %s, seeded FP64 weights" % (
+                "copper" if desc["ntypes"] == 1 else "water", "-".join(map(str, desc["emb"])), desc["m2"],
+                "x".join(map(str, desc["fit"]))),
+            "l2": "inputs larger than L2, and L2 flushed between steps (256 MB write)",
+            "parallelism": f"replicas x{world}"}
+
+
+def cpu_model():
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu part")):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return platform.processor() or platform.machine()
+
+
+# ------------------------------------------------------------ the oracle --
+
+def oracle_sample_step(O, w, desc, P, S):
+    """One MD step's work of the oracle for the first S atoms of the workload
+    as centres (the 393,216-atom box lists its molecules in a random order of
+    lattice sites, so they are spread over the box): candidates of those
+    centres from the cell list (counted 1/10, rebuilt every 10 steps),
+    Algorithm 1 and the FP64 evaluation of their energies and pair gradients.
+    Returns the seconds per MD step of S atoms."""
+    x, t, box = w["coords"], w["types"], w["box"]
+    N = len(x)
+    S = min(S, N)
+    cap = O.default_cap(desc, box, N, SKIN)
+    t0 = time.perf_counter()
+    ncand, cand, _ = O.candidates(x, box, desc["rcut"] + SKIN, cap, ncentre=S if S < N else None)
+    t_cand = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    nl, _, _ = O.format_nlist(x, t, box, ncand, cand, desc["sel"], desc["rcut"], ncentre=S)
+    O.eval_nlist(desc, P, x, t, box, nl, nloc=S)
+    return time.perf_counter() - t0 + t_cand / REBUILD_EVERY
+
+
+def cpu_baseline(w, desc, P, name):
+    """The oracle as it stands on this host's cores (all, then one), each on a
+    bounded sample of the workload: S centres' MD-step work, best of 2."""
+    from oracle import oracle as O
+    wl = WORKLOADS[name]
+    out = {}
+    for key, S, threads in (("all", wl["sample"], None), ("one", wl["sample_1core"], 1)):
+        if threads is not None:
+            O.set_num_threads(threads)
+        cores = O.num_threads()
+        per = min(oracle_sample_step(O, w, desc, P, S) for _ in range(2))
+        S = min(S, len(w["coords"]))
+        out[key] = {"value": S / per, "unit": METRIC, "cores": cores, "kind": "oracle",
+                    "sample": f"{S} of the {len(w['coords'])} atoms as centres: candidates (cell list, /"
+                              f"{REBUILD_EVERY}), Algorithm 1 and the FP64 evaluation of one MD step, best of 2; "
+                              f"{per:.2f} s"}
+    O.set_num_threads(os.cpu_count() or 1)
+    res = dict(out["all"])
+    res["cpu"] = cpu_model()
+    res["nproc"] = os.cpu_count()
+    res["one_core"] = out["one"]
+    return res
+
 
 def run_reference(args, rank, world):
+    """The FP64 oracle on the host cores: every benchmark step is a bounded
+    sample of one MD step of the workload (the first S atoms as centres on the
+    starting configuration), scaled to atom-steps/s."""
     if rank != 0:
         return 0
     from oracle import oracle as O
@@ -183,57 +292,30 @@ def run_reference(args, rank, world):
     w = synth.workload(args.workload)
     desc = w["model"]
     P = synth.model_params(desc, 0)
-    m = np.array(w["masses"])[w["types"]]
-    x, v = w["coords"].copy(), synth.maxwell_velocities(m, T0, seed=2)
-    F = None
-    N = len(x)
+    wl = WORKLOADS[args.workload]
+    S = min(wl["sample"], len(w["coords"]))
     times = []
     for k in range(args.warmup + args.steps):
-        t0 = time.perf_counter()
-        x, v, F, th, _ = O.md(desc, P, x, v, w["types"], w["box"], w["masses"], DT_FS, 1,
-                              rebuild_every=MD_PER_STEP, skin=SKIN, force=F)
-        dt = time.perf_counter() - t0
+        dt = oracle_sample_step(O, w, desc, P, S) * wl["md_per_step"]
         if k >= args.warmup:
             times.append(dt)
     total = sum(times)
-    value = N * len(times) / total
+    # atom-steps of the sample per benchmark step
+    value = S * wl["md_per_step"] * len(times) / total
     cores = O.num_threads()
-    sample = (f"{args.steps} oracle velocity-Verlet steps of the {N}-atom system, each with a "
-              f"brute-force candidate rebuild, Algorithm 1 and the FP64 evaluation")
+    sample = (f"each step: {wl['md_per_step']} MD step(s) of {S} of the {len(w['coords'])} atoms as centres "
+              f"(candidates from the cell list counted 1/{REBUILD_EVERY}, Algorithm 1, FP64 evaluation)")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * total / len(times),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": args.workload, "atoms": N, "md_steps_per_step": 1,
-                                        "dt_fs": DT_FS, "skin": SKIN, "rebuild_every": MD_PER_STEP},
-        "cpu_baseline": {"value": value, "unit": METRIC, "cores": cores, "kind": "oracle", "sample": sample},
+        "data": "synthetic", "config": workload_config(args.workload, w, world),
+        "cpu_baseline": {"value": value, "unit": METRIC, "cores": cores, "kind": "oracle", "sample": sample,
+                         "cpu": cpu_model(), "nproc": os.cpu_count()},
         "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
     return 0
-
-
-def cpu_baseline(w, desc, P):
-    """The oracle as it stands on this host's cores: one candidate build
-    (amortised over the 10-step rebuild period) plus one Algorithm 1 +
-    evaluation, i.e. the cost of one MD step; two samples."""
-    from oracle import oracle as O
-    x, t, box = w["coords"], w["types"], w["box"]
-    N = len(x)
-    cap = O.default_cap(desc, box, N, SKIN)
-    t0 = time.perf_counter()
-    ncand, cand, _ = O.candidates(x, box, desc["rcut"] + SKIN, cap)
-    t_cand = time.perf_counter() - t0
-    ts = []
-    for _ in range(2):
-        t0 = time.perf_counter()
-        nl, _, _ = O.format_nlist(x, t, box, ncand, cand, desc["sel"], desc["rcut"])
-        O.eval_nlist(desc, P, x, t, box, nl)
-        ts.append(time.perf_counter() - t0)
-    per_step = min(ts) + t_cand / MD_PER_STEP
-    return {"value": N / per_step, "unit": METRIC, "cores": O.num_threads(), "kind": "oracle",
-            "sample": f"1 candidate build (/{MD_PER_STEP}) + 2 x (Algorithm 1 + FP64 evaluation) of the "
-                      f"{N}-atom system, best of 2; {per_step:.2f} s per MD step"}
 
 
 # ------------------------------------------------------------------ ours --
@@ -252,8 +334,9 @@ def mixed_kernel_flops(desc, rows, natoms):
 
 def _accuracy(dp, ctx, refc, x, t, box):
     """Forces, energy and virial of ctx against the reference context (FP64 full
-    model) on the configuration x: RMSE per component, per-atom |dF|
-    percentiles, energy error per atom, virial error relative to its max."""
+    model) on the configuration x: RMSE per component, absolute and relative to
+    the RMS reference force, per-atom |dF| percentiles, energy error per atom,
+    virial error relative to its max."""
     import torch
     N = x.shape[0]
     dp.dp_build_nlist(ctx, x, t, box, SKIN)
@@ -270,29 +353,65 @@ def _accuracy(dp, ctx, refc, x, t, box):
             "rel_force_rmse": rmse / frms if frms > 0 else None,
             "atom_force_err_p50_p90_p99_eV_per_A": [p50, p90, p99],
             "energy_err_eV_per_atom": abs(a["energy"].item() - b["energy"].item()) / N,
-            "virial_rel_err": float((a["virial"] - b["virial"]).abs().max() / b["virial"].abs().max())}
+            "virial_rel_err": float((a["virial"] - b["virial"]).abs().max() / b["virial"].abs().max()),
+            "meets_target": rmse <= FORCE_RMSE_TARGET}
 
 
-def measure_mode(args, dp, w, run_desc, run_P, ref_model, v0, dev, world, flush, dtype):
+def _mode_roofline(fl, groups, dom, tag, traffic):
+    sec = groups[dom]["ms"] / groups[dom]["launches"] / 1000.0
+    pk = measured_peaks()
+    bf16_peak = pk.get("bf16_tflops_sustained", pk.get("bf16_tflops", 1720.9))
+    ach_t = fl[dom]["tensor"] / sec / 1e12
+    ach_d = fl[dom]["fp64"] / sec / 1e12
+    ft, fd = ach_t / bf16_peak, ach_d / FP64_PEAK_TFLOPS
+    return {"bound": "alu" if fd >= ft else "tensor", "kernel": tag,
+            "achieved": ach_d if fd >= ft else ach_t,
+            "peak": FP64_PEAK_TFLOPS if fd >= ft else bf16_peak, "unit": "TFLOP/s",
+            "frac": max(fd, ft), "traffic": traffic,
+            "fp64": {"achieved": ach_d, "peak": FP64_PEAK_TFLOPS, "frac": fd,
+                     "what": "algorithmic FP64 FLOPs (T = R~^T G / N_m, D and their backward)"},
+            "tensor_bf16": {"achieved": ach_t, "peak": bf16_peak, "frac": ft,
+                            "what": "algorithmic BF16 GEMM FLOPs (unpadded)",
+                            "peak_source": "MEASURED_PEAKS bf16_tflops_sustained (of measured)"}}
+
+
+def measure_mode(args, dp, w, run_desc, run_P, ref_model, v0, dev, world, flush, dtype, fast_path=False):
     """MD with another model or precision on the same workload: throughput,
     per-kernel times, roofline of the dominant kernel, and accuracy against
-    the FP64 full model on the first and on the last configuration."""
+    the FP64 full model at the start and at the end of the mode's trajectory
+    (WORKLOADS[...]["traj"] MD steps, continued untimed after the timed steps).
+    fast_path: the run goes through student.FastPathMD (the FP64 full model
+    checks the force error every 10 MD steps inside the timed region and takes
+    over when it exceeds the target)."""
     import torch
+    from paper_2004_11658_gb300 import student
+    wl = WORKLOADS[args.workload]
     N = len(v0)
     model = dp.Model(run_desc, run_P)
-    ctx = dp.Context(model, N, precision=dp.DP_PREC_MIXED)
     refc = dp.Context(ref_model, N)
     x = torch.tensor(w["coords"], dtype=torch.float64, device=dev)
     v = torch.tensor(v0, dtype=torch.float64, device=dev)
     t = torch.tensor(w["types"], dtype=torch.int32, device=dev)
+    th = torch.empty((wl["md_per_step"], 4), dtype=torch.float64, device=dev)
+    if fast_path:
+        fp = student.FastPathMD(ref_model, model, N, tol=FORCE_RMSE_TARGET, check_every=REBUILD_EVERY)
+        ctx = fp.fast
+    else:
+        ctx = dp.Context(model, N, precision=dp.DP_PREC_MIXED)
     acc_first = _accuracy(dp, ctx, refc, x, t, w["box"])
-    th = torch.empty((MD_PER_STEP, 4), dtype=torch.float64, device=dev)
+    dp.dp_md_reset(ctx)
+    done = 0
 
     def step():
-        dp.dp_md_step(ctx, x, v, t, w["box"], w["masses"], DT_FS, MD_PER_STEP, rebuild_every=MD_PER_STEP,
-                      skin=SKIN, thermo=th, check=False)
+        nonlocal done
+        n = wl["md_per_step"]
+        if fast_path:
+            fp.run(x, v, t, w["box"], w["masses"], wl["dt"], n, rebuild_every=REBUILD_EVERY, skin=SKIN)
+        else:
+            dp.dp_md_step(ctx, x, v, t, w["box"], w["masses"], wl["dt"], n, rebuild_every=REBUILD_EVERY,
+                          skin=SKIN, thermo=th, check=False)
+        done += n
 
-    dp.dp_md_reset(ctx)
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -306,7 +425,8 @@ def measure_mode(args, dp, w, run_desc, run_P, ref_model, v0, dev, world, flush,
         step()
         e1.record()
         evs.append((e0, e1))
-        thermo_all.append(th.clone())
+        if not fast_path:
+            thermo_all.append(th.clone())
     torch.cuda.synchronize()
     kt = ctx.kernel_times()
     ctx.set_timing(0)
@@ -318,41 +438,87 @@ def measure_mode(args, dp, w, run_desc, run_P, ref_model, v0, dev, world, flush,
     total_ms = float(tmax.item())
     nl, nr, _ = dp.dp_format_nlist(ctx, x, t, w["box"], check=False)
     rows = int(nr.sum().item())
-    acc_last = _accuracy(dp, ctx, refc, x, t, w["box"])
+    # the rest of the trajectory, untimed
+    while done < wl["traj"]:
+        n = min(wl["md_per_step"], wl["traj"] - done)
+        if fast_path:
+            fp.run(x, v, t, w["box"], w["masses"], wl["dt"], n, rebuild_every=REBUILD_EVERY, skin=SKIN)
+        else:
+            th2 = torch.empty((n, 4), dtype=torch.float64, device=dev)
+            dp.dp_md_step(ctx, x, v, t, w["box"], w["masses"], wl["dt"], n, rebuild_every=REBUILD_EVERY,
+                          skin=SKIN, thermo=th2, check=False)
+            thermo_all.append(th2)
+        done += n
+    last_ctx = fp.context if fast_path else ctx
+    acc_last = _accuracy(dp, last_ctx, refc, x, t, w["box"])
     fl = mixed_kernel_flops(run_desc, rows, N)
     groups = {g: {"ms": ms, "launches": n} for g, (ms, n) in kt.items() if n > 0}
     dom = max(groups, key=lambda g: groups[g]["ms"])
     roof = None
     if dom in fl:
-        sec = groups[dom]["ms"] / groups[dom]["launches"] / 1000.0
-        pk = measured_peaks()
-        bf16_peak = pk.get("bf16_tflops", 1886.6)
-        ach_t = fl[dom]["tensor"] / sec / 1e12
-        ach_d = fl[dom]["fp64"] / sec / 1e12
-        ft, fd = ach_t / bf16_peak, ach_d / FP64_PEAK_TFLOPS
-        tr = TRAFFIC.get(f"{dom}_mx<{run_desc['emb'][0]}>")
-        traffic = tr["bytes_per_launch"] if tr and tr.get("src_sha") == source_sha(tr["file"]) else None
-        roof = {"bound": "alu" if fd >= ft else "tensor", "kernel": f"{dom}_mx<{run_desc['emb'][0]}>",
-                "achieved": ach_d if fd >= ft else ach_t,
-                "peak": FP64_PEAK_TFLOPS if fd >= ft else bf16_peak, "unit": "TFLOP/s",
-                "frac": max(fd, ft), "traffic": traffic,
-                "fp64": {"achieved": ach_d, "peak": FP64_PEAK_TFLOPS, "frac": fd},
-                "tensor_bf16": {"achieved": ach_t, "peak": bf16_peak, "frac": ft,
-                                "peak_source": "MEASURED_PEAKS bf16_tflops (burst, of measured)"}}
-    th_all = torch.stack(thermo_all).cpu().numpy().reshape(-1, 4)
-    etot = th_all[:, 0] + th_all[:, 1]
-    return {"value": world * N * MD_PER_STEP * args.steps / (total_ms / 1000.0), "unit": METRIC,
-            "ms_per_step": total_ms / args.steps, "dtype": dtype,
-            "model": "se_a %s / M2 %d / fit %s" % ("-".join(map(str, run_desc["emb"])), run_desc["m2"],
-                                                        "x".join(map(str, run_desc["fit"]))),
-            "kernels_ms_per_step": {g: d["ms"] / args.steps for g, d in groups.items()},
-            "roofline": roof,
-            "accuracy_vs_fp64_full_model": {"first_config": acc_first, "last_config": acc_last},
-            "nve": {"max_abs_drift_eV_per_atom": float(np.abs(etot - etot[0]).max() / N),
-                    "T_last_K": float(th_all[-1, 2])}}
+        tag = f"{dom}_mx<{run_desc['emb'][0]}>"
+        tr = _counter(TRAFFIC, tag)
+        roof = _mode_roofline(fl, groups, dom, tag, tr["bytes_per_launch"] if tr else None)
+    out = {"value": world * N * wl["md_per_step"] * args.steps / (total_ms / 1000.0), "unit": METRIC,
+           "ms_per_step": total_ms / args.steps, "dtype": dtype,
+           "model": "se_a %s / M2 %d / fit %s" % ("-".join(map(str, run_desc["emb"])), run_desc["m2"],
+                                                   "x".join(map(str, run_desc["fit"]))),
+           "kernels_ms_per_step": {g: d["ms"] / args.steps for g, d in groups.items()},
+           "roofline": roof,
+           "accuracy_vs_fp64_full_model": {"target_force_rmse_eV_per_A": FORCE_RMSE_TARGET,
+                                           "first_config": acc_first,
+                                           "last_config": dict(acc_last, md_step=done)}}
+    if fast_path:
+        out["fast_path"] = {"check_every_md_steps": fp.check_every, "tol_force_rmse_eV_per_A": fp.tol,
+                            "checks": fp.checks, "switched_to_full_model_at_md_step": fp.switched_at,
+                            "note": "timed steps include the FP64 full-model checks that fall inside them"}
+    else:
+        th_all = torch.cat(thermo_all).cpu().numpy().reshape(-1, 4)
+        etot = th_all[:, 0] + th_all[:, 1]
+        out["nve"] = {"max_abs_drift_eV_per_atom": float(np.abs(etot - etot[0]).max() / N),
+                      "T_last_K": float(th_all[-1, 2]), "md_steps": int(len(th_all))}
+    return out
 
 
 STUDENT_PARAMS = os.path.join(ROOT, "paper_2004_11658_gb300", "data", "student_water12288.npy")
+
+
+def fp64_roofline(desc, groups, dom, rows, nreal, N):
+    """Roofline of the FP64 path's dominant kernel, by unit: the FP64 pipe
+    (FP64 FLOPs issued, from the kernel's ncu instruction counts per row),
+    the tensor cores (digit-MMA FLOPs issued), and the algorithmic FP64
+    FLOPs as an FP64-equivalent rate."""
+    flops = kernel_flops(desc, rows, N)
+    per_launch_s = groups[dom]["ms"] / groups[dom]["launches"] / 1000.0
+    pk = measured_peaks()
+    bf16_peak = pk.get("bf16_tflops_sustained", pk.get("bf16_tflops", 1720.9))
+    tr = _counter(TRAFFIC, dom)
+    issued = _counter(FP64_ISSUED, dom)
+    equiv = flops[dom] / per_launch_s / 1e12 if dom in flops else None
+    roof = {"bound": "alu", "kernel": dom, "unit": "TFLOP/s", "traffic": tr["bytes_per_launch"] if tr else None,
+            "rows_per_launch": rows,
+            "fp64_equivalent": {"achieved": equiv, "peak": FP64_PEAK_TFLOPS,
+                                "frac": equiv / FP64_PEAK_TFLOPS if equiv else None,
+                                "what": "algorithmic FP64 FLOPs per launch / time; part of them run on the "
+                                        "tensor cores as exact digit products, so this may exceed 1"}}
+    if dom == "embed_bwd":
+        mma = digit_mma_flops_bwd(desc, nreal)
+        roof["tensor_bf16"] = {"achieved": mma / per_launch_s / 1e12, "peak": bf16_peak,
+                               "frac": mma / per_launch_s / 1e12 / bf16_peak,
+                               "what": "BF16 digit-MMA FLOPs issued (padded shapes)",
+                               "peak_source": "MEASURED_PEAKS bf16_tflops_sustained (of measured)"}
+    if issued:
+        fp = issued["fp64_flop_per_row"] * rows / per_launch_s / 1e12
+        roof["fp64_pipe"] = {"achieved": fp, "peak": FP64_PEAK_TFLOPS, "frac": fp / FP64_PEAK_TFLOPS,
+                             "what": "FP64 FLOPs issued on the FP64 units (2 dfma + dadd + dmul, ncu count "
+                                     "per row)"}
+        roof.update(achieved=fp, peak=FP64_PEAK_TFLOPS, frac=fp / FP64_PEAK_TFLOPS,
+                    peak_source="FP64 pipe: 152 SMs x 2 FMA/clk x 2 FLOP x 2.07 GHz (nominal 1.25 TFLOP/s)")
+    else:
+        roof.update(achieved=equiv, peak=FP64_PEAK_TFLOPS, frac=equiv / FP64_PEAK_TFLOPS if equiv else None,
+                    peak_source="FP64 pipe: 152 SMs x 2 FMA/clk x 2 FLOP x 2.07 GHz (nominal 1.25 TFLOP/s)",
+                    note="FP64-equivalent rate (no ncu count of the issued FP64 FLOPs for this source)")
+    return roof
 
 
 def run_ours(args, rank, world, local_rank):
@@ -362,32 +528,32 @@ def run_ours(args, rank, world, local_rank):
 
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
+    wl = WORKLOADS[args.workload]
     w = synth.workload(args.workload)
     desc = w["model"]
     P = synth.model_params(desc, 0)
     m = np.array(w["masses"])[w["types"]]
-    v0 = synth.maxwell_velocities(m, T0, seed=2)
+    v0 = synth.maxwell_velocities(m, wl["T0"], seed=2)
     N = len(m)
     model = dp.Model(desc, P)
     ctx = dp.Context(model, N)
     x = torch.tensor(w["coords"], dtype=torch.float64, device=dev)
     v = torch.tensor(v0, dtype=torch.float64, device=dev)
     t = torch.tensor(w["types"], dtype=torch.int32, device=dev)
-    th = torch.empty((MD_PER_STEP, 4), dtype=torch.float64, device=dev)
+    th = torch.empty((wl["md_per_step"], 4), dtype=torch.float64, device=dev)
     flush = torch.empty(2 * L2_BYTES, dtype=torch.uint8, device=dev)
 
     statuses = {}
 
     def step():
-        _, s = dp.dp_md_step(ctx, x, v, t, w["box"], w["masses"], DT_FS, MD_PER_STEP, rebuild_every=MD_PER_STEP,
-                             skin=SKIN, thermo=th, check=False)
+        _, s = dp.dp_md_step(ctx, x, v, t, w["box"], w["masses"], wl["dt"], wl["md_per_step"],
+                             rebuild_every=REBUILD_EVERY, skin=SKIN, thermo=th, check=False)
         if s not in (0, -3, -4):  # anything but "results written" conditions is fatal
             raise dp.DPError(s, dp.lib().dp_last_error().decode())
         statuses[dp.STATUS_NAMES[s]] = statuses.get(dp.STATUS_NAMES[s], 0) + 1
 
     for _ in range(args.warmup):
         step()
-    thermo0 = th.cpu().numpy().copy()
 
     def barrier():
         if world > 1:
@@ -428,27 +594,17 @@ def run_ours(args, rank, world, local_rank):
     if world > 1:
         dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
     total_ms = float(tmax.item())
-    value = world * N * MD_PER_STEP * args.steps / (total_ms / 1000.0)
+    value = world * N * wl["md_per_step"] * args.steps / (total_ms / 1000.0)
 
     # rows actually evaluated (real neighbours, Algorithm 1 on the final positions)
     nl, nr, _ = dp.dp_format_nlist(ctx, x, t, w["box"], check=False)
     rows = int(nr.sum().item())
-    flops = kernel_flops(desc, rows, N)
+    nreal = nr.cpu().numpy()
+    del nl
     groups = {g: {"ms": ms, "launches": n} for g, (ms, n) in kt.items()}
     timed_groups = {g: d for g, d in groups.items() if d["launches"] > 0}
     dom = max(timed_groups, key=lambda g: timed_groups[g]["ms"])
-    roof = None
-    if dom in flops:
-        per_launch_s = groups[dom]["ms"] / groups[dom]["launches"] / 1000.0
-        achieved = flops[dom] / per_launch_s / 1e12
-        tr = TRAFFIC.get(dom)
-        traffic = tr["bytes_per_launch"] if tr and tr.get("src_sha") == source_sha(tr["file"]) else None
-        roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
-                "peak_source": "FP64 pipe: 152 SMs x 2 FMA/clk x 2 FLOP x 2.07 GHz (nominal 1.25 TFLOP/s)",
-                "note": "algorithmic FP64 FLOPs; the embedding net's dense layers (layer 1 and the last) run "
-                        "on the tensor cores by exact splitting (FP64 accuracy), the rest on the FP64 pipe",
-                "flops_per_launch": flops[dom], "rows_per_launch": rows}
+    roof = fp64_roofline(desc, groups, dom, rows, nreal, N)
     th_all = torch.stack(thermo_all).cpu().numpy().reshape(-1, 4)
     etot = th_all[:, 0] + th_all[:, 1]
 
@@ -481,19 +637,22 @@ def run_ours(args, rank, world, local_rank):
         if world > 1:
             dist.all_reduce(te, op=dist.ReduceOp.MAX)
         e_ms = float(te.item())
-        e2e = {"value": world * N * MD_PER_STEP * args.steps / (e_ms / 1000.0), "unit": METRIC,
+        e2e = {"value": world * N * wl["md_per_step"] * args.steps / (e_ms / 1000.0), "unit": METRIC,
                "h2d_bytes_per_step": int(2 * N * 3 * 8 + N * 4),
                "d2h_bytes_per_step": int(2 * N * 3 * 8 + th_h_bytes)}
+    del ctx
+    torch.cuda.empty_cache()
 
     modes = {}
     if not args.no_mixed:
         modes["mixed"] = measure_mode(args, dp, w, desc, P, model, v0, dev, world, flush,
                                       "bf16 GEMMs (fp32 accumulate) + f64")
+        torch.cuda.empty_cache()
     if not args.no_student and args.workload.startswith("water"):
         if os.path.exists(STUDENT_PARAMS):
             Ps = np.load(STUDENT_PARAMS).astype(np.float64)
             modes["student"] = measure_mode(args, dp, w, synth.WATER_STUDENT, Ps, model, v0, dev, world, flush,
-                                            "bf16 GEMMs (fp32 accumulate) + f64")
+                                            "bf16 GEMMs (fp32 accumulate) + f64", fast_path=True)
             modes["student"]["params"] = os.path.relpath(STUDENT_PARAMS, ROOT)
         else:
             modes["student"] = {"unavailable": "no trained student parameters at "
@@ -501,26 +660,20 @@ def run_ours(args, rank, world, local_rank):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(w, desc, P)
+        cpu = cpu_baseline(w, desc, P, args.workload)
 
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": args.workload, "atoms": N, "md_steps_per_step": MD_PER_STEP, "dt_fs": DT_FS,
-                       "skin": SKIN, "rebuild_every": MD_PER_STEP, "T0_K": T0,
-                       "model": "se_a %s %s / M2 %d / fit %s, seeded FP64 weights" % (
-                           "copper" if desc["ntypes"] == 1 else "water", "-".join(map(str, desc["emb"])), desc["m2"],
-                           "x".join(map(str, desc["fit"]))),
-                       "l2": "flushed between steps (256 MB write)",
-                       "parallelism": f"replicas x{world}"},
+            "config": workload_config(args.workload, w, world),
             "gpu_launches": launches,
             "roofline": roof,
             "kernels_ms_per_step": {g: d["ms"] / args.steps for g, d in timed_groups.items()},
             "nve": {"etot_first": float(etot[0]), "etot_last": float(etot[-1]),
                     "max_abs_drift_eV_per_atom": float(np.abs(etot - etot[0]).max() / N),
-                    "T_last_K": float(th_all[-1, 2])},
+                    "T_last_K": float(th_all[-1, 2]), "md_steps": int(len(th_all))},
             "status_counts": statuses,
             "clocks": clocks,
             "e2e": e2e,
@@ -555,9 +708,7 @@ def profile_eval(args):
 
 
 def main():
-    global DT_FS, T0
     args = parse()
-    DT_FS, T0 = MD_CONDITIONS.get(args.workload, (DT_FS, T0))
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

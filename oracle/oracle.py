@@ -125,11 +125,13 @@ def candidates(coords, box, rlist, cap, method="auto", ncentre=None):
     return ncand, cand, int(over)
 
 
-def format_nlist(coords, types, box, ncand, cand, sel, rcut):
+def format_nlist(coords, types, box, ncand, cand, sel, rcut, ncentre=None):
+    """Algorithm 1 for the centres [0, ncentre) (all atoms by default); the
+    neighbours may be any of the atoms."""
     x = np.ascontiguousarray(coords, dtype=np.float64)
     t = np.ascontiguousarray(types, dtype=np.int32)
     b = np.ascontiguousarray(box, dtype=np.float64)
-    N = len(x)
+    N = len(x) if ncentre is None else int(ncentre)
     cap = cand.shape[1]
     sel_a = np.ascontiguousarray(sel, dtype=np.int32)
     nm = int(sel_a.sum())
@@ -142,7 +144,12 @@ def format_nlist(coords, types, box, ncand, cand, sel, rcut):
     return nlist, nreal, ovf
 
 
-def eval_nlist(desc, params, coords, types, box, nlist, want_descriptor=False):
+def eval_nlist(desc, params, coords, types, box, nlist, want_descriptor=False, nloc=None):
+    """Evaluation on a formatted list.  With nloc, only the centres [0, nloc)
+    are evaluated (nlist holds their rows): E and the virial of those
+    centres, and their force increments on all atoms."""
+    if nloc is not None:
+        return _eval_centres(desc, params, coords, types, box, nlist, int(nloc))
     i, d = _desc_arrays(desc)
     x = np.ascontiguousarray(coords, dtype=np.float64)
     t = np.ascontiguousarray(types, dtype=np.int32)
@@ -164,6 +171,25 @@ def eval_nlist(desc, params, coords, types, box, nlist, want_descriptor=False):
     if want_descriptor:
         out["descriptor"] = D
     return out
+
+
+def _eval_centres(desc, params, coords, types, box, nlist, nloc):
+    i, d = _desc_arrays(desc)
+    x = np.ascontiguousarray(coords, dtype=np.float64)
+    t = np.ascontiguousarray(types, dtype=np.int32)
+    b = np.ascontiguousarray(box, dtype=np.float64)
+    P = np.ascontiguousarray(params, dtype=np.float64)
+    nl = np.ascontiguousarray(nlist[:nloc], dtype=np.int32)
+    N = len(x)
+    E = np.zeros(1)
+    F = np.zeros((N, 3))
+    V = np.zeros(9)
+    Ei = np.zeros(max(nloc, 1))
+    rc = lib().orc_eval_local(_p(i, _i32), _p(d, _d), _p(P, _d), N, nloc, _p(x, _d), _p(t, _i32), _p(b, _d),
+                              _p(nl, _i32), _p(E, _d), _p(F, _d), _p(V, _d), _p(Ei, _d), None)
+    if rc != 0:
+        raise RuntimeError(f"orc_eval_local failed: {rc}")
+    return dict(energy=float(E[0]), force=F, virial=V.reshape(3, 3), atom_energy=Ei[:nloc])
 
 
 def evaluate_local(desc, params, coords, types, box, nloc, cap=None):

@@ -220,6 +220,8 @@ class FastPathMD:
         self.check_every = int(check_every)
         self.on_full = False
         self.switched_at = None
+        self.done = 0          # MD steps advanced so far (over all calls)
+        self.checks = []       # every check so far
 
     def _check(self, x, t, box):
         dp.dp_build_nlist(self.refc, x, t, box, 0.0)
@@ -227,28 +229,37 @@ class FastPathMD:
         dp.dp_build_nlist(self.fast, x, t, box, 0.0)
         f = dp.dp_eval(self.fast, x, t, box)["force"]
         d = (f - ref).double()
-        return float(d.pow(2).mean().sqrt()), float(d.norm(dim=1).max())
+        return float(d.pow(2).mean().sqrt()), float(d.norm(dim=1).max()), float(ref.pow(2).mean().sqrt())
+
+    @property
+    def context(self):
+        """The context the run is currently on."""
+        return self.full if self.on_full else self.fast
 
     def run(self, x, v, t, box, masses, dt, nsteps, rebuild_every=10, skin=2.0):
-        checks = []
-        done = 0
-        while done < nsteps:
-            n = min(self.check_every, nsteps - done)
-            ctx = self.full if self.on_full else self.fast
-            dp.dp_md_step(ctx, x, v, t, box, masses, dt, n, rebuild_every=rebuild_every, skin=skin)
-            done += n
-            if not self.on_full:
-                rmse, worst = self._check(x, t, box)
+        """Advance nsteps.  The step count and the check schedule (every
+        check_every steps counted from the first call) continue across
+        calls, so the run may be advanced one step at a time."""
+        new = []
+        left = int(nsteps)
+        while left > 0:
+            n = min(left, self.check_every - self.done % self.check_every)
+            dp.dp_md_step(self.context, x, v, t, box, masses, dt, n, rebuild_every=rebuild_every, skin=skin)
+            self.done += n
+            left -= n
+            if not self.on_full and self.done % self.check_every == 0:
+                rmse, worst, frms = self._check(x, t, box)
                 if rmse > self.tol:
                     self.on_full = True
-                    self.switched_at = done
+                    self.switched_at = self.done
                     dp.dp_md_reset(self.full)  # forces of the current configuration on the next step
                 else:
                     # the check rebuilt the student's lists; its next step recomputes its forces
                     dp.dp_md_reset(self.fast)
-                checks.append(dict(step=done, force_rmse=rmse, max_atom_err=worst,
-                                   model="full" if self.on_full else "student"))
-        return checks, self.switched_at
+                new.append(dict(step=self.done, force_rmse=rmse, max_atom_err=worst, force_rms_full=frms,
+                                model="full" if self.on_full else "student"))
+        self.checks.extend(new)
+        return new, self.switched_at
 
 
 def main(argv=None):

@@ -1,8 +1,11 @@
 """Mixed precision (BF16 tensor-core GEMMs, FP64 environment / contractions /
 forces) against the FP64 oracle.
 
-Bar: force RMSE <= 1e-3 eV/A against the FP64 result; also reported and
-bounded: energy error per atom, relative force RMSE and virial error.
+Bars: force RMSE <= 1e-3 eV/A against the FP64 result and, because the
+seeded models' forces are small (RMS ~7e-3 eV/A), a relative force RMSE
+(RMSE / RMS force) <= 1e-2 as well; a static case whose output layer is scaled
+to RMS forces of 0.3 eV/A meets both.  Also bounded: energy error per atom and
+the virial error.
 """
 import numpy as np
 import pytest
@@ -11,6 +14,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 FORCE_RMSE = 1e-3      # eV/A
+REL_FORCE_RMSE = 1e-2  # RMSE / RMS force
 E_PER_ATOM = 1e-3      # eV
 
 
@@ -66,10 +70,31 @@ def test_mixed_against_fp64_oracle(dp, oracle, synth, name, variant):
     rmse, rel, eE, eV = errors(g, o, N)
     print(f"{name} {variant}: force RMSE {rmse:.2e} eV/A (rel {rel:.2e}), |dE|/N {eE:.2e} eV, virial {eV:.2e}")
     assert rmse <= FORCE_RMSE
-    assert rel < 0.05
+    assert rel <= REL_FORCE_RMSE
     assert eE <= E_PER_ATOM
     assert eV < 0.05
     assert np.isfinite(g["force"].cpu().numpy()).all()
+
+
+@pytest.mark.parametrize("name", ["water648", "cu864"])
+def test_mixed_accuracy_at_large_forces(dp, oracle, synth, name):
+    """One evaluation with the output layer scaled so that the RMS force is
+    0.3 eV/A (E is linear in the output weights, so every force scales with
+    them): the absolute bar then sits well below the force itself."""
+    w = system(synth, name)
+    desc = w["model"]
+    N = len(w["coords"])
+    base = oracle.evaluate(desc, synth.model_params(desc, 0), w["coords"], w["types"], w["box"])
+    frms = float(np.sqrt((base["force"] ** 2).mean()))
+    scale = desc["out_scale"] * 0.3 / frms
+    P = synth.model_params(desc, 0, out_scale=scale)
+    o = oracle.evaluate(desc, P, w["coords"], w["types"], w["box"])
+    assert 0.25 < float(np.sqrt((o["force"] ** 2).mean())) < 0.35
+    model, ctx, x, t, g = mixed_eval(dp, desc, P, w)
+    rmse, rel, eE, eV = errors(g, o, N)
+    print(f"{name} at RMS force 0.3 eV/A: force RMSE {rmse:.2e} eV/A (rel {rel:.2e}), |dE|/N {eE:.2e} eV")
+    assert rmse <= FORCE_RMSE
+    assert rel <= REL_FORCE_RMSE
 
 
 def test_mixed_deterministic_and_same_list(dp, synth):

@@ -99,10 +99,10 @@ def test_eval_parity(dp, oracle, synth, name, fit):
 
 
 def test_eval_with_skin_list_matches(dp, oracle, synth):
-    """Candidates built with a 2 A skin: the formatted list also holds the
-    candidates between rcut and rcut + skin that fit sel (zero rows), so it is
-    compared with the oracle's list from the same candidates; the energy,
-    forces and virial equal those of the rcut-only list."""
+    """Candidates built with a 2 A skin: Algorithm 1 keeps the candidates
+    within rcut only (L(i) of Sec. 2), so the formatted list equals the
+    oracle's from the same skin candidates and also its rcut-only list; the
+    energy, forces and virial equal those of the rcut-only evaluation."""
     w, d, P, o = oracle_eval(oracle, synth, "water648")
     model, ctx, x, t = gpu_run(dp, d, P, w, skin=2.0)
     nl, nr, _ = dp.dp_format_nlist(ctx, x, t, w["box"])

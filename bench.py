@@ -86,6 +86,9 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision measurement")
     p.add_argument("--no-student", action="store_true", help="skip the student-model measurement")
+    p.add_argument("--decomp", choices=["replicas", "slab"], default="replicas",
+                   help="replicas: one independent system per GPU; slab: one system cut into one slab per "
+                        "GPU (forward/reverse halos over NCCL point-to-point, all-reduce of E and the virial)")
     p.add_argument("--profile-eval", type=int, default=0, metavar="N",
                    help="run N energy/force evaluations of the workload and exit (profiling driver)")
     p.add_argument("--profile-precision", choices=["fp64", "mixed"], default="fp64")
@@ -684,6 +687,72 @@ def run_ours(args, rank, world, local_rank):
     return 0
 
 
+def run_slab(args, rank, world, local_rank):
+    """One system cut into `world` slabs along x, one per rank/GPU (Sec. 3.1):
+    every MD step runs the forward halo, dp_eval_local, the reverse halo and
+    the all-reduce (NCCL), kicks and drifts through the library; re-plans
+    with atom migration every 10 steps.  value = atoms x steps / max time."""
+    import torch
+    import torch.distributed as dist
+    from paper_2004_11658_gb300 import domain, dp, synth
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    wl = WORKLOADS[args.workload]
+    w = synth.workload(args.workload)
+    desc = w["model"]
+    P = synth.model_params(desc, 0)
+    m = np.array(w["masses"])[w["types"]]
+    N = len(m)
+    v0 = synth.maxwell_velocities(m, wl["T0"], seed=2)
+    model = dp.Model(desc, P)
+    rho = N / float(np.prod(w["box"]))
+    cap_atoms = int(min(N, N / world * (1.0 + 2.0 * (desc["rcut"] + SKIN) * world / w["box"][0]) * 1.3 + 1024))
+    ev = domain.DPLocalEvaluator(model, cap_atoms, rho)
+    comm = domain.LocalComm(1) if world == 1 else domain.DistComm(rank, world)
+    md = domain.SlabMD(comm, w["box"], desc["rcut"], SKIN, torch.tensor(w["coords"], device=dev),
+                       torch.tensor(v0, device=dev), torch.tensor(w["types"], device=dev), w["masses"], wl["dt"],
+                       [ev], [domain.GPUIntegrator(ev.ctx)], replan_every=REBUILD_EVERY)
+
+    def step():
+        for _ in range(wl["md_per_step"]):
+            md.step()
+
+    for _ in range(args.warmup):
+        step()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev.ctx.set_timing(1)
+    l0 = ev.ctx.launches
+    t0 = time.perf_counter()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ms = e0.elapsed_time(e1)
+    tm = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(tm, op=dist.ReduceOp.MAX)
+    ms = float(tm.item())
+    kt = ev.ctx.kernel_times()
+    if rank == 0:
+        cfg = workload_config(args.workload, w, world)
+        cfg["parallelism"] = f"slab x{world}"
+        print(json.dumps({
+            "metric": METRIC, "value": N * wl["md_per_step"] * args.steps / (ms / 1000.0), "unit": METRIC,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": cfg, "gpu_launches": ev.ctx.launches - l0,
+            "kernels_ms_per_step_rank0": {g: v[0] / args.steps for g, v in kt.items() if v[1]},
+            "wall_s": time.perf_counter() - t0, "e2e": None, "cpu_baseline": None}), flush=True)
+    return 0
+
+
 def profile_eval(args):
     """Small profiling driver: N x (candidate build + dp_eval) of the workload."""
     import torch
@@ -722,6 +791,8 @@ def main():
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     try:
+        if args.decomp == "slab":
+            return run_slab(args, rank, world, local_rank)
         return run_ours(args, rank, world, local_rank)
     finally:
         if world > 1:

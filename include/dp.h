@@ -276,6 +276,22 @@ dp_status dp_md_step(dp_ctx *ctx, double *coords, double *vel, const int32_t *ty
                      const double box[9], const double *mass_per_type, int64_t N,
                      double dt_fs, int32_t nsteps, int32_t rebuild_every, double skin,
                      double *thermo);
+/* The two halves of one velocity-Verlet step (Sec. 4) as separate calls, for
+ * drivers that evaluate the forces themselves between them (the slab
+ * decomposition of Sec. 3.1, whose forces come from dp_eval_local and the
+ * halo exchanges):
+ *   dp_md_kick_drift: v += F/m dt/2; x += v dt; x wrapped into [0, L) of box
+ *                     (box NULL: no wrapping, for drivers that keep positions
+ *                     continuous between their own wraps);
+ *   dp_md_kick:       v += F/m dt/2.
+ * coords, vel: device [N][3], updated in place; force: device [N][3] (eV/A);
+ * types: device [N]; mass_per_type: host [ntypes] (amu, > 0).  The same
+ * arithmetic as dp_md_step.  N <= the context's natoms_max. */
+dp_status dp_md_kick_drift(dp_ctx *ctx, double *coords, double *vel, const double *force,
+                           const int32_t *types, const double box[9], const double *mass_per_type,
+                           int64_t N, double dt_fs);
+dp_status dp_md_kick(dp_ctx *ctx, double *vel, const double *force, const int32_t *types,
+                     const double *mass_per_type, int64_t N, double dt_fs);
 /* Parameter gradient for training (the paper trains the model by
  * back-propagation; forces are -grad E, Remark 2):
  *     grad = d/dW [ cE * E(W) + sum_i lambda_i . F_i(W) ],

@@ -591,6 +591,32 @@ dp_status enqueue_eval(dp_ctx *c, const double *coords, const int32_t *types, co
     return DP_OK;
 }
 
+// Device copies of conv/m and m per type (uploaded when the masses change).
+dp_status upload_masses(dp_ctx *c, const double *mass_per_type)
+{
+    const int T = c->m.ntypes;
+    bool same = true;
+    for (int a = 0; a < T; ++a) {
+        if (!(mass_per_type[a] > 0.0)) return fail(DP_ERR_ARG, "masses must be positive");
+        same = same && c->last_mass[a] == mass_per_type[a];
+    }
+    if (same) return DP_OK;
+    // the pinned staging buffer may still feed an earlier asynchronous copy
+    DP_CUDA(cudaStreamSynchronize(c->stream), "masses");
+    for (int a = 0; a < T; ++a) {
+        c->h_mass_stage[a] = kAccConv / mass_per_type[a];
+        c->h_mass_stage[DP_MAX_TYPES + a] = mass_per_type[a];
+        c->last_mass[a] = mass_per_type[a];
+    }
+    DP_CUDA(cudaMemcpyAsync(c->d_inv_mass_conv, c->h_mass_stage, sizeof(double) * T, cudaMemcpyHostToDevice,
+                            c->stream),
+            "masses");
+    DP_CUDA(cudaMemcpyAsync(c->d_mass, c->h_mass_stage + DP_MAX_TYPES, sizeof(double) * T, cudaMemcpyHostToDevice,
+                            c->stream),
+            "masses");
+    return DP_OK;
+}
+
 // ------------------------------------------------------------ seeded weights
 // The paper's models are trained (Sec. 2) and none is shipped, so models are
 // drawn from a seed.  Element k of the flat parameter vector takes the k-th
@@ -1119,27 +1145,7 @@ dp_status dp_md_step(dp_ctx *c, double *coords, double *vel, const int32_t *type
     if (nsteps < 0 || rebuild_every < 0 || !(dt_fs > 0.0)) return fail(DP_ERR_ARG, "bad nsteps/rebuild_every/dt");
     Box3 b;
     if ((s = read_box(box, b))) return s;
-    const int T = c->m.ntypes;
-    bool same = true;
-    for (int a = 0; a < T; ++a) {
-        if (!(mass_per_type[a] > 0.0)) return fail(DP_ERR_ARG, "masses must be positive");
-        same = same && c->last_mass[a] == mass_per_type[a];
-    }
-    if (!same) {
-        // the pinned staging buffer may still feed an earlier asynchronous copy
-        DP_CUDA(cudaStreamSynchronize(c->stream), "dp_md_step");
-        for (int a = 0; a < T; ++a) {
-            c->h_mass_stage[a] = kAccConv / mass_per_type[a];
-            c->h_mass_stage[DP_MAX_TYPES + a] = mass_per_type[a];
-            c->last_mass[a] = mass_per_type[a];
-        }
-        DP_CUDA(cudaMemcpyAsync(c->d_inv_mass_conv, c->h_mass_stage, sizeof(double) * T, cudaMemcpyHostToDevice,
-                                c->stream),
-                "dp_md_step");
-        DP_CUDA(cudaMemcpyAsync(c->d_mass, c->h_mass_stage + DP_MAX_TYPES, sizeof(double) * T,
-                                cudaMemcpyHostToDevice, c->stream),
-                "dp_md_step");
-    }
+    if ((s = upload_masses(c, mass_per_type))) return s;
     const double vol = b.L[0] * b.L[1] * b.L[2];
     if (!c->md_force_valid || c->md_N != N) {
         if ((s = do_build(c, coords, types, b, N, skin))) return s;
@@ -1175,6 +1181,48 @@ dp_status dp_md_step(dp_ctx *c, double *coords, double *vel, const int32_t *type
                                      thermo + (size_t)(st - 1) * 4, &c->launches);
         }
         if (e != cudaSuccess) return cuda_fail(e, "kick_thermo");
+    }
+    return finish(c);
+}
+
+dp_status dp_md_kick_drift(dp_ctx *c, double *coords, double *vel, const double *force, const int32_t *types,
+                           const double box[9], const double *mass_per_type, int64_t N, double dt_fs)
+{
+    dp_status s = check_common(c, coords, types, N);
+    if (s) return s;
+    if (!vel || !force || !mass_per_type) return fail(DP_ERR_ARG, "vel/force/mass_per_type is NULL");
+    if (!(dt_fs > 0.0)) return fail(DP_ERR_ARG, "dt must be positive");
+    Box3 b;
+    if (box) {
+        if ((s = read_box(box, b))) return s;
+    } else {
+        b.L[0] = b.L[1] = b.L[2] = 0.0;   // no wrapping
+    }
+    if ((s = upload_masses(c, mass_per_type))) return s;
+    if (N > 0) {
+        GroupTimer tm(c, G_MD);
+        cudaError_t e = dp_launch_kick_drift(c->stream, (int)N, coords, vel, force, types, c->d_inv_mass_conv, dt_fs,
+                                             b, &c->launches);
+        if (e != cudaSuccess) return cuda_fail(e, "kick_drift");
+    }
+    return finish(c);
+}
+
+dp_status dp_md_kick(dp_ctx *c, double *vel, const double *force, const int32_t *types,
+                     const double *mass_per_type, int64_t N, double dt_fs)
+{
+    if (!c) return fail(DP_ERR_ARG, "context is NULL");
+    if (N < 0 || N > c->natoms_max) return fail(DP_ERR_ARG, "N out of range");
+    if (N > 0 && (!vel || !force || !types)) return fail(DP_ERR_ARG, "vel/force/types is NULL");
+    if (!mass_per_type) return fail(DP_ERR_ARG, "mass_per_type is NULL");
+    if (!(dt_fs > 0.0)) return fail(DP_ERR_ARG, "dt must be positive");
+    dp_status s;
+    if ((s = upload_masses(c, mass_per_type))) return s;
+    if (N > 0) {
+        GroupTimer tm(c, G_MD);
+        cudaError_t e = dp_launch_kick_thermo(c->stream, (int)N, vel, force, types, c->d_inv_mass_conv, c->d_mass,
+                                              dt_fs, c->ke_part, &c->launches);
+        if (e != cudaSuccess) return cuda_fail(e, "kick");
     }
     return finish(c);
 }

@@ -128,7 +128,7 @@ __global__ void __launch_bounds__(1024) k_reduce(int N, const double *__restrict
     }
 }
 
-// v += dt/2 * F/m ; x += dt * v ; wrap x into [0, L)
+// v += dt/2 * F/m ; x += dt * v ; wrap x into [0, L) (no wrapping where L = 0)
 __global__ void k_kick_drift(int N, double *__restrict__ x, double *__restrict__ v,
                              const double *__restrict__ f, const int32_t *__restrict__ types,
                              const double *__restrict__ inv_mass_conv, double dt, Box3 box)
@@ -142,8 +142,11 @@ __global__ void k_kick_drift(int N, double *__restrict__ x, double *__restrict__
         v[3 * i + a] = vv;
         double xx = x[3 * i + a] + dt * vv;
         const double L = box.L[a];
-        double n = floor(__ddiv_rn(xx, L));
-        x[3 * i + a] = __dsub_rn(xx, __dmul_rn(L, n));
+        if (L > 0.0) {
+            double n = floor(__ddiv_rn(xx, L));
+            xx = __dsub_rn(xx, __dmul_rn(L, n));
+        }
+        x[3 * i + a] = xx;
     }
 }
 

@@ -297,3 +297,307 @@ class DPLocalEvaluator:
         self.dp.dp_build_nlist(self.ctx, xs, ts, sub_box, 0.0)
         out = self.dp.dp_eval_local(self.ctx, xs, ts, sub_box, nloc)
         return out["energy"].item(), out["force"], out["virial"]
+
+
+# ----------------------------------------------------------- MD over slabs --
+#
+# Velocity-Verlet MD with the slab decomposition (Sec. 3.1; Sec. 4 for the
+# integrator).  Every slab owns a set of atoms (global id, position, velocity,
+# force, type) and computes, from its own atoms alone, which of them the other
+# slabs hold as ghosts, so no process needs the global positions:
+#
+#   step:  kick + drift of the owned atoms (v += F/m dt/2, x += v dt, wrap)
+#          [re-plan when due: migrate atoms whose x left the slab to their new
+#           owner, then rebuild the send lists and exchange the ghost counts
+#           and types]
+#          forward halo -> sub-region evaluation -> reverse halo -> all-reduce
+#          of E and the virial; kick (v += F/m dt/2)
+#
+# The ghost shell has width w = rcut + skin and is re-planned every
+# `replan_every` steps, and earlier as soon as an atom has moved more than
+# skin/2 since the last plan (the rule of a buffered neighbour list): until
+# then every neighbour within rcut of an owned atom is among the ghosts.
+# Positions are wrapped into the cell at each re-plan and move continuously
+# (unwrapped) in between, so that a ghost -- the owner's position plus the
+# periodic image fixed at the plan -- follows its atom across the cell's
+# faces; a sub-region is evaluated in its own frame (x shifted, the x edge
+# padded by rcut + skin of vacuum).
+
+def _send_lists(box, nslab, w, p, gid, x):
+    """Send lists of slab p to every slab q from p's owned atoms (ascending
+    global ids): for q, the positions in p's list and the periodic image
+    (-1, 0, +1 along x) of the atoms inside [q W - w, (q+1) W + w), images
+    in the order -1, 0, +1 and ids ascending within one image; slab p itself
+    receives the images of its own atoms only (not the atoms themselves)."""
+    L = box[0]
+    W = L / nslab
+    xw = x[:, 0] - L * np.floor(x[:, 0] / L)
+    out = []
+    for q in range(nslab):
+        lo, hi = q * W - w, (q + 1) * W + w
+        pos, shift = [], []
+        for s in (-1, 0, 1):
+            if s == 0 and q == p:
+                continue
+            xs = xw + s * L
+            idx = np.nonzero((xs >= lo) & (xs < hi))[0]
+            pos.append(idx)
+            shift.append(np.full(len(idx), s, dtype=np.int64))
+        out.append((np.concatenate(pos), np.concatenate(shift)))
+    return out
+
+
+class LocalComm:
+    """All slabs in one process: messages are passed by reference."""
+
+    def __init__(self, nslab):
+        self.nslab = nslab
+        self.slabs = list(range(nslab))
+
+    def alltoall(self, rows):
+        """rows[k][q]: message of local slab k to slab q -> [k][p]: from p."""
+        return [[rows[p][q] for p in range(self.nslab)] for q in range(self.nslab)]
+
+    def allreduce_sum(self, parts):
+        return sum(parts)
+
+    def allreduce_max(self, parts):
+        return max(parts)
+
+
+class DistComm:
+    """One slab per rank of a torch.distributed group (rank = slab); point-to
+    point messages with the sizes exchanged first."""
+
+    def __init__(self, rank, nslab, group=None):
+        import torch.distributed as dist
+        self.dist = dist
+        self.rank = rank
+        self.nslab = nslab
+        self.group = group
+        self.slabs = [rank]
+
+    def _p2p(self, send, recv):
+        dist = self.dist
+        ops = []
+        for q, t in send.items():
+            if t.numel():
+                ops.append(dist.P2POp(dist.isend, t.contiguous(), q, self.group))
+        for p, t in recv.items():
+            if t.numel():
+                ops.append(dist.P2POp(dist.irecv, t, p, self.group))
+        if ops:
+            for r in dist.batch_isend_irecv(ops):
+                r.wait()
+
+    def alltoall(self, rows):
+        (row,) = rows
+        me, P = self.rank, self.nslab
+        peers = [q for q in range(P) if q != me]
+        dev = row[me].device
+        # sizes first: every message is [n, k] float64 with k known to both sides
+        sizes = {q: torch.tensor([row[q].shape[0]], dtype=torch.int64, device=dev) for q in peers}
+        got = {p: torch.zeros(1, dtype=torch.int64, device=dev) for p in peers}
+        self._p2p(sizes, got)
+        k = row[me].shape[1]
+        recv = {p: torch.empty((int(got[p].item()), k), dtype=row[me].dtype, device=dev) for p in peers}
+        self._p2p({q: row[q] for q in peers}, recv)
+        return [[row[me] if p == me else recv[p] for p in range(P)]]
+
+    def allreduce_sum(self, parts):
+        (t,) = parts
+        t = t.clone()
+        self.dist.all_reduce(t, group=self.group)
+        return t
+
+    def allreduce_max(self, parts):
+        (t,) = parts
+        t = t.clone()
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX, group=self.group)
+        return t
+
+
+class GPUIntegrator:
+    """Kicks and drifts through the library (dp_md_kick_drift, dp_md_kick)
+    on the context of a slab's evaluator."""
+
+    def __init__(self, ctx):
+        from . import dp
+        self.dp = dp
+        self.ctx = ctx
+
+    def kick_drift(self, x, v, f, t, masses, dt):
+        if x.shape[0]:
+            self.dp.dp_md_kick_drift(self.ctx, x, v, f, t, None, masses, dt)
+
+    def kick(self, v, f, t, masses, dt):
+        if v.shape[0]:
+            self.dp.dp_md_kick(self.ctx, v, f, t, masses, dt)
+
+
+class SlabMD:
+    """Velocity-Verlet MD over P slabs along x (Sec. 3.1, Remark 4, Sec. 4).
+
+    coords, vel: [N, 3] float64 tensors, types: [N] int32 (the starting state;
+    each slab keeps the atoms it owns); evaluators[k] / integrators[k]: the
+    sub-region evaluator and the integrator of local slab k (comm.slabs[k]).
+    run(n) advances n steps and returns thermo rows (E_pot, E_kin) per step;
+    gather() returns the global (x, v, f) in id order (for checks)."""
+
+    ACC_CONV = 9.648533212e-3   # (eV/A/amu) -> A/fs^2
+
+    def __init__(self, comm, box, rcut, skin, coords, vel, types, masses, dt, evaluators, integrators,
+                 replan_every=10):
+        self.comm = comm
+        self.P = comm.nslab
+        self.box = _box3(box)
+        self.rcut, self.skin = float(rcut), float(skin)
+        self.w = self.rcut + self.skin
+        self.pad = self.rcut + self.skin
+        if self.w > self.box[0] * self.P:
+            raise ValueError("ghost width larger than the cell")
+        self.masses = np.asarray(masses, dtype=np.float64)
+        self.dt = float(dt)
+        self.ev = evaluators
+        self.integ = integrators
+        self.replan_every = int(replan_every)
+        self.nstep = 0
+        dev = coords.device
+        L, W = self.box[0], self.box[0] / self.P
+        Ld = torch.as_tensor(self.box, dtype=torch.float64, device=dev)
+        xw = coords - Ld * torch.floor(coords / Ld)
+        owner = torch.clamp((xw[:, 0] / W).long(), max=self.P - 1)
+        gid = torch.arange(coords.shape[0], device=dev)
+        self.s = []
+        for p in comm.slabs:
+            m = owner == p
+            self.s.append(dict(gid=gid[m].clone(), x=xw[m].clone(), v=vel[m].clone(),
+                               f=torch.zeros_like(coords[m]), t=types[m].clone().contiguous()))
+        self._plan()
+        self._forces()
+
+    # -- planning ------------------------------------------------------------
+    def _migrate(self):
+        """Atoms whose x left their slab go to the new owner (id, x, v, f, type)."""
+        L, W, P = self.box[0], self.box[0] / self.P, self.P
+        rows = []
+        Lv = torch.as_tensor(self.box, dtype=torch.float64)
+        for k, p in enumerate(self.comm.slabs):
+            s = self.s[k]
+            Ld = Lv.to(s["x"].device)
+            xw = s["x"] - Ld * torch.floor(s["x"] / Ld)       # wrapped into the cell
+            owner = torch.clamp((xw[:, 0] / W).long(), max=P - 1)
+            pack = torch.cat([s["gid"].double()[:, None], xw, s["v"], s["f"], s["t"].double()[:, None]], 1)
+            rows.append([pack[owner == q] for q in range(P)])
+        inbox = self.comm.alltoall(rows)
+        for k in range(len(self.comm.slabs)):
+            allp = torch.cat(inbox[k], 0)
+            order = torch.argsort(allp[:, 0])
+            allp = allp[order]
+            self.s[k] = dict(gid=allp[:, 0].long(), x=allp[:, 1:4].contiguous(), v=allp[:, 4:7].contiguous(),
+                             f=allp[:, 7:10].contiguous(), t=allp[:, 10].to(torch.int32).contiguous())
+
+    def _plan(self):
+        P = self.P
+        rows = []
+        for k, p in enumerate(self.comm.slabs):
+            s = self.s[k]
+            s["send"] = _send_lists(self.box, P, self.w, p, s["gid"].cpu().numpy(), s["x"].cpu().numpy())
+            s["xref"] = s["x"].clone()
+            # ghost types travel once per plan, by the route of the positions
+            rows.append([self._pack(s, q, s["t"].double()[:, None]) for q in range(P)])
+        inbox = self.comm.alltoall(rows)
+        for k in range(len(self.comm.slabs)):
+            s = self.s[k]
+            s["nrecv"] = [m.shape[0] for m in inbox[k]]
+            s["tg"] = torch.cat(inbox[k], 0)[:, 0].to(torch.int32)
+        self.since_plan = 0
+
+    def _pack(self, s, q, a):
+        pos, _ = s["send"][q]
+        return a.index_select(0, torch.as_tensor(pos, device=a.device))
+
+    # -- one evaluation ------------------------------------------------------
+    def _forces(self):
+        P, L = self.P, self.box[0]
+        W = L / P
+        rows = []
+        for k, p in enumerate(self.comm.slabs):
+            s = self.s[k]
+            row = []
+            for q in range(P):
+                pos, shift = s["send"][q]
+                xq = s["x"].index_select(0, torch.as_tensor(pos, device=s["x"].device)).clone()
+                xq[:, 0] += torch.as_tensor(shift, dtype=xq.dtype, device=xq.device) * L
+                row.append(xq)
+            rows.append(row)
+        inbox = self.comm.alltoall(rows)
+        sub_box = np.array([W + 2.0 * self.w + self.pad, self.box[1], self.box[2]])
+        E, V, back_rows = [], [], []
+        for k, p in enumerate(self.comm.slabs):
+            s = self.s[k]
+            nloc = s["x"].shape[0]
+            ghosts = torch.cat(inbox[k], 0)
+            xs = torch.cat([s["x"], ghosts], 0)
+            xs[:, 0] -= p * W - self.w
+            ts = torch.cat([s["t"], s["tg"]], 0).contiguous()
+            if xs.shape[0]:
+                e, f, v = self.ev[k](xs.contiguous(), ts, sub_box, nloc)
+                v = torch.as_tensor(v, dtype=torch.float64, device=xs.device).reshape(9)
+            else:
+                e, f, v = 0.0, xs.new_zeros((0, 3)), xs.new_zeros(9)
+            E.append(torch.as_tensor([float(e)], dtype=torch.float64, device=xs.device))
+            V.append(v)
+            s["f"] = f[:nloc].clone()
+            # reverse halo: increments on the ghosts go back to their owners
+            starts = np.concatenate([[0], np.cumsum(s["nrecv"])])
+            back_rows.append([f[nloc + starts[q]: nloc + starts[q + 1]] for q in range(P)])
+        got = self.comm.alltoall(back_rows)
+        for k in range(len(self.comm.slabs)):
+            s = self.s[k]
+            for q in range(P):
+                pos, _ = s["send"][q]
+                if len(pos):
+                    s["f"].index_add_(0, torch.as_tensor(pos, device=s["f"].device), got[k][q])
+        red = self.comm.allreduce_sum([torch.cat([e, v]) for e, v in zip(E, V)])
+        self.energy = float(red[0])
+        self.virial = red[1:].reshape(3, 3)
+
+    # -- MD --------------------------------------------------------------------
+    def _max_disp(self):
+        L = torch.as_tensor(self.box, dtype=torch.float64)
+        parts = []
+        for s in self.s:
+            if s["x"].shape[0]:
+                d = s["x"] - s["xref"]
+                Ld = L.to(d.device)
+                d = d - Ld * torch.round(d / Ld)
+                parts.append(d.pow(2).sum(1).max().sqrt().reshape(1))
+            else:
+                parts.append(torch.zeros(1, dtype=torch.float64, device=s["x"].device))
+        return float(self.comm.allreduce_max(parts)[0])
+
+    def step(self):
+        for k, s in enumerate(self.s):
+            self.integ[k].kick_drift(s["x"], s["v"], s["f"], s["t"], self.masses, self.dt)
+        self.nstep += 1
+        self.since_plan += 1
+        if (self.replan_every > 0 and self.since_plan >= self.replan_every) or \
+                self._max_disp() > 0.5 * self.skin:
+            self._migrate()
+            self._plan()
+        self._forces()
+        ke = []
+        for k, s in enumerate(self.s):
+            self.integ[k].kick(s["v"], s["f"], s["t"], self.masses, self.dt)
+            m = torch.as_tensor(self.masses, device=s["v"].device)[s["t"].long()]
+            ke.append((0.5 * m[:, None] * s["v"] * s["v"]).sum().reshape(1) / self.ACC_CONV)
+        self.kinetic = float(self.comm.allreduce_sum(ke)[0])
+        return self.energy, self.kinetic
+
+    def run(self, n):
+        return [self.step() for _ in range(n)]
+
+    def owned(self):
+        """(global ids, x, v, f) of the local slabs."""
+        return [(s["gid"], s["x"], s["v"], s["f"]) for s in self.s]

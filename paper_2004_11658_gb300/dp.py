@@ -89,6 +89,10 @@ def lib():
             L.dp_eval_local.argtypes = [_vp, _vp, _vp, _vp, _i64, _i64, _vp, _vp, _vp, _vp]
             L.dp_md_step.restype = _i32
             L.dp_md_step.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, _i64, _dbl, _i32, _i32, _dbl, _vp]
+            L.dp_md_kick_drift.restype = _i32
+            L.dp_md_kick_drift.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _i64, _dbl]
+            L.dp_md_kick.restype = _i32
+            L.dp_md_kick.argtypes = [_vp, _vp, _vp, _vp, _vp, _i64, _dbl]
             L.dp_md_get_force.restype = _i32
             L.dp_md_get_force.argtypes = [_vp, _vp, _i64]
             L.dp_md_reset.restype = _i32
@@ -424,6 +428,28 @@ def dp_md_step(ctx, coords, vel, types, box, masses, dt, nsteps, rebuild_every=1
     if check:
         _check(s)
     return thermo, s
+
+
+def dp_md_kick_drift(ctx, coords, vel, force, types, box, masses, dt):
+    """First half of a velocity-Verlet step: v += F/m dt/2, x += v dt, and
+    x wrapped into the cell (box None: no wrapping)."""
+    N = coords.shape[0]
+    b = _box9(box) if box is not None else None
+    m = np.ascontiguousarray(masses, dtype=np.float64)
+    _check(lib().dp_md_kick_drift(ctx.handle, _dev(coords, torch.float64, (N, 3), "coords"),
+                                  _dev(vel, torch.float64, (N, 3), "vel"), _dev(force, torch.float64, (N, 3), "force"),
+                                  _dev(types, torch.int32, (N,), "types"),
+                                  b.ctypes.data_as(_vp) if b is not None else None,
+                                  m.ctypes.data_as(_vp), N, float(dt)))
+
+
+def dp_md_kick(ctx, vel, force, types, masses, dt):
+    """Second half of a velocity-Verlet step: v += F/m dt/2."""
+    N = vel.shape[0]
+    m = np.ascontiguousarray(masses, dtype=np.float64)
+    _check(lib().dp_md_kick(ctx.handle, _dev(vel, torch.float64, (N, 3), "vel"),
+                            _dev(force, torch.float64, (N, 3), "force"), _dev(types, torch.int32, (N,), "types"),
+                            m.ctypes.data_as(_vp), N, float(dt)))
 
 
 def dp_md_get_force(ctx, N, device="cuda"):

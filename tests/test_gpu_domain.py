@@ -110,3 +110,51 @@ def test_emulated_slabs_match_whole(dp, synth, precision, nslab):
     assert E == pytest.approx(ref["energy"].item(), rel=tol)
     assert (F - ref["force"]).abs().max().item() <= tol * fs
     assert (V.reshape(9) - ref["virial"]).abs().max().item() <= tol * ref["virial"].abs().max().item()
+
+
+@pytest.mark.parametrize("nslab", [2, 3])
+def test_slab_md_matches_single_domain_md(dp, synth, nslab):
+    """Velocity-Verlet MD over slabs emulated on one GPU (kicks and drifts by
+    dp_md_kick_drift / dp_md_kick, forces by dp_eval_local and the halos,
+    re-plans with atom migration every 4 steps) follows the whole-system
+    dp_md_step trajectory."""
+    from paper_2004_11658_gb300 import domain
+    w = _water648(synth)
+    desc = w["model"]
+    P = synth.model_params(desc, 0)
+    N = len(w["coords"])
+    m = np.array(w["masses"])[w["types"]]
+    v0 = synth.maxwell_velocities(m, 300.0, seed=4)
+    v0[:, 0] += 0.08          # uniform drift along x: atoms cross slab faces
+    model = dp.Model(desc, P)
+    n, dt = 16, 1.0
+    # whole system
+    ctx = dp.Context(model, N)
+    x = torch.tensor(w["coords"], device="cuda")
+    v = torch.tensor(v0, device="cuda")
+    t = torch.tensor(w["types"], device="cuda")
+    th = torch.empty((n, 4), dtype=torch.float64, device="cuda")
+    dp.dp_md_step(ctx, x, v, t, w["box"], w["masses"], dt, n, rebuild_every=1, skin=0.0, thermo=th)
+    # slabs
+    rho = N / float(np.prod(w["box"]))
+    evs = [domain.DPLocalEvaluator(model, N, rho) for _ in range(nslab)]
+    integ = [domain.GPUIntegrator(e.ctx) for e in evs]
+    md = domain.SlabMD(domain.LocalComm(nslab), w["box"], desc["rcut"], 1.0, torch.tensor(w["coords"], device="cuda"),
+                       torch.tensor(v0, device="cuda"), torch.tensor(w["types"], device="cuda"), w["masses"], dt,
+                       evs, integ, replan_every=4)
+    owner0 = {int(g): k for k, s in enumerate(md.s) for g in s["gid"]}
+    rows = np.array(md.run(n))
+    xs = np.zeros((N, 3))
+    vs = np.zeros((N, 3))
+    for gid, xx, vv, ff in md.owned():
+        xs[gid.cpu().numpy()] = xx.cpu().numpy()
+        vs[gid.cpu().numpy()] = vv.cpu().numpy()
+    d = xs - x.cpu().numpy()
+    d -= w["box"] * np.round(d / w["box"])
+    assert np.abs(d).max() < 1e-9
+    assert np.abs(vs - v.cpu().numpy()).max() < 1e-10
+    th = th.cpu().numpy()
+    np.testing.assert_allclose(rows[:, 0], th[:, 0], rtol=1e-11)
+    np.testing.assert_allclose(rows[:, 1], th[:, 1], rtol=1e-11)
+    owner1 = {int(g): k for k, s in enumerate(md.s) for g in s["gid"]}
+    assert sum(owner0[g] != owner1[g] for g in owner0) > 20

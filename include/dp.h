@@ -216,6 +216,8 @@ dp_status dp_tanh_f64(const double *x, double *y, int64_t n, void *stream);
  * for the same candidate radius.  coords, types: device; box: host double[9];
  * stream: cudaStream_t (NULL = legacy default stream); the call returns after
  * the stream has finished the work.
+ * Every cell edge must be at least 2 (rcut + skin), as for dp_build_nlist
+ * (DP_ERR_BOX otherwise).
  * Scratch: one file-scope device array of fixed size (about 21 MB) that every
  * GPU loading the library holds until the process exits; it bounds
  * N <= DP_NOALLOC_MAX_ATOMS and the candidates of an atom to
@@ -223,7 +225,10 @@ dp_status dp_tanh_f64(const double *x, double *y, int64_t n, void *stream);
  * candidates give DP_ERR_CAPACITY after it.  The call makes no cudaMalloc,
  * cudaFree or other allocating call.  Its first call on a device looks up
  * the array's device address (cudaGetSymbolAddress) with that device
- * current, so make that first call before any stream capture.  All calls
+ * current, so make that first call before any stream capture.  With lazy
+ * module loading (the CUDA default) that first call is also when the driver
+ * loads the array's module and commits its ~21 MB on the device: a caller
+ * with a fixed device budget should make one call at start-up.  All calls
  * share the array, which keeps the last call's contents: calls that overlap
  * on the GPU (other streams, other host threads) race and must not be made. */
 #define DP_NOALLOC_MAX_ATOMS 2048

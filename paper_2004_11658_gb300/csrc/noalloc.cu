@@ -41,8 +41,6 @@ static __device__ __align__(256) unsigned char dp_noalloc_scratch[kScratchBytes]
 std::mutex g_mu;
 unsigned char *g_addr[kMaxDevices] = {nullptr};
 
-thread_local std::string g_err;
-
 }  // namespace
 
 // Defined in dp_api.cu: keeps dp_last_error() in sync for this entry point.

@@ -72,7 +72,13 @@ TRAFFIC = {
     "embed_bwd": {"bytes_per_launch": 206.746112e6 + 21.276672e6, "file": "embed_x.cu", "src_sha": "8c4c5603a99cc6ec"},
     "embed_bwd_mx<25>": {"bytes_per_launch": 204.936448e6 + 17.953792e6, "file": "mixed.cu", "src_sha": "97f3fe1bf34f81b7"},
 }
-FP64_ISSUED = {}
+FP64_ISSUED = {
+    # ncu on one evaluation of the 12,288-atom water box (bench.py --workload
+    # water12288 --profile-eval 1), 1,046,154 real rows: dfma 2.984e9, dadd
+    # 1.796e9, dmul 1.630e9 thread instructions; FP64 pipe busy 64.5%
+    "embed_bwd": {"fp64_flop_per_row": 8979.6, "pipe_busy": 0.645, "file": "embed_x.cu",
+                  "src_sha": "8c4c5603a99cc6ec"},
+}
 
 
 def parse():
@@ -513,8 +519,10 @@ def fp64_roofline(desc, groups, dom, rows, nreal, N):
     if issued:
         fp = issued["fp64_flop_per_row"] * rows / per_launch_s / 1e12
         roof["fp64_pipe"] = {"achieved": fp, "peak": FP64_PEAK_TFLOPS, "frac": fp / FP64_PEAK_TFLOPS,
+                             "busy_ncu": issued["pipe_busy"],
                              "what": "FP64 FLOPs issued on the FP64 units (2 dfma + dadd + dmul, ncu count "
-                                     "per row)"}
+                                     "per row of the 12,288-atom box); busy_ncu: the FP64 pipe's share of "
+                                     "issue cycles (conversions, compares and idle lanes included)"}
         roof.update(achieved=fp, peak=FP64_PEAK_TFLOPS, frac=fp / FP64_PEAK_TFLOPS,
                     peak_source="FP64 pipe: 152 SMs x 2 FMA/clk x 2 FLOP x 2.07 GHz (nominal 1.25 TFLOP/s)")
     else:

@@ -314,7 +314,9 @@ dp_status dp_param_grad(dp_ctx *ctx, const double *coords, const int32_t *types,
                         int64_t N, double cE, const double *lambda, double *grad);
 /* Replace the parameters of a model (host array, nparams doubles).  Contexts
  * made from the model see the new values on their next call; mixed-precision
- * contexts keep the BF16 copies made at their creation and must be recreated. */
+ * contexts keep the BF16 copies made at their creation and must be recreated.
+ * Values equal bit for bit to the current ones change nothing (no upload, the
+ * FP64 contexts keep their weight digits). */
 dp_status dp_model_set_params(dp_model *model, const double *params, int64_t nparams);
 
 /* Copy the context's MD force ([N][3]) to a device buffer. */

@@ -1231,6 +1231,10 @@ dp_status dp_model_set_params(dp_model *md, const double *params, int64_t nparam
 {
     if (!md || !params) return fail(DP_ERR_ARG, "model/params is NULL");
     if (nparams != md->nparams) return fail(DP_ERR_ARG, "nparams does not match the model");
+    // the same values again (a training loop evaluating several frames with
+    // one set of parameters): nothing to upload, the contexts' derived copies
+    // (weight digits, BF16 weights) stay valid
+    if (std::memcmp(md->h_params, params, sizeof(double) * nparams) == 0) return DP_OK;
     for (int64_t q = 0; q < nparams; ++q)
         if (!std::isfinite(params[q])) return fail(DP_ERR_ARG, "non-finite parameter");
     std::memcpy(md->h_params, params, sizeof(double) * nparams);

@@ -44,12 +44,16 @@ MASS = {"O": 15.999, "H": 1.008, "Cu": 63.546}
 # ---------------------------------------------------------------- models ----
 
 # fit_in_gain / out_scale: the seeded weights' first-fitting-layer gain and
-# output scale (model_params); they give RMS forces of ~7e-3 eV/A on both the
-# water and the copper boxes (the nearly symmetric FCC environments cancel
-# most of a copper atom's force, so copper's output scale is larger).
+# output scale (model_params).  Water: RMS force ~4e-3 eV/A at the start; the
+# random landscape has no repulsion, and at this scale a 300 K NVE run of the
+# water boxes reaches ~320 K and RMS forces of ~1.4e-2 eV/A (largest ~0.4 eV/A)
+# after 100 steps of 0.5 fs, while twice the scale gives ~350 K and ~4e-2
+# (largest ~1.4 eV/A, close contacts).  Copper: RMS force ~7e-3 eV/A (the
+# nearly symmetric FCC environments cancel most of an atom's force, so its
+# output scale is larger).
 WATER_MODEL = dict(ntypes=2, sel=(46, 92), rcut=6.0, rcut_smth=0.5,
                    emb=(25, 50, 100), m2=16, fit=(240, 240, 240),
-                   desc_scale_nm=1, fit_in_gain=300.0, out_scale=0.04)
+                   desc_scale_nm=1, fit_in_gain=300.0, out_scale=0.02)
 CU_MODEL = dict(ntypes=1, sel=(512,), rcut=8.0, rcut_smth=2.0,
                 emb=(32, 64, 128), m2=16, fit=(240, 240, 240),
                 desc_scale_nm=1, fit_in_gain=300.0, out_scale=8.0)
@@ -137,10 +141,10 @@ def model_params(desc, seed=0, fit_in_gain=None, out_scale=None):
     The gains default to the model's own (``desc["fit_in_gain"]``,
     ``desc["out_scale"]``).  The first fitting layer's gain brings its
     pre-activations to O(1) (with the 1/N_m scale the descriptor entries are
-    ~1e-3).  The output scale sets the force scale: RMS forces of ~0.01 eV/A
-    on the water and copper boxes.  The random landscape has no physical
-    repulsion and slowly draws atoms together, so much larger forces heat an
-    NVE run quickly."""
+    ~1e-3).  The output scale sets the force scale (RMS forces of ~4e-3 eV/A
+    on the water boxes, ~7e-3 on copper).  The random landscape has no
+    physical repulsion and slowly draws atoms together, so much larger forces
+    heat an NVE run quickly."""
     if fit_in_gain is None:
         fit_in_gain = desc.get("fit_in_gain", 300.0)
     if out_scale is None:

@@ -12,9 +12,9 @@ fitting, backward, ProdForce/ProdVirial, energy sum, integrator).  The
 12,288-atom box (--workload water12288) and copper run 10 MD steps per
 benchmark step.
 
-Modes beside the FP64 path: mixed precision (full model) and the student
-model as the fast path with the FP64 full model as its periodic judge and
-fallback; each reports its force error against the FP64 full model at the
+Modes beside the FP64 path: mixed precision (full model; plain BF16 and
+split-operand embedding GEMMs) and the student model as the fast path with
+the FP64 full model as its periodic judge and fallback; each reports its force error against the FP64 full model at the
 start and at the end of a 100-step trajectory (200 for copper).
 
 Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle on
@@ -384,7 +384,8 @@ def _mode_roofline(fl, groups, dom, tag, traffic):
                             "peak_source": "MEASURED_PEAKS bf16_tflops_sustained (of measured)"}}
 
 
-def measure_mode(args, dp, w, run_desc, run_P, ref_model, v0, dev, world, flush, dtype, fast_path=False):
+def measure_mode(args, dp, w, run_desc, run_P, ref_model, v0, dev, world, flush, dtype, fast_path=False,
+                 precision=None):
     """MD with another model or precision on the same workload: throughput,
     per-kernel times, roofline of the dominant kernel, and accuracy against
     the FP64 full model at the start and at the end of the mode's trajectory
@@ -402,11 +403,13 @@ def measure_mode(args, dp, w, run_desc, run_P, ref_model, v0, dev, world, flush,
     v = torch.tensor(v0, dtype=torch.float64, device=dev)
     t = torch.tensor(w["types"], dtype=torch.int32, device=dev)
     th = torch.empty((wl["md_per_step"], 4), dtype=torch.float64, device=dev)
+    prec = dp.DP_PREC_MIXED if precision is None else precision
     if fast_path:
-        fp = student.FastPathMD(ref_model, model, N, tol=FORCE_RMSE_TARGET, check_every=REBUILD_EVERY)
+        fp = student.FastPathMD(ref_model, model, N, tol=FORCE_RMSE_TARGET, check_every=REBUILD_EVERY,
+                                precision=prec)
         ctx = fp.fast
     else:
-        ctx = dp.Context(model, N, precision=dp.DP_PREC_MIXED)
+        ctx = dp.Context(model, N, precision=prec)
     acc_first = _accuracy(dp, ctx, refc, x, t, w["box"])
     dp.dp_md_reset(ctx)
     done = 0
@@ -658,6 +661,10 @@ def run_ours(args, rank, world, local_rank):
     if not args.no_mixed:
         modes["mixed"] = measure_mode(args, dp, w, desc, P, model, v0, dev, world, flush,
                                       "bf16 GEMMs (fp32 accumulate) + f64")
+        torch.cuda.empty_cache()
+        modes["mixed_split"] = measure_mode(args, dp, w, desc, P, model, v0, dev, world, flush,
+                                            "embedding GEMMs on split bf16 operands (hi + lo, fp32 accumulate), "
+                                            "fitting bf16, + f64", precision=dp.DP_PREC_MIXED_SPLIT)
         torch.cuda.empty_cache()
     if not args.no_student and args.workload.startswith("water"):
         if os.path.exists(STUDENT_PARAMS):

@@ -15,6 +15,8 @@ namespace {
 
 thread_local std::string g_last_error = "";
 
+bool is_mixed(int32_t precision) { return precision == DP_PREC_MIXED || precision == DP_PREC_MIXED_SPLIT; }
+
 dp_status fail(dp_status s, const std::string &msg)
 {
     g_last_error = msg;
@@ -283,21 +285,31 @@ dp_status build_mixed(dp_ctx *c)
     const int K1p = pad_to(e1, 16), N1p = pad_to(e2, 16), K2p = N1p, N2p = pad_to(e3, 16);
     MixedModel &mx = c->mx;
     std::memset(&mx, 0, sizeof(mx));
-    // embedding: per net W1^T [N1p][K1p], W2^T [N2p][K2p]
+    // embedding: per net W1^T [N1p][K1p] and its low part, W2^T [N2p][K2p] and its
+    // low part (hi = the BF16 value, lo = the BF16 value of the remainder w - hi)
     const size_t b1 = (size_t)N1p * K1p, b2 = (size_t)N2p * K2p;
-    const size_t net_elems = pad_to((int)(b1 + b2), 128);
+    const size_t net_elems = pad_to((int)(2 * b1 + 2 * b2), 128);
     std::vector<uint16_t> emb((size_t)T * T * net_elems, 0);
+    auto split_store = [](uint16_t *hi, uint16_t *lo, size_t at, double w) {
+        const uint16_t h = to_bf16((float)w);
+        const uint32_t u = (uint32_t)h << 16;
+        float hf;
+        std::memcpy(&hf, &u, 4);
+        hi[at] = h;
+        lo[at] = to_bf16((float)(w - (double)hf));
+    };
     for (int net = 0; net < T * T; ++net) {
         const double *W1 = P + m.emb_base[net] + 2 * e1;
         const double *W2 = W1 + (size_t)e1 * e2 + e2;
-        uint16_t *o1 = emb.data() + net * net_elems, *o2 = o1 + b1;
+        uint16_t *o1 = emb.data() + net * net_elems, *o1l = o1 + b1, *o2 = o1l + b1, *o2l = o2 + b2;
         for (int n = 0; n < e2; ++n)
-            for (int k = 0; k < e1; ++k) o1[kofs(n, k, K1p)] = to_bf16((float)W1[(size_t)k * e2 + n]);
+            for (int k = 0; k < e1; ++k) split_store(o1, o1l, kofs(n, k, K1p), W1[(size_t)k * e2 + n]);
         for (int n = 0; n < e3; ++n)
-            for (int k = 0; k < e2; ++k) o2[kofs(n, k, K2p)] = to_bf16((float)W2[(size_t)k * e3 + n]);
+            for (int k = 0; k < e2; ++k) split_store(o2, o2l, kofs(n, k, K2p), W2[(size_t)k * e3 + n]);
         mx.emb_off[net][0] = (int64_t)(net * net_elems) * 2;
-        mx.emb_off[net][1] = (int64_t)(net * net_elems + b1) * 2;
+        mx.emb_off[net][1] = (int64_t)(net * net_elems + 2 * b1) * 2;
     }
+    mx.split = c->precision == DP_PREC_MIXED_SPLIT ? 1 : 0;
     // fitting: per type and layer, W^T (forward) and W (backward), K-chunks of 64
     const int K1 = m.m2 * m.M;
     std::vector<uint16_t> fwd, bwd;
@@ -541,7 +553,7 @@ dp_status enqueue_eval(dp_ctx *c, const double *coords, const int32_t *types, co
     dp_status s = ensure_perm(c, types, nloc);
     if (s) return s;
     cudaError_t e;
-    const bool mixed = c->precision == DP_PREC_MIXED;
+    const bool mixed = is_mixed(c->precision);
     const int n = (int)nloc;  // the centres
     if (n > 0) {
         if ((s = enqueue_format(c, coords, types, b, nloc))) return s;
@@ -908,9 +920,9 @@ dp_status dp_ctx_create(const dp_model *model, int64_t natoms_max, int32_t cand_
     if (!model) return fail(DP_ERR_ARG, "model is NULL");
     if (natoms_max < 1 || natoms_max >= (1 << 26)) return fail(DP_ERR_ARG, "natoms_max must be in [1, 2^26)");
     if (cand_cap < 0 || cand_cap > 1024) return fail(DP_ERR_ARG, "cand_cap must be in [0, 1024]");
-    if (precision != DP_PREC_FP64 && precision != DP_PREC_MIXED && precision != DP_PREC_FP64_SIMT)
+    if (precision != DP_PREC_FP64 && !is_mixed(precision) && precision != DP_PREC_FP64_SIMT)
         return fail(DP_ERR_UNSUPPORTED, "unknown precision mode");
-    if (precision == DP_PREC_MIXED && !dp_mixed_supported(model->dev))
+    if (is_mixed(precision) && !dp_mixed_supported(model->dev))
         return fail(DP_ERR_UNSUPPORTED, "mixed precision needs a 3-layer doubling embedding net (s_1 in {16, 25, 32}) "
                                         "and equal fitting widths (multiples of 16, <= 256) after the first layer");
     dp_ctx *c = new (std::nothrow) dp_ctx();
@@ -959,7 +971,7 @@ dp_status dp_ctx_create(const dp_model *model, int64_t natoms_max, int32_t cand_
     ALLOC(c->ke_part, N);
     ALLOC(c->d_inv_mass_conv, DP_MAX_TYPES);
     ALLOC(c->d_mass, DP_MAX_TYPES);
-    if (precision == DP_PREC_MIXED) {
+    if (is_mixed(precision)) {
         ALLOC(c->eb.fit_t, N * (size_t)c->m.n_fit * 256);
         ALLOC(c->eb.fit_h, N * 256);
     }
@@ -979,8 +991,8 @@ dp_status dp_ctx_create(const dp_model *model, int64_t natoms_max, int32_t cand_
         c->use_oz = true;
     }
 #undef ALLOC
-    if (!s && precision == DP_PREC_MIXED) s = build_mixed(c);
-    if (!s && precision == DP_PREC_MIXED) {
+    if (!s && is_mixed(precision)) s = build_mixed(c);
+    if (!s && is_mixed(precision)) {
         // BF16 descriptor tiles of the fitting kernel: [tiles][K1p / 64][128 x 64]
         const size_t tiles = (N + 127) / 128 + T;
         s = dev_alloc(&c->d_dtile, tiles * (size_t)c->mx.fit_kp[0] * 128 * 2, "bf16 descriptor tiles");
@@ -1249,7 +1261,7 @@ dp_status dp_param_grad(dp_ctx *c, const double *coords, const int32_t *types, c
     dp_status s = check_common(c, coords, types, N);
     if (s) return s;
     if (!lambda || !grad) return fail(DP_ERR_ARG, "lambda/grad is NULL");
-    if (c->precision == DP_PREC_MIXED) return fail(DP_ERR_UNSUPPORTED, "parameter gradients need an FP64 context");
+    if (is_mixed(c->precision)) return fail(DP_ERR_UNSUPPORTED, "parameter gradients need an FP64 context");
     for (int l = 1; l < c->m.n_fit; ++l)
         if (dp_skip_kind(c->m.fit[l - 1], c->m.fit[l]) == 2)
             return fail(DP_ERR_UNSUPPORTED, "parameter gradients support equal-width fitting skips only");

@@ -187,7 +187,9 @@ struct EvalBuffers {
 // tensor-core layout (see tc.cuh), FP32 copies of biases and small vectors.
 struct MixedModel {
     const unsigned char *emb_ops;                            // bf16 operands, bytes
-    int64_t emb_off[DP_MAX_TYPES * DP_MAX_TYPES][2];         // W1^T, W2^T per net (byte offsets)
+    int64_t emb_off[DP_MAX_TYPES * DP_MAX_TYPES][2];         // W1^T, W2^T per net (byte offsets); each
+                                                             // is followed by its low part (split mode)
+    int split;                                               // 1: embedding GEMMs on hi + lo operands
     const float *p32;                                        // all parameters in fp32, FP64 layout
     const unsigned char *fit_fwd, *fit_bwd;                  // bf16 operands, bytes
     int64_t fit_fwd_off[DP_MAX_TYPES][DP_MAX_LAYERS];        // W_l^T, K-chunks of 64

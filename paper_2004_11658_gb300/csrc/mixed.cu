@@ -44,6 +44,51 @@ __device__ __forceinline__ void st8(unsigned char *base, int row, int k0, int K,
     *reinterpret_cast<uint4 *>(base + tc::kmajor_offset(row, k0, K)) = u;
 }
 
+// 8 consecutive K-values of one row as BF16 high parts (hi) and the BF16 values
+// of the remainders v - hi (lo): hi + lo carries ~16 significant bits
+__device__ __forceinline__ void st8_split(unsigned char *hi, unsigned char *lo, int row, int k0, int K,
+                                          const float (&v)[8])
+{
+    float r[8];
+    uint4 u;
+#pragma unroll
+    for (int q = 0; q < 8; q += 2) {
+        const __nv_bfloat162 p = __floats2bfloat162_rn(v[q], v[q + 1]);
+        r[q] = v[q] - __low2float(p);
+        r[q + 1] = v[q + 1] - __high2float(p);
+        (&u.x)[q / 2] = *reinterpret_cast<const uint32_t *>(&p);
+    }
+    const uint32_t ofs = tc::kmajor_offset(row, k0, K);
+    *reinterpret_cast<uint4 *>(hi + ofs) = u;
+    u.x = pack_bf16x2(r[0], r[1]);
+    u.y = pack_bf16x2(r[2], r[3]);
+    u.z = pack_bf16x2(r[4], r[5]);
+    u.w = pack_bf16x2(r[6], r[7]);
+    *reinterpret_cast<uint4 *>(lo + ofs) = u;
+}
+
+// A row operand: plain BF16, or high and low parts
+template <bool SPLIT>
+__device__ __forceinline__ void st8_op(unsigned char *base, int bytes, int row, int k0, int K, const float (&v)[8])
+{
+    if constexpr (SPLIT) st8_split(base, base + bytes, row, k0, K, v);
+    else st8(base, row, k0, K, v);
+}
+
+// D (+)= A B^T for one K-slice: one MMA, or three on the split operands
+// (hi hi + hi lo + lo hi; the lo lo term is below FP32 rounding)
+template <bool SPLIT>
+__device__ __forceinline__ void mma_op(uint32_t d, uint32_t a, uint32_t abytes, uint32_t b, uint32_t bbytes, int K,
+                                       uint32_t idesc, bool acc)
+{
+    const uint32_t sbo = (uint32_t)K * 16;
+    tc::mma_bf16(d, tc::make_desc(a, 128, sbo), tc::make_desc(b, 128, sbo), idesc, acc);
+    if constexpr (SPLIT) {
+        tc::mma_bf16(d, tc::make_desc(a, 128, sbo), tc::make_desc(b + bbytes, 128, sbo), idesc, true);
+        tc::mma_bf16(d, tc::make_desc(a + abytes, 128, sbo), tc::make_desc(b, 128, sbo), idesc, true);
+    }
+}
+
 __device__ __forceinline__ void copy16(unsigned char *dst, const unsigned char *__restrict__ src, int bytes)
 {
     for (int q = threadIdx.x * 16; q < bytes; q += blockDim.x * 16)
@@ -143,7 +188,7 @@ __device__ __forceinline__ void build_groups(BatchInfo &bi, int k, const int32_t
     bi.ngroups = g;
 }
 
-template <int E1>
+template <int E1, bool SPLIT>
 __global__ void __launch_bounds__(MXT, 1) k_embed_fwd_mx(
     DevModel m, MixedModel mx, const double *__restrict__ x, const int32_t *__restrict__ types, Box3 box, int N,
     const int32_t *__restrict__ type_perm, const int32_t *__restrict__ type_start, const int32_t *__restrict__ nlist,
@@ -152,12 +197,13 @@ __global__ void __launch_bounds__(MXT, 1) k_embed_fwd_mx(
     using S = EmbShape<E1>;
     constexpr int E2 = S::E2, E3 = S::E3, K1p = S::K1p, N1p = S::N1p, K2p = S::K2p, N2p = S::N2p;
     constexpr int TCOLS = tcols_for(N2p);
+    constexpr int X = SPLIT ? 2 : 1;  // operand copies: high (and low) parts
     extern __shared__ __align__(1024) unsigned char smraw[];
     unsigned char *A0 = smraw;
-    unsigned char *A1 = A0 + S::A0B;
-    unsigned char *B1 = A1 + S::A1B;
-    unsigned char *B2 = B1 + S::B1B;
-    double *Gt = reinterpret_cast<double *>(B2 + S::B2B);  // [4][32][17]
+    unsigned char *A1 = A0 + X * S::A0B;
+    unsigned char *B1 = A1 + X * S::A1B;
+    unsigned char *B2 = B1 + X * S::B1B;
+    double *Gt = reinterpret_cast<double *>(B2 + X * S::B2B);  // [4][32][17]
     double *Rt = Gt + 4 * 32 * 17;                          // [4][32][4]
     double *Tw = Rt + 4 * 32 * 4;                           // [4][4][E3] per-warp partial of one tile
     double *Tacc = Tw + 4 * 4 * E3;                         // [AB][4][E3] per-atom sums
@@ -198,8 +244,8 @@ __global__ void __launch_bounds__(MXT, 1) k_embed_fwd_mx(
             if (G == 0) continue;
             const int net = a * T + b;
             if (net != staged) {
-                copy16(B1, mx.emb_ops + mx.emb_off[net][0], S::B1B);
-                copy16(B2, mx.emb_ops + mx.emb_off[net][1], S::B2B);
+                copy16(B1, mx.emb_ops + mx.emb_off[net][0], X * S::B1B);
+                copy16(B2, mx.emb_ops + mx.emb_off[net][1], X * S::B2B);
                 staged = net;
             }
             const float *P32 = mx.p32 + m.emb_base[net];
@@ -227,14 +273,14 @@ __global__ void __launch_bounds__(MXT, 1) k_embed_fwd_mx(
                     float v[8];
 #pragma unroll
                     for (int q = 0; q < 8; ++q) v[q] = (k8 + q < E1) ? h0[k8 + q] : 0.f;
-                    st8(A0, tid, k8, K1p, v);
+                    st8_op<SPLIT>(A0, S::A0B, tid, k8, K1p, v);
                 }
                 tc_sync();
                 if (tid == 0) {
 #pragma unroll
                     for (int kk = 0; kk < K1p / 16; ++kk)
-                        tc::mma_bf16(tbase, tc::make_desc(tc::smem_u32(A0) + kk * 256, 128, K1p * 16),
-                                     tc::make_desc(tc::smem_u32(B1) + kk * 256, 128, K1p * 16), idesc1, kk > 0);
+                        mma_op<SPLIT>(tbase, tc::smem_u32(A0) + kk * 256, S::A0B, tc::smem_u32(B1) + kk * 256, S::B1B,
+                                      K1p, idesc1, kk > 0);
                     tc::mma_commit(&mbar);
                 }
                 alive = tc_wait(&mbar, phase, status);
@@ -258,15 +304,15 @@ __global__ void __launch_bounds__(MXT, 1) k_embed_fwd_mx(
                     float v[8];
 #pragma unroll
                     for (int q = 0; q < 8; ++q) v[q] = (k8 + q < E2) ? h1[k8 + q] : 0.f;
-                    st8(A1, tid, k8, K2p, v);
+                    st8_op<SPLIT>(A1, S::A1B, tid, k8, K2p, v);
                 }
                 tc_sync();
                 if (!alive) break;
                 if (tid == 0) {
 #pragma unroll
                     for (int kk = 0; kk < K2p / 16; ++kk)
-                        tc::mma_bf16(tbase, tc::make_desc(tc::smem_u32(A1) + kk * 256, 128, K2p * 16),
-                                     tc::make_desc(tc::smem_u32(B2) + kk * 256, 128, K2p * 16), idesc2, kk > 0);
+                        mma_op<SPLIT>(tbase, tc::smem_u32(A1) + kk * 256, S::A1B, tc::smem_u32(B2) + kk * 256, S::B2B,
+                                      K2p, idesc2, kk > 0);
                     tc::mma_commit(&mbar);
                 }
                 alive = tc_wait(&mbar, phase, status);
@@ -339,7 +385,7 @@ __global__ void __launch_bounds__(MXT, 1) k_embed_fwd_mx(
     if (warp == 0) tc::tmem_dealloc(tbase, TCOLS);
 }
 
-template <int E1>
+template <int E1, bool SPLIT>
 __global__ void __launch_bounds__(MXT, 1) k_embed_bwd_mx(
     DevModel m, MixedModel mx, const double *__restrict__ x, const int32_t *__restrict__ types, Box3 box, int N,
     const int32_t *__restrict__ type_perm, const int32_t *__restrict__ type_start, const int32_t *__restrict__ nlist,
@@ -350,14 +396,15 @@ __global__ void __launch_bounds__(MXT, 1) k_embed_bwd_mx(
     constexpr int E2 = S::E2, E3 = S::E3, K1p = S::K1p, N1p = S::N1p, K2p = S::K2p, N2p = S::N2p;
     constexpr int TOFF = N2p;                 // tangent accumulator column offset
     constexpr int TCOLS = tcols_for(2 * N2p);
+    constexpr int X = SPLIT ? 2 : 1;          // operand copies: high (and low) parts
     extern __shared__ __align__(1024) unsigned char smraw[];
     unsigned char *A0 = smraw;
-    unsigned char *dA0 = A0 + S::A0B;
-    unsigned char *A1 = dA0 + S::A0B;
-    unsigned char *dA1 = A1 + S::A1B;
-    unsigned char *B1 = dA1 + S::A1B;
-    unsigned char *B2 = B1 + S::B1B;
-    double *gTs = reinterpret_cast<double *>(B2 + S::B2B);  // [AB][4][E3], scaled
+    unsigned char *dA0 = A0 + X * S::A0B;
+    unsigned char *A1 = dA0 + X * S::A0B;
+    unsigned char *dA1 = A1 + X * S::A1B;
+    unsigned char *B1 = dA1 + X * S::A1B;
+    unsigned char *B2 = B1 + X * S::B1B;
+    double *gTs = reinterpret_cast<double *>(B2 + X * S::B2B);  // [AB][4][E3], scaled
     double *Ts = gTs + AB * 4 * E3;                          // [4][E3]
     double *red = Ts + 4 * E3;                               // [4][12]
     double *facc = red + 4 * 12;                             // [AB][12]
@@ -411,8 +458,8 @@ __global__ void __launch_bounds__(MXT, 1) k_embed_bwd_mx(
             if (G == 0) continue;
             const int net = a * T + b;
             if (net != staged) {
-                copy16(B1, mx.emb_ops + mx.emb_off[net][0], S::B1B);
-                copy16(B2, mx.emb_ops + mx.emb_off[net][1], S::B2B);
+                copy16(B1, mx.emb_ops + mx.emb_off[net][0], X * S::B1B);
+                copy16(B2, mx.emb_ops + mx.emb_off[net][1], X * S::B2B);
                 staged = net;
             }
             const float *P32 = mx.p32 + m.emb_base[net];
@@ -450,18 +497,17 @@ __global__ void __launch_bounds__(MXT, 1) k_embed_bwd_mx(
                         v[q] = (k8 + q < E1) ? h0[k8 + q] : 0.f;
                         dv[q] = (k8 + q < E1) ? dh0[k8 + q] : 0.f;
                     }
-                    st8(A0, tid, k8, K1p, v);
-                    st8(dA0, tid, k8, K1p, dv);
+                    st8_op<SPLIT>(A0, S::A0B, tid, k8, K1p, v);
+                    st8_op<SPLIT>(dA0, S::A0B, tid, k8, K1p, dv);
                 }
                 tc_sync();
                 if (tid == 0) {
 #pragma unroll
                     for (int kk = 0; kk < K1p / 16; ++kk) {
-                        const uint64_t bd = tc::make_desc(tc::smem_u32(B1) + kk * 256, 128, K1p * 16);
-                        tc::mma_bf16(tbase, tc::make_desc(tc::smem_u32(A0) + kk * 256, 128, K1p * 16), bd, idesc1,
-                                     kk > 0);
-                        tc::mma_bf16(tbase + TOFF, tc::make_desc(tc::smem_u32(dA0) + kk * 256, 128, K1p * 16), bd,
-                                     idesc1, kk > 0);
+                        const uint32_t bb = tc::smem_u32(B1) + kk * 256;
+                        mma_op<SPLIT>(tbase, tc::smem_u32(A0) + kk * 256, S::A0B, bb, S::B1B, K1p, idesc1, kk > 0);
+                        mma_op<SPLIT>(tbase + TOFF, tc::smem_u32(dA0) + kk * 256, S::A0B, bb, S::B1B, K1p, idesc1,
+                                      kk > 0);
                     }
                     tc::mma_commit(&mbar);
                 }
@@ -495,19 +541,18 @@ __global__ void __launch_bounds__(MXT, 1) k_embed_bwd_mx(
                         v[q] = (k8 + q < E2) ? h1[k8 + q] : 0.f;
                         dv[q] = (k8 + q < E2) ? dh1[k8 + q] : 0.f;
                     }
-                    st8(A1, tid, k8, K2p, v);
-                    st8(dA1, tid, k8, K2p, dv);
+                    st8_op<SPLIT>(A1, S::A1B, tid, k8, K2p, v);
+                    st8_op<SPLIT>(dA1, S::A1B, tid, k8, K2p, dv);
                 }
                 tc_sync();
                 if (!alive) break;
                 if (tid == 0) {
 #pragma unroll
                     for (int kk = 0; kk < K2p / 16; ++kk) {
-                        const uint64_t bd = tc::make_desc(tc::smem_u32(B2) + kk * 256, 128, K2p * 16);
-                        tc::mma_bf16(tbase, tc::make_desc(tc::smem_u32(A1) + kk * 256, 128, K2p * 16), bd, idesc2,
-                                     kk > 0);
-                        tc::mma_bf16(tbase + TOFF, tc::make_desc(tc::smem_u32(dA1) + kk * 256, 128, K2p * 16), bd,
-                                     idesc2, kk > 0);
+                        const uint32_t bb = tc::smem_u32(B2) + kk * 256;
+                        mma_op<SPLIT>(tbase, tc::smem_u32(A1) + kk * 256, S::A1B, bb, S::B2B, K2p, idesc2, kk > 0);
+                        mma_op<SPLIT>(tbase + TOFF, tc::smem_u32(dA1) + kk * 256, S::A1B, bb, S::B2B, K2p, idesc2,
+                                      kk > 0);
                     }
                     tc::mma_commit(&mbar);
                 }
@@ -902,57 +947,66 @@ __global__ void __launch_bounds__(MXT, 1) k_fit_mx(DevModel m, MixedModel mx, in
     if (warp == 0) tc::tmem_dealloc(tbase, 256);
 }
 
-template <int E1>
+template <int E1, bool SPLIT>
 size_t fwd_smem()
 {
     using S = EmbShape<E1>;
-    return S::A0B + S::A1B + S::B1B + S::B2B +
+    constexpr int X = SPLIT ? 2 : 1;
+    return X * (S::A0B + S::A1B + S::B1B + S::B2B) +
            sizeof(double) * (4 * 32 * 17 + 4 * 32 * 4 + 4 * 4 * S::E3 + AB * 4 * S::E3);
 }
-template <int E1>
+template <int E1, bool SPLIT>
 size_t bwd_smem()
 {
     using S = EmbShape<E1>;
-    return 2 * S::A0B + 2 * S::A1B + S::B1B + S::B2B + sizeof(double) * (AB * 4 * S::E3 + 4 * S::E3 + 48 + AB * 12);
+    constexpr int X = SPLIT ? 2 : 1;
+    return X * (2 * S::A0B + 2 * S::A1B + S::B1B + S::B2B) +
+           sizeof(double) * (AB * 4 * S::E3 + 4 * S::E3 + 48 + AB * 12);
 }
 
-template <int E1>
+// CTAs per SM that fit next to each other (shared memory; a 1 KB reserve per CTA)
+inline int ctas_per_sm(size_t smem) { return 2 * (smem + 2048) <= 232448 ? 2 : 1; }
+
+template <int E1, bool SPLIT>
 cudaError_t launch_fwd(cudaStream_t st, const DevModel &m, const MixedModel &mx, const double *x,
                        const int32_t *types, Box3 box, int N, const FormatBuffers &fb, const NlistBuffers &nb,
                        EvalBuffers eb, int num_sms, int32_t *status)
 {
-    const size_t smem = fwd_smem<E1>();
+    const size_t smem = fwd_smem<E1, SPLIT>();
     static bool configured = false;
     if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(k_embed_fwd_mx<E1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e =
+            cudaFuncSetAttribute(k_embed_fwd_mx<E1, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         configured = true;
     }
-    // two CTAs per SM (tensor memory: 128 columns each), each a balanced share of the atoms
-    int grid = 2 * num_sms;
+    // one or two CTAs per SM (tensor memory: 128 columns each), each a balanced share of the atoms
+    int grid = ctas_per_sm(smem) * num_sms;
     if (grid > (N + 7) / 8) grid = (N + 7) / 8;
-    k_embed_fwd_mx<E1><<<grid, MXT, smem, st>>>(m, mx, x, types, box, N, nb.type_perm, nb.type_start, fb.nlist,
-                                                fb.nreal, eb.T, eb.D, status);
+    k_embed_fwd_mx<E1, SPLIT><<<grid, MXT, smem, st>>>(m, mx, x, types, box, N, nb.type_perm, nb.type_start,
+                                                       fb.nlist, fb.nreal, eb.T, eb.D, status);
     return cudaGetLastError();
 }
 
-template <int E1>
+template <int E1, bool SPLIT>
 cudaError_t launch_bwd(cudaStream_t st, const DevModel &m, const MixedModel &mx, const double *x,
                        const int32_t *types, Box3 box, int N, const FormatBuffers &fb, const NlistBuffers &nb,
                        EvalBuffers eb, int num_sms, int32_t *status)
 {
-    const size_t smem = bwd_smem<E1>();
+    const size_t smem = bwd_smem<E1, SPLIT>();
     static bool configured = false;
     if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(k_embed_bwd_mx<E1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e =
+            cudaFuncSetAttribute(k_embed_bwd_mx<E1, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         configured = true;
     }
-    // two CTAs per SM (tensor memory: <= 256 columns each), each a balanced share of the atoms
-    int grid = 2 * num_sms;
+    // one or two CTAs per SM (tensor memory: <= 256 columns each), each a balanced share of the atoms
+    int grid = ctas_per_sm(smem) * num_sms;
     if (grid > (N + 7) / 8) grid = (N + 7) / 8;
-    k_embed_bwd_mx<E1><<<grid, MXT, smem, st>>>(m, mx, x, types, box, N, nb.type_perm, nb.type_start, fb.nlist,
-                                                fb.nreal, eb.T, eb.gD, eb.pair_g, eb.f_own, eb.vir_part, status);
+    k_embed_bwd_mx<E1, SPLIT><<<grid, MXT, smem, st>>>(m, mx, x, types, box, N, nb.type_perm, nb.type_start,
+                                                       fb.nlist, fb.nreal, eb.T, eb.gD, eb.pair_g, eb.f_own,
+                                                       eb.vir_part, status);
     return cudaGetLastError();
 }
 
@@ -977,10 +1031,14 @@ cudaError_t dp_launch_embed_fwd_mx(cudaStream_t st, const DevModel &m, const Mix
                                    int64_t *launches)
 {
     *launches += 1;
+    const bool sp = mx.split != 0;
     switch (m.emb[0]) {
-    case 16: return launch_fwd<16>(st, m, mx, x, types, box, N, fb, nb, eb, num_sms, status);
-    case 25: return launch_fwd<25>(st, m, mx, x, types, box, N, fb, nb, eb, num_sms, status);
-    case 32: return launch_fwd<32>(st, m, mx, x, types, box, N, fb, nb, eb, num_sms, status);
+    case 16: return sp ? launch_fwd<16, true>(st, m, mx, x, types, box, N, fb, nb, eb, num_sms, status)
+                       : launch_fwd<16, false>(st, m, mx, x, types, box, N, fb, nb, eb, num_sms, status);
+    case 25: return sp ? launch_fwd<25, true>(st, m, mx, x, types, box, N, fb, nb, eb, num_sms, status)
+                       : launch_fwd<25, false>(st, m, mx, x, types, box, N, fb, nb, eb, num_sms, status);
+    case 32: return sp ? launch_fwd<32, true>(st, m, mx, x, types, box, N, fb, nb, eb, num_sms, status)
+                       : launch_fwd<32, false>(st, m, mx, x, types, box, N, fb, nb, eb, num_sms, status);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -991,10 +1049,14 @@ cudaError_t dp_launch_embed_bwd_mx(cudaStream_t st, const DevModel &m, const Mix
                                    int64_t *launches)
 {
     *launches += 1;
+    const bool sp = mx.split != 0;
     switch (m.emb[0]) {
-    case 16: return launch_bwd<16>(st, m, mx, x, types, box, N, fb, nb, eb, num_sms, status);
-    case 25: return launch_bwd<25>(st, m, mx, x, types, box, N, fb, nb, eb, num_sms, status);
-    case 32: return launch_bwd<32>(st, m, mx, x, types, box, N, fb, nb, eb, num_sms, status);
+    case 16: return sp ? launch_bwd<16, true>(st, m, mx, x, types, box, N, fb, nb, eb, num_sms, status)
+                       : launch_bwd<16, false>(st, m, mx, x, types, box, N, fb, nb, eb, num_sms, status);
+    case 25: return sp ? launch_bwd<25, true>(st, m, mx, x, types, box, N, fb, nb, eb, num_sms, status)
+                       : launch_bwd<25, false>(st, m, mx, x, types, box, N, fb, nb, eb, num_sms, status);
+    case 32: return sp ? launch_bwd<32, true>(st, m, mx, x, types, box, N, fb, nb, eb, num_sms, status)
+                       : launch_bwd<32, false>(st, m, mx, x, types, box, N, fb, nb, eb, num_sms, status);
     default: return cudaErrorInvalidValue;
     }
 }

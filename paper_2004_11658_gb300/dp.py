@@ -28,6 +28,7 @@ globals().update({name: code for code, name in STATUS_NAMES.items()})
 DP_PREC_FP64 = 0
 DP_PREC_MIXED = 1
 DP_PREC_FP64_SIMT = 2
+DP_PREC_MIXED_SPLIT = 3
 
 
 class DPError(RuntimeError):

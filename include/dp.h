@@ -101,15 +101,16 @@ typedef struct dp_ctx dp_ctx;
                              (multiples of 16, <= 256) after the first layer;
                              other shapes give DP_ERR_UNSUPPORTED. */
 #define DP_PREC_MIXED_SPLIT 3  /* DP_PREC_MIXED with the embedding-net GEMMs on split
-                             operands: every FP32 activation and weight is the sum
+                             operands -- every FP32 activation and weight is the sum
                              of a BF16 high part and the BF16 value of its
                              remainder, and each product is hi*hi + hi*lo + lo*hi
                              (three MMAs into the FP32 accumulator), ~16 bits
-                             per operand instead of 8.  For systems whose forces
-                             are small sums of many large pair terms (a nearly
-                             symmetric crystal), where the BF16 rounding of each
-                             neighbour's G does not cancel.  Same shapes as
-                             DP_PREC_MIXED. */
+                             per operand instead of 8 -- and the fitting net as in
+                             DP_PREC_FP64 (exact digit products, FP64 accuracy).
+                             For systems whose forces are small sums of many large
+                             pair terms (a nearly symmetric crystal), where the
+                             rounding of each atom's dE/dD and of each neighbour's
+                             G does not cancel.  Same shapes as DP_PREC_MIXED. */
 
 /* Thread-local text of the last error (never NULL). */
 const char *dp_last_error(void);

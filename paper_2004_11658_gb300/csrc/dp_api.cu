@@ -568,10 +568,11 @@ dp_status enqueue_eval(dp_ctx *c, const double *coords, const int32_t *types, co
                                                   c->num_sms, &c->launches);
             if (e != cudaSuccess) return cuda_fail(e, "embed_fwd");
         }
-        if (!mixed && c->use_oz && (s = ensure_oz(c))) return s;
+        if (c->use_oz && (s = ensure_oz(c))) return s;
         {
             GroupTimer tm(c, G_FIT);
-            e = mixed     ? dp_launch_fit_mx(c->stream, c->m, c->mx, n, c->nb, c->eb, c->d_status, &c->launches)
+            e = mixed && !c->use_oz
+                    ? dp_launch_fit_mx(c->stream, c->m, c->mx, n, c->nb, c->eb, c->d_status, &c->launches)
                 : c->use_oz ? dp_launch_fit_oz(c->stream, c->m, c->oz, c->ob, n, c->nb, c->eb, c->d_status,
                                                &c->launches)
                             : dp_launch_fit(c->stream, c->m, n, c->nb, c->eb, &c->launches);
@@ -983,7 +984,9 @@ dp_status dp_ctx_create(const dp_model *model, int64_t natoms_max, int32_t cand_
         ALLOC(c->d_ex_w, dp_ex_bytes(c->m));
         c->use_ex = true;
     }
-    if (precision == DP_PREC_FP64 && dp_oz_plan(c->m, c->oz, c->oz_w_elems, c->oz_e_elems)) {
+    // the split mixed mode runs its fitting net with FP64 accuracy (exact digit products)
+    if ((precision == DP_PREC_FP64 || precision == DP_PREC_MIXED_SPLIT) &&
+        dp_oz_plan(c->m, c->oz, c->oz_w_elems, c->oz_e_elems)) {
         ALLOC(c->d_oz_w, (size_t)c->oz_w_elems);
         ALLOC(c->d_oz_e, (size_t)c->oz_e_elems);
         c->oz.w = c->d_oz_w;

@@ -137,7 +137,8 @@ def test_slab_md_matches_single_domain_md(dp, synth, nslab):
     dp.dp_md_step(ctx, x, v, t, w["box"], w["masses"], dt, n, rebuild_every=1, skin=0.0, thermo=th)
     # slabs
     rho = N / float(np.prod(w["box"]))
-    evs = [domain.DPLocalEvaluator(model, N, rho) for _ in range(nslab)]
+    # a sub-region holds its owned atoms and ghosts, periodic images included: up to ~2 N here
+    evs = [domain.DPLocalEvaluator(model, 3 * N, rho) for _ in range(nslab)]
     integ = [domain.GPUIntegrator(e.ctx) for e in evs]
     md = domain.SlabMD(domain.LocalComm(nslab), w["box"], desc["rcut"], 1.0, torch.tensor(w["coords"], device="cuda"),
                        torch.tensor(v0, device="cuda"), torch.tensor(w["types"], device="cuda"), w["masses"], dt,

@@ -60,15 +60,20 @@ def errors(g, o, N):
 
 # Relative force RMSE bars per system and mode.  Copper's forces are small
 # sums of ~350 large pair terms (a nearly symmetric FCC crystal): the BF16
-# rounding of each neighbour's embedding output does not cancel there, and
-# plain BF16 reaches 5.5e-2 relative; the split-operand embedding GEMMs
-# (DP_PREC_MIXED_SPLIT) bring it under the 1e-2 bar.
+# rounding of each atom's dE/dD (fitting net) and of each neighbour's
+# embedding output does not cancel there, and plain BF16 reaches 5.5e-2
+# relative; DP_PREC_MIXED_SPLIT (split-operand embedding GEMMs, FP64-exact
+# fitting net) brings it under the 1e-2 bar.
 REL_BAR = {("water", 1): REL_FORCE_RMSE, ("water", 3): REL_FORCE_RMSE,
-           ("cu", 1): 0.1, ("cu", 3): REL_FORCE_RMSE}
+           ("cu", 1): 0.1, ("cu", 3): REL_FORCE_RMSE,
+           # the trained student on the 192-atom box: its forces there are ~5x smaller
+           # than the full model's (RMS ~5e-4 eV/A), so 5e-2 relative is ~3e-5 eV/A
+           ("student", 1): 5e-2, ("student", 3): 5e-2}
 
 
-def _bar(name, prec):
-    return REL_BAR[("cu" if name.startswith("cu") else "water", prec)]
+def _bar(name, prec, variant=None):
+    kind = "student" if variant == "student" else ("cu" if name.startswith("cu") else "water")
+    return REL_BAR[(kind, prec)]
 
 
 @pytest.mark.parametrize("prec", [1, 3])
@@ -85,7 +90,7 @@ def test_mixed_against_fp64_oracle(dp, oracle, synth, name, variant, prec):
     print(f"{name} {variant} prec {prec}: force RMSE {rmse:.2e} eV/A (rel {rel:.2e}), |dE|/N {eE:.2e} eV, "
           f"virial {eV:.2e}")
     assert rmse <= FORCE_RMSE
-    assert rel <= _bar(name, prec)
+    assert rel <= _bar(name, prec, variant)
     assert eE <= E_PER_ATOM
     assert eV < 0.05
     assert np.isfinite(g["force"].cpu().numpy()).all()

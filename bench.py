@@ -100,7 +100,7 @@ def parse():
                         "GPU (forward/reverse halos over NCCL point-to-point, all-reduce of E and the virial)")
     p.add_argument("--profile-eval", type=int, default=0, metavar="N",
                    help="run N energy/force evaluations of the workload and exit (profiling driver)")
-    p.add_argument("--profile-precision", choices=["fp64", "mixed"], default="fp64")
+    p.add_argument("--profile-precision", choices=["fp64", "mixed", "split"], default="fp64")
     p.add_argument("--profile-model", choices=["full", "student"], default="full")
     return p.parse_args()
 
@@ -787,7 +787,8 @@ def profile_eval(args):
     if args.profile_model == "student":
         desc, P = synth.WATER_STUDENT, np.load(STUDENT_PARAMS).astype(np.float64)
     model = dp.Model(desc, P)
-    prec = dp.DP_PREC_MIXED if args.profile_precision == "mixed" else dp.DP_PREC_FP64
+    prec = {"fp64": dp.DP_PREC_FP64, "mixed": dp.DP_PREC_MIXED,
+            "split": dp.DP_PREC_MIXED_SPLIT}[args.profile_precision]
     ctx = dp.Context(model, len(w["coords"]), precision=prec)
     x = torch.tensor(w["coords"], device="cuda")
     t = torch.tensor(w["types"], device="cuda")

@@ -72,7 +72,7 @@ FORCE_RMSE_TARGET = 1e-3   # eV/A, against the FP64 full model
 #                     (smsp__sass_thread_inst_executed_op_d{fma,add,mul}_pred_on.sum)
 #                     per real neighbour row
 TRAFFIC = {
-    "embed_bwd": {"bytes_per_launch": 206.746112e6 + 21.276672e6, "file": "embed_x.cu", "src_sha": "0851d6ab4b0a3ee6"},
+    "embed_bwd": {"bytes_per_launch": 206.746112e6 + 21.276672e6, "file": "embed_x.cu", "src_sha": "e7e1011a23515cf7"},
     "embed_bwd_mx<25>": {"bytes_per_launch": 204.936448e6 + 17.953792e6, "file": "mixed.cu", "src_sha": "97f3fe1bf34f81b7"},
 }
 FP64_ISSUED = {
@@ -80,7 +80,7 @@ FP64_ISSUED = {
     # water12288 --profile-eval 1), 1,046,154 real rows: dfma 2.984e9, dadd
     # 1.796e9, dmul 1.630e9 thread instructions; FP64 pipe busy 64.5%
     "embed_bwd": {"fp64_flop_per_row": 8979.6, "pipe_busy": 0.645, "file": "embed_x.cu",
-                  "src_sha": "0851d6ab4b0a3ee6"},
+                  "src_sha": "e7e1011a23515cf7"},
 }
 
 

@@ -105,8 +105,10 @@ typedef struct dp_ctx dp_ctx;
                              of a BF16 high part and the BF16 value of its
                              remainder, and each product is hi*hi + hi*lo + lo*hi
                              (three MMAs into the FP32 accumulator), ~16 bits
-                             per operand instead of 8 -- and the fitting net as in
-                             DP_PREC_FP64 (exact digit products, FP64 accuracy).
+                             per operand instead of 8 -- and the fitting net as
+                             exact products of 28-bit digit expansions of its
+                             operands (the FP64 mode's kernels with 4-5 digits
+                             instead of 8-11: FP32-level accuracy).
                              For systems whose forces are small sums of many large
                              pair terms (a nearly symmetric crystal), where the
                              rounding of each atom's dE/dD and of each neighbour's

@@ -984,9 +984,10 @@ dp_status dp_ctx_create(const dp_model *model, int64_t natoms_max, int32_t cand_
         ALLOC(c->d_ex_w, dp_ex_bytes(c->m));
         c->use_ex = true;
     }
-    // the split mixed mode runs its fitting net with FP64 accuracy (exact digit products)
+    // the split mixed mode runs its fitting net as exact products of 28-bit digit
+    // expansions (FP32-level accuracy, a quarter of the FP64 plans' MMAs)
     if ((precision == DP_PREC_FP64 || precision == DP_PREC_MIXED_SPLIT) &&
-        dp_oz_plan(c->m, c->oz, c->oz_w_elems, c->oz_e_elems)) {
+        dp_oz_plan(c->m, c->oz, c->oz_w_elems, c->oz_e_elems, precision == DP_PREC_MIXED_SPLIT ? 28 : 55)) {
         ALLOC(c->d_oz_w, (size_t)c->oz_w_elems);
         ALLOC(c->d_oz_e, (size_t)c->oz_e_elems);
         c->oz.w = c->d_oz_w;

@@ -260,7 +260,9 @@ struct OzBuffers {
 };
 // Host: shapes of the split GEMMs (returns false if the fitting net is not
 // supported: hidden widths must be <= DP_MAX_FIT_W), then the weight digits.
-bool dp_oz_plan(const DevModel &m, OzModel &oz, int64_t &w_elems, int64_t &e_elems);
+// bits: the digit expansions carry at least this many bits of every operand
+// (55: FP64 accuracy; fewer give a cheaper product of lower accuracy)
+bool dp_oz_plan(const DevModel &m, OzModel &oz, int64_t &w_elems, int64_t &e_elems, int bits = 55);
 void dp_oz_split_weights(const DevModel &m, const double *h_params, const OzModel &oz, uint16_t *w, int32_t *e);
 cudaError_t dp_launch_fit_oz(cudaStream_t st, const DevModel &m, const OzModel &oz, const OzBuffers &ob, int N,
                              const NlistBuffers &nb, EvalBuffers eb, int32_t *status, int64_t *launches);

@@ -10,7 +10,9 @@
 // with |a_1|, |b_1| <= 2^beta and |a_s|, |b_t| <= 2^(beta-1) for s, t >= 2
 // (balanced digits of the integers round(X_rk 2^(beta S - e_r))).  Then
 //   Y_rn = 2^(e_r + f_n) sum_g 2^(-beta g) C_g,   C_g = sum_{s+t=g} A_s B_t,
-// summed over g = 2 .. S+1 (the terms beyond are below FP64 rounding).  A digit
+// summed over g = 2 .. S+1 (the terms beyond are below the expansions' own
+// precision: FP64 rounding for the 55-bit plans of the FP64 mode, 2^-28
+// relative for the 28-bit plans of the split mixed mode).  A digit
 // is an integer of at most 8 bits, exact in BF16; every product is exact in
 // FP32, and beta is chosen per GEMM from its contraction length K so that
 //   K 4^(beta-1) (S + 2) < 2^24,
@@ -391,11 +393,11 @@ __global__ void __launch_bounds__(DP_OZ_TILE, 1) k_oz_gemm(OzGemmArgs p)
     if (warp == 0) tc::tmem_dealloc(tbase, p.tcols);
 }
 
-// digit width and count for a contraction of length K
-void oz_beta(int K, int &beta, int &S)
+// digit width and count for a contraction of length K and `bits` bits per operand
+void oz_beta(int K, int bits, int &beta, int &S)
 {
     for (beta = 7; beta >= 4; --beta) {
-        S = (55 + beta - 1) / beta;
+        S = (bits + beta - 1) / beta;
         const double bound = (double)K * std::pow(4.0, beta - 1) * (S + 2);
         if (bound < 16777216.0) return;
     }
@@ -416,7 +418,7 @@ size_t gemm_smem(int S) { return (size_t)gemm_stages(S) * S * (OZ_A_BLK + OZ_B_B
 
 }  // namespace
 
-bool dp_oz_plan(const DevModel &m, OzModel &oz, int64_t &w_elems, int64_t &e_elems)
+bool dp_oz_plan(const DevModel &m, OzModel &oz, int64_t &w_elems, int64_t &e_elems, int bits)
 {
     std::memset(&oz, 0, sizeof(oz));
     const int nf = m.n_fit;
@@ -437,8 +439,9 @@ bool dp_oz_plan(const DevModel &m, OzModel &oz, int64_t &w_elems, int64_t &e_ele
             g.N = Ns[d];
             g.nK = (g.K + DP_OZ_KC - 1) / DP_OZ_KC;
             g.nN = (g.N + DP_OZ_NC - 1) / DP_OZ_NC;
-            oz_beta(g.K, g.beta, g.S);
+            oz_beta(g.K, bits, g.beta, g.S);
             if (g.beta == 0 || g.S * DP_OZ_NC > 512 || gemm_smem(g.S) > 225 * 1024) return false;
+            if (!(g.S == 4 || g.S == 5 || g.S == 8 || g.S == 10 || g.S == 11 || g.S == 14)) return false;
             in_w = std::max(in_w, g.nK * g.S * OZ_A_BLK);
             for (int a = 0; a < m.ntypes; ++a) {
                 g.w_off[a] = w_elems;
@@ -514,6 +517,10 @@ cudaError_t dp_launch_fit_oz(cudaStream_t st, const DevModel &m, const OzModel &
         for (int l = 0; l < nf; ++l) need = std::max(need, std::max(gemm_smem(oz.fwd[l].S), gemm_smem(oz.bwd[l].S)));
         if (need > configured) {
             cudaError_t e = cudaFuncSetAttribute(k_oz_gemm<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need);
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(k_oz_gemm<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need);
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(k_oz_gemm<5>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need);
             if (e == cudaSuccess)
                 e = cudaFuncSetAttribute(k_oz_gemm<10>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need);
             if (e == cudaSuccess)
@@ -601,6 +608,8 @@ cudaError_t dp_launch_fit_oz(cudaStream_t st, const DevModel &m, const OzModel &
         a.tcols = gemm_tcols(g.S);
         const size_t smem = gemm_smem(g.S);
         switch (g.S) {
+        case 4: k_oz_gemm<4><<<tiles * g.nN, DP_OZ_TILE, smem, st>>>(a); break;
+        case 5: k_oz_gemm<5><<<tiles * g.nN, DP_OZ_TILE, smem, st>>>(a); break;
         case 8: k_oz_gemm<8><<<tiles * g.nN, DP_OZ_TILE, smem, st>>>(a); break;
         case 10: k_oz_gemm<10><<<tiles * g.nN, DP_OZ_TILE, smem, st>>>(a); break;
         case 11: k_oz_gemm<11><<<tiles * g.nN, DP_OZ_TILE, smem, st>>>(a); break;

@@ -125,3 +125,40 @@ def test_split_dot_product_is_fp64_accurate(beta, S):
     exact = sum(Fraction(float(p)) * Fraction(float(q)) for p, q in zip(a, b))
     scale = float(np.abs(a).max() * np.abs(b).max())
     assert abs(Fraction(res) - exact) <= 4 * K * 2.0 ** -55 * scale + abs(float(exact)) * 2.0 ** -52
+
+
+# The 28-bit plans of the split mixed mode's fitting net ((beta, S) = (7, 4)
+# for K = 240, (6, 5) for K <= 2,048): the same exactness of every group sum
+# and of the combination, and a dot product within the expansions' precision.
+REDUCED = [(7, 4), (6, 5)]
+
+
+@pytest.mark.parametrize("beta,S", REDUCED)
+def test_reduced_plans_are_exact_to_their_precision(beta, S):
+    assert beta * S >= 28
+    assert k_max(beta, S) >= (240 if beta == 7 else 2048)
+    assert worst_group_bound(beta, S) == (S + 2) * 4 ** (beta - 1)
+    H = (S + 1) // 2
+    for n in (H, S - H):
+        assert 2 ** 24 * sum(2 ** (beta * j) for j in range(n)) < 2 ** 53
+    rng = np.random.default_rng(11 * beta + S)
+    K = 240 if beta == 7 else 2048
+    a = rng.standard_normal(K) * np.exp(rng.uniform(-3, 3, K))
+    b = rng.standard_normal(K) * 1e-3
+    A, ea = split(a, beta, S)
+    B, eb = split(b, beta, S)
+    C = {}
+    for g in range(2, S + 2):
+        terms = np.concatenate([A[s - 1] * B[g - s - 1] for s in range(1, g) if 1 <= g - s <= S])
+        acc32 = np.add.accumulate(terms.astype(np.float32), dtype=np.float32)
+        acc64 = np.add.accumulate(terms.astype(np.int64))
+        np.testing.assert_array_equal(acc32.astype(np.int64), acc64)
+        C[g] = int(acc64[-1])
+    y = 0
+    for g in range(2, S + 2):
+        y = y * 2 ** beta + C[g]
+    res = float(Fraction(y) * Fraction(2) ** (ea + eb - beta * (S + 1)))
+    exact = sum(Fraction(float(p)) * Fraction(float(q)) for p, q in zip(a, b))
+    scale = float(np.abs(a).max() * np.abs(b).max())
+    # truncation of the operands to beta S bits plus the dropped groups g > S + 1
+    assert abs(Fraction(res) - exact) <= 4 * K * 2.0 ** -(beta * S) * scale

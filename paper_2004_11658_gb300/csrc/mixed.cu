@@ -13,6 +13,13 @@
 // one type; layer 1 streams the descriptor (converted to BF16) and the weight
 // K-chunks through double-buffered shared memory.
 //
+// Split operands (DP_PREC_MIXED_SPLIT, template flag SPLIT of the embedding
+// kernels): every FP32 row operand and weight is stored as a BF16 high part
+// and the BF16 value of its remainder, and each K-slice issues hi*hi + hi*lo +
+// lo*hi into the same FP32 accumulator (~16 bits per operand instead of 8);
+// the operand buffers double, so these kernels run one CTA per SM.  That mode
+// runs its fitting net on fit_oz.cu's exact digit kernels, not on k_fit_mx.
+//
 // Supported shapes: embedding widths (e1, 2 e1, 4 e1) with e1 in {16, 25, 32}
 // (the paper's doubling nets), fitting layers of equal width <= 256 after the
 // first one.  Every wait on the tensor core is bounded; on a timeout the

@@ -360,3 +360,22 @@ def test_set_params_refreshes_fp64_contexts(dp, oracle, synth):
     g = dp.dp_eval(ctx, x, t, w["box"])
     o2 = oracle.evaluate(d, P2, w["coords"], w["types"], w["box"])
     assert max(rel_errors(g, o2)) < TOL
+
+
+def test_model_from_seed_matches_oracle(dp, oracle, synth):
+    """A model made in the library from a seed (dp_model_from_seed) is the
+    input module's seeded model: parameters equal value for value on this
+    machine's libm, and the evaluation matches the oracle's on those weights."""
+    w = system(synth, "water648")
+    d = w["model"]
+    P = synth.model_params(d, 7)
+    np.testing.assert_array_equal(dp.dp_model_params_from_seed(d, 7), P)
+    o = oracle.evaluate(d, P, w["coords"], w["types"], w["box"])
+    model = dp.Model.from_seed(d, 7)
+    ctx = dp.Context(model, len(w["coords"]))
+    x = torch.tensor(w["coords"], dtype=torch.float64, device="cuda")
+    t = torch.tensor(w["types"], dtype=torch.int32, device="cuda")
+    dp.dp_build_nlist(ctx, x, t, w["box"], 0.0)
+    g = dp.dp_eval(ctx, x, t, w["box"])
+    eE, eF, eV = rel_errors(g, o)
+    assert eE < TOL and eF < TOL and eV < TOL, (eE, eF, eV)

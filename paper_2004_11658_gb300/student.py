@@ -24,7 +24,7 @@ from . import dp, synth
 def generate_frames(teacher_desc, teacher_params, workload, n_traj=20, frames_per_traj=50, stride=2,
                     T0=300.0, dt=0.5, seed0=100, device="cuda"):
     """Frames from n_traj teacher trajectories (different Maxwell seeds), one
-    frame every `stride` MD steps (20 x 50 frames at stride 3: twenty 150-step
+    frame every `stride` MD steps (20 x 50 frames at stride 2: twenty 100-step
     NVE runs of the starting configuration), labelled by the FP64 teacher.
     Returns dict(coords [F,N,3], energy [F], force [F,N,3]) on the device."""
     w = workload
@@ -270,10 +270,10 @@ def main(argv=None):
     import os
     ap = argparse.ArgumentParser(description=main.__doc__)
     ap.add_argument("--out", required=True, help="parameter file (.npy); the summary goes to <out>.json")
-    ap.add_argument("--minutes", type=float, default=15.0, help="training wall time")
+    ap.add_argument("--minutes", type=float, default=40.0, help="training wall time")
     ap.add_argument("--trajectories", type=int, default=20)
     ap.add_argument("--frames", type=int, default=50, help="frames per trajectory")
-    ap.add_argument("--stride", type=int, default=3, help="MD steps between frames")
+    ap.add_argument("--stride", type=int, default=2, help="MD steps between frames")
     ap.add_argument("--seed", type=int, default=7)
     a = ap.parse_args(argv)
     w = synth.workload("water12288")

@@ -115,6 +115,54 @@ __device__ __forceinline__ void combine_groups8(uint32_t taddr, double (&y)[8])
     for (int q = 0; q < 8; ++q) y[q] = fma((double)hi[q], 4294967296.0, (double)lo[q]);
 }
 
+// The backward kernel runs 16 warps (four per SM sub-partition, to hide the
+// latency of its dependent FP64 chains): in its epilogues each thread owns 8
+// rows of the last layer's accumulator (32x32b layout) and 4 rows of each
+// lane-half of layer 1's M = 64 accumulator.
+constexpr int XTB = 512;                   // threads of the backward kernel
+constexpr int XRB = XNR * 4 / (XTB / 32);  // rows per thread in the last layer's epilogue (8)
+constexpr int XQB = XRB / 2;               // rows per thread per lane-half in layer 1's epilogue (4)
+
+__device__ __forceinline__ void combine_groups_8(uint32_t taddr, double (&y)[8])
+{
+    long long hi[8], lo[8];
+#pragma unroll
+    for (int g = 2; g <= XS + 1; ++g) {
+        float v[8];
+        tc::tmem_ld8(taddr + (uint32_t)(g - 2) * XNR, v);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const long long iv = (long long)__float2int_rn(v[q]);
+            if (g == 2) hi[q] = iv;
+            else if (g <= 4) hi[q] = (hi[q] << XBETA) + iv;
+            else if (g == 5) lo[q] = iv;
+            else lo[q] = (lo[q] << XBETA) + iv;
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) y[q] = fma((double)hi[q], 4294967296.0, (double)lo[q]);
+}
+
+__device__ __forceinline__ void combine_groups4(uint32_t taddr, double (&y)[4])
+{
+    long long hi[4], lo[4];
+#pragma unroll
+    for (int g = 2; g <= XS + 1; ++g) {
+        float v[4];
+        tc::tmem_ld16x2_4<16>(taddr + (uint32_t)(g - 2) * XNR, v);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const long long iv = (long long)__float2int_rn(v[q]);
+            if (g == 2) hi[q] = iv;
+            else if (g <= 4) hi[q] = (hi[q] << XBETA) + iv;
+            else if (g == 5) lo[q] = iv;
+            else lo[q] = (lo[q] << XBETA) + iv;
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) y[q] = fma((double)hi[q], 4294967296.0, (double)lo[q]);
+}
+
 template <int E1>
 struct XShape {
     static constexpr int E2 = 2 * E1, E3 = 4 * E1, K2p = k2p_of(E1), K1p = k1p_of(E1);
@@ -504,20 +552,20 @@ struct XBShape {
     // buffer), H1, dH1 (aliased by gT [4][XM] in each atom's prologue), geometry [GR][GS]
     // (10 values, odd stride)
     static constexpr size_t H0SZ = (size_t)2 * XNR * LD0;
-    static constexpr size_t RED = (size_t)8 * 16 * 8;
+    static constexpr size_t RED = (size_t)(XTB / 32) * XRB * 8;
     static constexpr size_t F64 = (L1 ? 0 : (size_t)E1 * E2) + 2 * E1 + E2 + XM + (H0SZ > RED ? H0SZ : RED) +
                                   2 * XNR * LD1 + GR * GS;
     static_assert(4 * XM <= XNR * LD1 && 4 * E3 <= XNR * LD1, "T and gT fit in the h1 and dh1 rows");
     // + two [XNR] int32 row exponents (layer 2's and layer 1's tangent rows)
     static constexpr size_t SMEM = WD + BD + F64 * 8 + 2 * XNR * 4;
-    static_assert(GR % XNR == 0 && GR <= XT, "geometry is staged one row per thread, whole chunks at a time");
+    static_assert(GR % XNR == 0 && GR <= XTB, "geometry is staged one row per thread, whole chunks at a time");
     static_assert(!L1 || (2 * XS * XNR * K1p * 2 <= BD && E2 <= XM1),
                   "layer 1's value and tangent digits share the row-digit buffer");
     static_assert(SMEM + 1024 <= 232448, "dynamic plus static shared memory above the 227 KB opt-in limit");
 };
 
 template <int E1>
-__global__ void __launch_bounds__(XT, 1) k_embed_bwd_x(DevModel m, const unsigned char *__restrict__ wx,
+__global__ void __launch_bounds__(XTB, 1) k_embed_bwd_x(DevModel m, const unsigned char *__restrict__ wx,
                                                        const double *__restrict__ x,
                                                        const int32_t *__restrict__ types, Box3 box, int N,
                                                        const int32_t *__restrict__ type_perm,
@@ -544,7 +592,7 @@ __global__ void __launch_bounds__(XT, 1) k_embed_bwd_x(DevModel m, const unsigne
     double *b2s = b1s + E2;
     double *H0 = b2s + XM;
     double *dH0 = H0 + XNR * LD0;
-    double *red = H0;  // [8 warps][16 rows][8], used after layer 1 (aliases H0, dH0)
+    double *red = H0;  // [16 warps][8 rows][8], used after layer 1 (aliases H0, dH0)
     double *H1 = H0 + (X::H0SZ > X::RED ? X::H0SZ : X::RED);
     double *dH1 = H1 + XNR * LD1;
     double *geo = dH1 + XNR * LD1;  // [GR][GS]: s, ds, R[4], d[3], r
@@ -573,7 +621,7 @@ __global__ void __launch_bounds__(XT, 1) k_embed_bwd_x(DevModel m, const unsigne
     bool alive = true, pend_w = false, pend_m = false;
     int staged = -1;
     const int f = tid & (XM - 1);
-    const int half = tid >> 7;
+    const int grp = tid >> 7;  // last layer: rows XRB grp .. XRB grp + XRB - 1
 
     // z^T = W2^T digits x (row digits in Bd) into 7 groups at column base col0
     auto mma_rows = [&](uint32_t col0) -> bool {
@@ -603,7 +651,7 @@ __global__ void __launch_bounds__(XT, 1) k_embed_bwd_x(DevModel m, const unsigne
     };
     // digits of the 32 x E2 rows of src (row scale 2^(56 - e_r), e_r from erow or fixed)
     auto make_digits = [&](const double *src, bool fixed) {
-        for (int p = tid; p < XNR * (K2p / 8); p += XT) {
+        for (int p = tid; p < XNR * (K2p / 8); p += XTB) {
             const int row = p % XNR, k0 = (p / XNR) * 8;  // lanes on consecutive rows
             const double sc = oz_pow2(XBETA * XS - (fixed ? 1 : erow[row]));
             long long I[8];
@@ -631,7 +679,7 @@ __global__ void __launch_bounds__(XT, 1) k_embed_bwd_x(DevModel m, const unsigne
     // (row scale 2^(56 - erow0)) after them
     auto make_digits1 = [&]() {
         constexpr int NP = XNR * (K1p / 8);
-        for (int p = tid; p < 2 * NP; p += XT) {
+        for (int p = tid; p < 2 * NP; p += XTB) {
             const int which = p / NP, pp = p - which * NP;
             const int row = pp % XNR, k0 = (pp / XNR) * 8;
             const double *src = which ? dH0 : H0;
@@ -698,10 +746,10 @@ __global__ void __launch_bounds__(XT, 1) k_embed_bwd_x(DevModel m, const unsigne
         // gT[c][x] = scale ([x < M2] sum_b gD[x][b] T[c][b] + sum_{a<M2} gD[a][x] T[c][a])
         {
             double *Ts = H1;  // T of this atom, [4][E3]
-            for (int p = tid; p < 4 * E3; p += XT) Ts[p] = Tin[(size_t)i * 4 * E3 + p];
+            for (int p = tid; p < 4 * E3; p += XTB) Ts[p] = Tin[(size_t)i * 4 * E3 + p];
             __syncthreads();
             const double *g = gD + (size_t)i * m2 * E3;
-            for (int p = tid; p < 4 * E3; p += XT) {
+            for (int p = tid; p < 4 * E3; p += XTB) {
                 const int cc = p / E3, xx = p - cc * E3;
                 double acc = 0.0;
                 if (xx < m2)
@@ -730,14 +778,14 @@ __global__ void __launch_bounds__(XT, 1) k_embed_bwd_x(DevModel m, const unsigne
                     bulk_g2s_x(Wd, wx + (size_t)net * X::NB, (uint32_t)X::WD, &mbar_w);
                 }
                 const double *src = m.params + m.emb_base[net];
-                for (int q = tid; q < E1; q += XT) {
+                for (int q = tid; q < E1; q += XTB) {
                     w0s[q] = src[q];
                     b0s[q] = src[E1 + q];
                 }
                 if constexpr (!L1)
-                    for (int q = tid; q < E1 * E2; q += XT) W1s[q] = src[2 * E1 + q];
-                for (int q = tid; q < E2; q += XT) b1s[q] = src[2 * E1 + E1 * E2 + q];
-                for (int q = tid; q < XM; q += XT)
+                    for (int q = tid; q < E1 * E2; q += XTB) W1s[q] = src[2 * E1 + q];
+                for (int q = tid; q < E2; q += XTB) b1s[q] = src[2 * E1 + E1 * E2 + q];
+                for (int q = tid; q < XM; q += XTB)
                     b2s[q] = q < E3 ? src[2 * E1 + E1 * E2 + E2 + E2 * E3 + q] : 0.0;
                 const bool ok = tc::mbar_wait(&mbar_w, ph_w);
                 ph_w ^= 1u;
@@ -754,7 +802,7 @@ __global__ void __launch_bounds__(XT, 1) k_embed_bwd_x(DevModel m, const unsigne
                 const int nv = min(XNR, nb - c0);
                 if (c0 % GR == 0) {
                     __syncthreads();
-                    for (int q = tid; q < GR; q += XT) {
+                    for (int q = tid; q < GR; q += XTB) {
                         const int r = c0 + q;
                         double *gq = geo + q * GS;
                         double s = 0.0, ds = 0.0, d[3] = {0.0, 0.0, 0.0}, rr = 1.0;
@@ -782,7 +830,7 @@ __global__ void __launch_bounds__(XT, 1) k_embed_bwd_x(DevModel m, const unsigne
                 // layer 0 and its tangent
                 {
                     const double sv = gc[lane * GS];
-                    for (int o = warp; o < E1; o += XT / 32) {
+                    for (int o = warp; o < E1; o += XTB / 32) {
                         const double w0 = w0s[o];
                         const double t = dp_tanh64(fma(sv, w0, b0s[o]), m.tanh_tab);
                         H0[lane * LD0 + o] = t;
@@ -817,20 +865,20 @@ __global__ void __launch_bounds__(XT, 1) k_embed_bwd_x(DevModel m, const unsigne
                     }
                     // epilogue: the warp's TMEM quarter holds features 16 (warp % 4) .. + 15 in
                     // its first 16 lanes; lanes < 16 take rows 0..15, the others rows 16..31,
-                    // and warps w, w + 4 take 8 of them each
+                    // and warps w, w + 4, w + 8, w + 12 take 4 of them each
                     const int f1 = 16 * (warp & 3) + (lane & 15);
-                    const int r0 = 16 * (lane >> 4) + 8 * (warp >> 2);
-                    const uint32_t ta = tlane + 8 * (uint32_t)(warp >> 2);
-                    double y1[8], dy1[8];
-                    combine_groups8(ta, y1);
-                    combine_groups8(ta + 256, dy1);
+                    const int r0 = 16 * (lane >> 4) + XQB * (warp >> 2);
+                    const uint32_t ta = tlane + XQB * (uint32_t)(warp >> 2);
+                    double y1[XQB], dy1[XQB];
+                    combine_groups4(ta, y1);
+                    combine_groups4(ta + 256, dy1);
                     if (f1 < E2) {
                         const int fx1 = fexp1[f1];
                         const double cv1 = oz_pow2(1 + fx1 - XBETA * (XS + 1));
                         const double bb = b1s[f1];
                         const int os = f1 < E1 ? f1 : f1 - E1;
 #pragma unroll
-                        for (int j = 0; j < 8; ++j) {
+                        for (int j = 0; j < XQB; ++j) {
                             const int row = r0 + j;
                             const double t = dp_tanh64(fma(y1[j], cv1, bb), m.tanh_tab);
                             const double dz = dy1[j] * oz_pow2(erow0[row] + fx1 - XBETA * (XS + 1));
@@ -841,7 +889,7 @@ __global__ void __launch_bounds__(XT, 1) k_embed_bwd_x(DevModel m, const unsigne
                     tc::fence_before_sync();
                 } else {
                     const double *hr = H0 + lane * LD0, *dhr = dH0 + lane * LD0;
-                    for (int o = warp; o < E2; o += XT / 32) {
+                    for (int o = warp; o < E2; o += XTB / 32) {
                         double z = b1s[o], dz = 0.0;
 #pragma unroll 5
                         for (int q = 0; q < E1; ++q) {
@@ -885,23 +933,23 @@ __global__ void __launch_bounds__(XT, 1) k_embed_bwd_x(DevModel m, const unsigne
                     alive = false;
                     break;
                 }
-                // epilogue: feature f of rows 16 half .. 16 half + 15
-                double yv[16], yt[16];
-                combine_groups(tlane + 16 * half, yv);
-                combine_groups(tlane + 256 + 16 * half, yt);
+                // epilogue: feature f of rows XRB grp .. XRB grp + XRB - 1
+                double yv[XRB], yt[XRB];
+                combine_groups_8(tlane + XRB * grp, yv);
+                combine_groups_8(tlane + 256 + XRB * grp, yt);
                 const double cv = oz_pow2(1 + fx - XBETA * (XS + 1));
                 const double bf = f < E3 ? b2s[f] : 0.0;
                 const int fs = f < E2 ? f : (f < E3 ? f - E2 : 0);
-                double *rw = red + (warp * 16) * 8;  // this warp's [16 rows][8]
+                double *rw = red + (warp * XRB) * 8;  // this warp's [XRB rows][8]
                 // partials p[r][c] = G gT[c] (c < 4), dG gT[c - 4] for 4 rows at a time, summed over
                 // the warp's 32 features by a transposing shuffle tree (31 adds per lane): lane L ends
                 // with the sum of row L / 8, component L % 8
 #pragma unroll 1
-                for (int q4 = 0; q4 < 16; q4 += 4) {
+                for (int q4 = 0; q4 < XRB; q4 += 4) {
                     double p[32];
 #pragma unroll
                     for (int r4 = 0; r4 < 4; ++r4) {
-                        const int qq = q4 + r4, q = 16 * half + qq;
+                        const int qq = q4 + r4, q = XRB * grp + qq;
                         double G = 0.0, dG = 0.0;
                         if (q < nv && f < E3) {
                             const double t = dp_tanh64(fma(yv[qq], cv, bf), m.tanh_tab);
@@ -930,13 +978,13 @@ __global__ void __launch_bounds__(XT, 1) k_embed_bwd_x(DevModel m, const unsigne
                 __syncthreads();
                 // chain rule through R~(r_ij), one lane per row (warp 0)
                 if (warp == 0 && lane < nv) {
-                    const int q = lane, hq = q >> 4, qq = q & 15;
+                    const int q = lane, hq = q / XRB, qq = q % XRB;
                     double sa[8];
 #pragma unroll
                     for (int c = 0; c < 8; ++c) sa[c] = 0.0;
                     for (int w = 4 * hq; w < 4 * hq + 4; ++w)
 #pragma unroll
-                        for (int c = 0; c < 8; ++c) sa[c] += red[(w * 16 + qq) * 8 + c];
+                        for (int c = 0; c < 8; ++c) sa[c] += red[(w * XRB + qq) * 8 + c];
                     const double *gq = gc + q * GS;
                     const double gs = gq[0], gds = gq[1], gd[3] = {gq[6], gq[7], gq[8]}, gr = gq[9];
                     double gR0 = sa[0];
@@ -1007,7 +1055,7 @@ cudaError_t launch_bwd_x(cudaStream_t st, const DevModel &m, const unsigned char
     int grid = num_sms;
     if (grid > N) grid = N;
     if (grid < 1) grid = 1;
-    k_embed_bwd_x<E1><<<grid, XT, X::SMEM, st>>>(m, wx, x, types, box, N, nb.type_perm, fb.nlist, fb.nreal, eb.T,
+    k_embed_bwd_x<E1><<<grid, XTB, X::SMEM, st>>>(m, wx, x, types, box, N, nb.type_perm, fb.nlist, fb.nreal, eb.T,
                                                  eb.gD, eb.pair_g, eb.f_own, eb.vir_part, status);
     return cudaGetLastError();
 }

@@ -127,6 +127,21 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
     for (int q = 0; q < 16; ++q) v[q] = __uint_as_float(r[q]);
 }
 
+// 32 lanes x 8 consecutive 32-bit columns (as tmem_ld16, half the columns).
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8])
+{
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7])
+                 :
+                 : "memory");
+#pragma unroll
+    for (int q = 0; q < 8; ++q) v[q] = __uint_as_float(r[q]);
+}
+
 // The accumulator of an M = 64 MMA (cta_group::1) holds row m in lane
 // 32 (m / 16) + m % 16: the first 16 lanes of each warp's quarter.  This load
 // reads those 16 lanes twice: thread t < 16 gets lane (taddr's lane + t),
@@ -145,6 +160,19 @@ __device__ __forceinline__ void tmem_ld16x2_8(uint32_t taddr, float (&v)[8])
                  : "memory");
 #pragma unroll
     for (int q = 0; q < 8; ++q) v[q] = __uint_as_float(r[q]);
+}
+
+// tmem_ld16x2_8 with 4 columns per thread.
+template <int OFF>
+__device__ __forceinline__ void tmem_ld16x2_4(uint32_t taddr, float (&v)[4])
+{
+    uint32_t r[4];
+    asm volatile("tcgen05.ld.sync.aligned.16x32bx2.x4.b32 {%0,%1,%2,%3}, [%4], %5;\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(taddr), "n"(OFF));
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n" : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]) : : "memory");
+#pragma unroll
+    for (int q = 0; q < 4; ++q) v[q] = __uint_as_float(r[q]);
 }
 
 }  // namespace tc

@@ -35,7 +35,6 @@ constexpr int XS = 7;        // digits
 constexpr int XBETA = 8;     // digit width (bits)
 constexpr int XNR = 32;      // neighbour rows per MMA (N)
 constexpr int XM = 128;      // output features per MMA (M), 4 e1 <= 128
-constexpr int XT = 256;      // threads: 8 warps; in the epilogue warps w and w + 4 share TMEM lanes 32 (w % 4) ..
 constexpr int XGR = 512;     // rows of one neighbour block whose geometry is staged at once
 
 constexpr int XM1 = 64;      // output features of the layer-1 MMA (M), 2 e1 <= 64
@@ -68,63 +67,22 @@ __device__ __forceinline__ void mbar_expect_tx_x(uint64_t *mbar, uint32_t bytes)
                  : "memory");
 }
 
-// y[q] = sum_{g=2}^{8} C_g[q] 2^(8 (8 - g)) for the 16 columns at taddr (group g
-// at column offset (g - 2) * XNR): the group sums are integers below 2^24, so
-// they are combined exactly in two int64 Horner chains (g = 2..4 and g = 5..8,
-// below 2^41 and 2^49) and converted once: y = hi 2^32 + lo, one rounding.
-__device__ __forceinline__ void combine_groups(uint32_t taddr, double (&y)[16])
-{
-    static_assert(XS == 7 && XBETA == 8, "combine_groups assumes 7 digits of 8 bits");
-    long long hi[16], lo[16];
-#pragma unroll
-    for (int g = 2; g <= XS + 1; ++g) {
-        float v[16];
-        tc::tmem_ld16(taddr + (uint32_t)(g - 2) * XNR, v);
-#pragma unroll
-        for (int q = 0; q < 16; ++q) {
-            const long long iv = (long long)__float2int_rn(v[q]);
-            if (g == 2) hi[q] = iv;
-            else if (g <= 4) hi[q] = (hi[q] << XBETA) + iv;
-            else if (g == 5) lo[q] = iv;
-            else lo[q] = (lo[q] << XBETA) + iv;
-        }
-    }
-#pragma unroll
-    for (int q = 0; q < 16; ++q) y[q] = fma((double)hi[q], 4294967296.0, (double)lo[q]);
-}
-
-// combine_groups for an M = 64 accumulator: the 8 columns that tc::tmem_ld16x2_8
-// (second half 16 columns on) gives this thread.
-__device__ __forceinline__ void combine_groups8(uint32_t taddr, double (&y)[8])
-{
-    long long hi[8], lo[8];
-#pragma unroll
-    for (int g = 2; g <= XS + 1; ++g) {
-        float v[8];
-        tc::tmem_ld16x2_8<16>(taddr + (uint32_t)(g - 2) * XNR, v);
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const long long iv = (long long)__float2int_rn(v[q]);
-            if (g == 2) hi[q] = iv;
-            else if (g <= 4) hi[q] = (hi[q] << XBETA) + iv;
-            else if (g == 5) lo[q] = iv;
-            else lo[q] = (lo[q] << XBETA) + iv;
-        }
-    }
-#pragma unroll
-    for (int q = 0; q < 8; ++q) y[q] = fma((double)hi[q], 4294967296.0, (double)lo[q]);
-}
-
-// The backward kernel runs 16 warps (four per SM sub-partition, to hide the
-// latency of its dependent FP64 chains): in its epilogues each thread owns 8
+// Both embedding kernels run 16 warps (four per SM sub-partition, to hide the
+// latency of their dependent FP64 chains).  In the epilogues warps w, w + 4,
+// w + 8 and w + 12 share TMEM lanes 32 (w % 4) .. + 31: each thread owns 8
 // rows of the last layer's accumulator (32x32b layout) and 4 rows of each
 // lane-half of layer 1's M = 64 accumulator.
-constexpr int XTB = 512;                   // threads of the backward kernel
+constexpr int XTB = 512;                   // threads of the embedding kernels
 constexpr int XRB = XNR * 4 / (XTB / 32);  // rows per thread in the last layer's epilogue (8)
 constexpr int XQB = XRB / 2;               // rows per thread per lane-half in layer 1's epilogue (4)
 
+// y[q] = sum_{g=2}^{8} C_g[q] 2^(8 (8 - g)) for the 8 columns at taddr (group g
+// at column offset (g - 2) * XNR): the group sums are integers below 2^24, so
+// they are combined exactly in two int64 Horner chains (g = 2..4 and g = 5..8,
+// below 2^41 and 2^49) and converted once: y = hi 2^32 + lo, one rounding.
 __device__ __forceinline__ void combine_groups_8(uint32_t taddr, double (&y)[8])
 {
+    static_assert(XS == 7 && XBETA == 8, "combine_groups_8 assumes 7 digits of 8 bits");
     long long hi[8], lo[8];
 #pragma unroll
     for (int g = 2; g <= XS + 1; ++g) {
@@ -143,6 +101,8 @@ __device__ __forceinline__ void combine_groups_8(uint32_t taddr, double (&y)[8])
     for (int q = 0; q < 8; ++q) y[q] = fma((double)hi[q], 4294967296.0, (double)lo[q]);
 }
 
+// combine_groups_8 for an M = 64 accumulator: the 4 columns that
+// tc::tmem_ld16x2_4 (second half 16 columns on) gives this thread.
 __device__ __forceinline__ void combine_groups4(uint32_t taddr, double (&y)[4])
 {
     long long hi[4], lo[4];
@@ -173,16 +133,18 @@ struct XShape {
     static constexpr size_t NB = net_bytes(E1);              // stride of the nets' weight blocks
     static constexpr size_t BD = (size_t)XS * XNR * K2p * 2;  // row digits
     // FP64 region: W1 (E1 x E2, SIMT layer 1 only), w0, b0 (E1), b1 (E2), b2 (XM), H0, H1,
-    // Rt (XGR x 4), srow (XGR), Tsm (2 x 4 x XM)
+    // Rt (XGR x 4), srow (XGR); after an atom's last chunk the geometry rows hold Tsm
+    // ([XTB / XM] x 4 x XM: one T partial per row group)
     static constexpr size_t F64 =
-        (L1 ? 0 : (size_t)E1 * E2) + 2 * E1 + E2 + XM + XNR * LD0 + XNR * LD1 + XGR * 4 + XGR + 8 * XM;
+        (L1 ? 0 : (size_t)E1 * E2) + 2 * E1 + E2 + XM + XNR * LD0 + XNR * LD1 + XGR * 4 + XGR;
+    static_assert((XTB / XM) * 4 * XM <= XGR * 5, "the T partials fit in the geometry rows");
     static constexpr size_t SMEM = WD + BD + F64 * 8;
     static_assert(!L1 || (XS * XNR * K1p * 2 <= BD && E2 <= XM1), "layer 1's digits use the row-digit buffer");
     static_assert(SMEM + 1024 <= 232448, "dynamic plus static shared memory above the 227 KB opt-in limit");
 };
 
 template <int E1>
-__global__ void __launch_bounds__(XT, 1) k_embed_fwd_x(DevModel m, const unsigned char *__restrict__ wx,
+__global__ void __launch_bounds__(XTB, 1) k_embed_fwd_x(DevModel m, const unsigned char *__restrict__ wx,
                                                        const double *__restrict__ x,
                                                        const int32_t *__restrict__ types, Box3 box, int N,
                                                        const int32_t *__restrict__ type_perm,
@@ -208,7 +170,7 @@ __global__ void __launch_bounds__(XT, 1) k_embed_fwd_x(DevModel m, const unsigne
     double *H1 = H0 + XNR * LD0;
     double *Rga = H1 + XNR * LD1;   // environment rows of the block [XGR][4]
     double *sga = Rga + XGR * 4;    // s of the block [XGR]
-    double *Tsm = sga + XGR;        // [2][4][XM]
+    double *Tsm = Rga;              // [XTB / XM][4][XM], once the atom's chunks are done
     __shared__ __align__(8) uint64_t mbar_w, mbar_m;
     __shared__ uint32_t tslot;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -230,7 +192,7 @@ __global__ void __launch_bounds__(XT, 1) k_embed_fwd_x(DevModel m, const unsigne
     bool pend_w = false, pend_m = false;  // a copy or MMAs still in flight after a timeout
     int staged = -1;
     const int f = tid & (XM - 1);  // epilogue: this thread's output feature
-    const int half = tid >> 7;     // ... and half of the chunk's rows
+    const int grp = tid >> 7;      // ... and rows XRB grp .. XRB grp + XRB - 1 of the chunk
 
     for (int ii = blockIdx.x; ii < N && alive; ii += gridDim.x) {
         const int i = type_perm[ii];
@@ -249,14 +211,14 @@ __global__ void __launch_bounds__(XT, 1) k_embed_fwd_x(DevModel m, const unsigne
                     bulk_g2s_x(Wd, wx + (size_t)net * X::NB, (uint32_t)X::WD, &mbar_w);
                 }
                 const double *src = m.params + m.emb_base[net];
-                for (int q = tid; q < E1; q += XT) {
+                for (int q = tid; q < E1; q += XTB) {
                     w0s[q] = src[q];
                     b0s[q] = src[E1 + q];
                 }
                 if constexpr (!L1)
-                    for (int q = tid; q < E1 * E2; q += XT) W1s[q] = src[2 * E1 + q];
-                for (int q = tid; q < E2; q += XT) b1s[q] = src[2 * E1 + E1 * E2 + q];
-                for (int q = tid; q < XM; q += XT)
+                    for (int q = tid; q < E1 * E2; q += XTB) W1s[q] = src[2 * E1 + q];
+                for (int q = tid; q < E2; q += XTB) b1s[q] = src[2 * E1 + E1 * E2 + q];
+                for (int q = tid; q < XM; q += XTB)
                     b2s[q] = q < E3 ? src[2 * E1 + E1 * E2 + E2 + E2 * E3 + q] : 0.0;
                 const bool ok = tc::mbar_wait(&mbar_w, ph_w);
                 ph_w ^= 1u;
@@ -274,7 +236,7 @@ __global__ void __launch_bounds__(XT, 1) k_embed_fwd_x(DevModel m, const unsigne
                 // geometry of the next XGR rows of the block, one row per thread
                 if (c0 % XGR == 0) {
                     __syncthreads();
-                    for (int q = tid; q < XGR; q += XT) {
+                    for (int q = tid; q < XGR; q += XTB) {
                         const int r = c0 + q;
                         double s = 0.0, R[4] = {0.0, 0.0, 0.0, 0.0};
                         if (r < nb) {
@@ -300,13 +262,13 @@ __global__ void __launch_bounds__(XT, 1) k_embed_fwd_x(DevModel m, const unsigne
                 // layer 0: h0 = tanh(s w0 + b0), one row per lane, warps split the columns
                 {
                     const double sv = srow[lane];
-                    for (int o = warp; o < E1; o += XT / 32) H0[lane * LD0 + o] = dp_tanh64(fma(sv, w0s[o], b0s[o]), m.tanh_tab);
+                    for (int o = warp; o < E1; o += XTB / 32) H0[lane * LD0 + o] = dp_tanh64(fma(sv, w0s[o], b0s[o]), m.tanh_tab);
                 }
                 __syncthreads();
                 // layer 1: h1 = (h0, h0) + tanh(h0 W1 + b1)
                 if constexpr (L1) {
                     // digits of h0 (fixed scale: |h0| <= 1), then z1^T (64 features x 32 rows)
-                    for (int p = tid; p < XNR * (K1p / 8); p += XT) {
+                    for (int p = tid; p < XNR * (K1p / 8); p += XTB) {
                         const int row = p % XNR, k0 = (p / XNR) * 8;
                         long long I[8];
 #pragma unroll
@@ -361,17 +323,17 @@ __global__ void __launch_bounds__(XT, 1) k_embed_fwd_x(DevModel m, const unsigne
                     }
                     // epilogue: the warp's TMEM quarter holds features 16 (warp % 4) .. + 15 in
                     // its first 16 lanes; lanes < 16 take rows 0..15, the others rows 16..31,
-                    // and warps w, w + 4 take 8 of them each
+                    // and warps w, w + 4, w + 8, w + 12 take 4 of them each
                     const int f1 = 16 * (warp & 3) + (lane & 15);
-                    const int r0 = 16 * (lane >> 4) + 8 * (warp >> 2);
-                    double y1[8];
-                    combine_groups8(tlane + 8 * (uint32_t)(warp >> 2), y1);
+                    const int r0 = 16 * (lane >> 4) + XQB * (warp >> 2);
+                    double y1[XQB];
+                    combine_groups4(tlane + XQB * (uint32_t)(warp >> 2), y1);
                     if (f1 < E2) {
                         const double cv1 = oz_pow2(1 + fexp1[f1] - XBETA * (XS + 1));
                         const double bb = b1s[f1];
                         const int os = f1 < E1 ? f1 : f1 - E1;
 #pragma unroll
-                        for (int j = 0; j < 8; ++j) {
+                        for (int j = 0; j < XQB; ++j) {
                             const int row = r0 + j;
                             H1[row * LD1 + f1] = H0[row * LD0 + os] + dp_tanh64(fma(y1[j], cv1, bb), m.tanh_tab);
                         }
@@ -379,7 +341,7 @@ __global__ void __launch_bounds__(XT, 1) k_embed_fwd_x(DevModel m, const unsigne
                     tc::fence_before_sync();
                 } else {
                     const double *hr = H0 + lane * LD0;
-                    for (int o = warp; o < E2; o += XT / 32) {
+                    for (int o = warp; o < E2; o += XTB / 32) {
                         double z = b1s[o];
 #pragma unroll 5
                         for (int q = 0; q < E1; ++q) z = fma(hr[q], W1s[q * E2 + o], z);
@@ -388,7 +350,7 @@ __global__ void __launch_bounds__(XT, 1) k_embed_fwd_x(DevModel m, const unsigne
                 }
                 __syncthreads();
                 // digits of h1 (fixed scale: |h1| < 2), 8 columns per thread-iteration
-                for (int p = tid; p < XNR * (K2p / 8); p += XT) {
+                for (int p = tid; p < XNR * (K2p / 8); p += XTB) {
                     const int row = p % XNR, k0 = (p / XNR) * 8;  // lanes on consecutive rows
                     long long I[8];
 #pragma unroll
@@ -444,15 +406,15 @@ __global__ void __launch_bounds__(XT, 1) k_embed_fwd_x(DevModel m, const unsigne
                         break;
                     }
                 }
-                // epilogue: feature f of rows 16 half .. 16 half + 15 of the chunk
-                double y[16];
-                combine_groups(tlane + 16 * half, y);
+                // epilogue: feature f of rows XRB grp .. XRB grp + XRB - 1 of the chunk
+                double y[XRB];
+                combine_groups_8(tlane + XRB * grp, y);
                 if (f < E3) {
                     const double bf = b2s[f];
                     const int fs = f < E2 ? f : f - E2;
 #pragma unroll
-                    for (int qq = 0; qq < 16; ++qq) {
-                        const int q = 16 * half + qq;
+                    for (int qq = 0; qq < XRB; ++qq) {
+                        const int q = XRB * grp + qq;
                         if (q < nv) {
                             const double z = fma(y[qq], cscale, bf);
                             const double G = H1[q * LD1 + fs] + dp_tanh64(z, m.tanh_tab);
@@ -467,23 +429,26 @@ __global__ void __launch_bounds__(XT, 1) k_embed_fwd_x(DevModel m, const unsigne
             }
         }
         if (!alive) break;
-        // T (the two halves' partials summed, scaled) and D = T_<^T T
-        if (half == 1 && f < E3) {
+        // T (the four row groups' partials summed in group order, scaled) and D = T_<^T T
+        if (grp > 0 && f < E3) {
 #pragma unroll
-            for (int c = 0; c < 4; ++c) Tsm[4 * XM + c * E3 + f] = tacc[c];
+            for (int c = 0; c < 4; ++c) Tsm[4 * XM * grp + c * E3 + f] = tacc[c];
         }
         __syncthreads();
-        if (half == 0 && f < E3) {
+        if (grp == 0 && f < E3) {
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
-                const double v = (tacc[c] + Tsm[4 * XM + c * E3 + f]) * m.desc_scale;
+                double v = tacc[c];
+#pragma unroll
+                for (int g = 1; g < XTB / XM; ++g) v += Tsm[4 * XM * g + c * E3 + f];
+                v *= m.desc_scale;
                 Tsm[c * E3 + f] = v;
                 Tout[(size_t)i * 4 * E3 + c * E3 + f] = v;
             }
         }
         __syncthreads();
         const int nd = m.m2 * E3;
-        for (int q = tid; q < nd; q += XT) {
+        for (int q = tid; q < nd; q += XTB) {
             const int a2 = q / E3, b2 = q - a2 * E3;
             double acc = Tsm[a2] * Tsm[b2];
             acc = fma(Tsm[E3 + a2], Tsm[E3 + b2], acc);
@@ -517,7 +482,7 @@ cudaError_t launch_fwd_x(cudaStream_t st, const DevModel &m, const unsigned char
     int grid = num_sms;
     if (grid > N) grid = N;
     if (grid < 1) grid = 1;
-    k_embed_fwd_x<E1><<<grid, XT, X::SMEM, st>>>(m, wx, x, types, box, N, nb.type_perm, fb.nlist, fb.nreal, eb.T,
+    k_embed_fwd_x<E1><<<grid, XTB, X::SMEM, st>>>(m, wx, x, types, box, N, nb.type_perm, fb.nlist, fb.nreal, eb.T,
                                                  eb.D, status);
     return cudaGetLastError();
 }

@@ -145,24 +145,8 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8])
 // The accumulator of an M = 64 MMA (cta_group::1) holds row m in lane
 // 32 (m / 16) + m % 16: the first 16 lanes of each warp's quarter.  This load
 // reads those 16 lanes twice: thread t < 16 gets lane (taddr's lane + t),
-// columns col .. col+7; thread t >= 16 gets lane (taddr's lane + t - 16),
-// columns col + OFF .. col + OFF + 7.
-template <int OFF>
-__device__ __forceinline__ void tmem_ld16x2_8(uint32_t taddr, float (&v)[8])
-{
-    uint32_t r[8];
-    asm volatile("tcgen05.ld.sync.aligned.16x32bx2.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8], %9;\n"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
-                 : "r"(taddr), "n"(OFF));
-    asm volatile("tcgen05.wait::ld.sync.aligned;\n"
-                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7])
-                 :
-                 : "memory");
-#pragma unroll
-    for (int q = 0; q < 8; ++q) v[q] = __uint_as_float(r[q]);
-}
-
-// tmem_ld16x2_8 with 4 columns per thread.
+// columns col .. col+3; thread t >= 16 gets lane (taddr's lane + t - 16),
+// columns col + OFF .. col + OFF + 3.
 template <int OFF>
 __device__ __forceinline__ void tmem_ld16x2_4(uint32_t taddr, float (&v)[4])
 {

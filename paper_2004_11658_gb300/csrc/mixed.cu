@@ -96,6 +96,34 @@ __device__ __forceinline__ void mma_op(uint32_t d, uint32_t a, uint32_t abytes, 
     }
 }
 
+// Double-float arithmetic for the FP64 contractions (T = R~^T G and the
+// backward products with gT): a sum S = sh + sl of two FP32 numbers gathers
+// a (bh + bl), a an FP32 value (G, dG/ds) and bh + bl an FP64 value split into
+// two FP32 parts.  a bh is formed exactly as p + e (e by FMA), p joins sh by
+// an error-free two-sum, and the sum's rounding error, e and a bl go to sl;
+// the result is within about 2^-46 of the sum of the products, relative to
+// the sum of their magnitudes.  Every step is an _rn intrinsic, so no
+// multiply-add contraction can change the error-free transformations.
+__device__ __forceinline__ void df_fma(float &sh, float &sl, float a, float bh, float bl)
+{
+    const float p = __fmul_rn(a, bh);
+    const float e = __fmaf_rn(a, bh, -p);
+    const float s = __fadd_rn(sh, p);
+    const float z = __fsub_rn(s, sh);
+    const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(s, z)), __fsub_rn(p, z));
+    sh = s;
+    sl = __fadd_rn(sl, __fadd_rn(err, __fmaf_rn(a, bl, e)));
+}
+
+// v = h + l to about 2^-48 relative (h = v rounded to FP32, l = the rest rounded)
+__device__ __forceinline__ void df_split(double v, float &h, float &l)
+{
+    h = __double2float_rn(v);
+    l = __double2float_rn(v - (double)h);
+}
+
+__device__ __forceinline__ double df_value(float h, float l) { return (double)h + (double)l; }
+
 __device__ __forceinline__ void copy16(unsigned char *dst, const unsigned char *__restrict__ src, int bytes)
 {
     for (int q = threadIdx.x * 16; q < bytes; q += blockDim.x * 16)
@@ -210,10 +238,11 @@ __global__ void __launch_bounds__(MXT, 1) k_embed_fwd_mx(
     unsigned char *A1 = A0 + X * S::A0B;
     unsigned char *B1 = A1 + X * S::A1B;
     unsigned char *B2 = B1 + X * S::B1B;
-    double *Gt = reinterpret_cast<double *>(B2 + X * S::B2B);  // [4][32][17]
-    double *Rt = Gt + 4 * 32 * 17;                          // [4][32][4]
-    double *Tw = Rt + 4 * 32 * 4;                           // [4][4][E3] per-warp partial of one tile
+    double *Tw = reinterpret_cast<double *>(B2 + X * S::B2B);  // [4][4][E3] per-warp partial of one tile
     double *Tacc = Tw + 4 * 4 * E3;                         // [AB][4][E3] per-atom sums
+    float *Gt = reinterpret_cast<float *>(Tacc + AB * 4 * E3);  // [4][32][17]
+    float *Rth = Gt + 4 * 32 * 17;                          // [4][32][4]: R~ = Rth + Rtl
+    float *Rtl = Rth + 4 * 32 * 4;
     __shared__ __align__(8) uint64_t mbar;
     __shared__ uint32_t tslot;
     __shared__ BatchInfo bi;
@@ -230,8 +259,8 @@ __global__ void __launch_bounds__(MXT, 1) k_embed_fwd_mx(
     uint32_t phase = 0;
     bool alive = true;
     int staged = -1;
-    double *Gw = Gt + warp * 32 * 17;
-    double *Rw = Rt + warp * 32 * 4;
+    float *Gw = Gt + warp * 32 * 17;
+    float *Rwh = Rth + warp * 32 * 4, *Rwl = Rtl + warp * 32 * 4;
     double *Tww = Tw + warp * 4 * E3;
     const int lo = (int)(((long long)blockIdx.x * N) / gridDim.x);
     const int hi = (int)(((long long)(blockIdx.x + 1) * N) / gridDim.x);
@@ -323,10 +352,11 @@ __global__ void __launch_bounds__(MXT, 1) k_embed_fwd_mx(
                     tc::mma_commit(&mbar);
                 }
                 alive = tc_wait(&mbar, phase, status);
-                // epilogue 2: G = (h1, h1) + tanh(z2 + b2); the warp's partial of T = R~^T G in FP64
+                // epilogue 2: G = (h1, h1) + tanh(z2 + b2); the warp's partial of T = R~^T G in
+                // double-float arithmetic (exact products of G with R~'s FP32 parts)
                 if (alive && warp_live) {
 #pragma unroll
-                    for (int c = 0; c < 4; ++c) Rw[lane * 4 + c] = valid ? gg.R[c] : 0.0;
+                    for (int c = 0; c < 4; ++c) df_split(valid ? gg.R[c] : 0.0, Rwh[lane * 4 + c], Rwl[lane * 4 + c]);
 #pragma unroll
                     for (int cc = 0; cc < N2p; cc += 16) {
                         float v[16];
@@ -336,17 +366,18 @@ __global__ void __launch_bounds__(MXT, 1) k_embed_fwd_mx(
                             const int o = cc + q;
                             float G2 = 0.f;
                             if (o < E3 && valid) G2 = h1[o < E2 ? o : o - E2] + tanhf(v[q] + b2[o]);
-                            Gw[lane * 17 + q] = (double)G2;
+                            Gw[lane * 17 + q] = G2;
                         }
                         __syncwarp();
 #pragma unroll
                         for (int u = 0; u < 2; ++u) {
                             const int p = lane + 32 * u, c = p >> 4, q = p & 15, o = cc + q;
                             if (o < E3) {
-                                double acc = 0.0;
+                                float sh = 0.f, sl = 0.f;
 #pragma unroll 8
-                                for (int rr = 0; rr < 32; ++rr) acc = fma(Rw[rr * 4 + c], Gw[rr * 17 + q], acc);
-                                Tww[c * E3 + o] = acc;
+                                for (int rr = 0; rr < 32; ++rr)
+                                    df_fma(sh, sl, Gw[rr * 17 + q], Rwh[rr * 4 + c], Rwl[rr * 4 + c]);
+                                Tww[c * E3 + o] = df_value(sh, sl);
                             }
                         }
                         __syncwarp();
@@ -411,10 +442,11 @@ __global__ void __launch_bounds__(MXT, 1) k_embed_bwd_mx(
     unsigned char *dA1 = A1 + X * S::A1B;
     unsigned char *B1 = dA1 + X * S::A1B;
     unsigned char *B2 = B1 + X * S::B1B;
-    double *gTs = reinterpret_cast<double *>(B2 + X * S::B2B);  // [AB][4][E3], scaled
-    double *Ts = gTs + AB * 4 * E3;                          // [4][E3]
+    double *Ts = reinterpret_cast<double *>(B2 + X * S::B2B);  // [4][E3]
     double *red = Ts + 4 * E3;                               // [4][12]
     double *facc = red + 4 * 12;                             // [AB][12]
+    float *gTh = reinterpret_cast<float *>(facc + AB * 12);  // [AB][4][E3], scaled: gT = gTh + gTl
+    float *gTl = gTh + AB * 4 * E3;
     __shared__ __align__(8) uint64_t mbar;
     __shared__ uint32_t tslot;
     __shared__ BatchInfo bi;
@@ -453,7 +485,7 @@ __global__ void __launch_bounds__(MXT, 1) k_embed_bwd_mx(
                 if (xx < m2)
                     for (int b2i = 0; b2i < E3; ++b2i) acc = fma(gd[xx * E3 + b2i], Ts[cc * E3 + b2i], acc);
                 for (int a2 = 0; a2 < m2; ++a2) acc = fma(gd[a2 * E3 + xx], Ts[cc * E3 + a2], acc);
-                gTs[j * 4 * E3 + p] = acc * m.desc_scale;
+                df_split(acc * m.desc_scale, gTh[j * 4 * E3 + p], gTl[j * 4 * E3 + p]);
             }
             __syncthreads();
         }
@@ -564,13 +596,15 @@ __global__ void __launch_bounds__(MXT, 1) k_embed_bwd_mx(
                     tc::mma_commit(&mbar);
                 }
                 alive = tc_wait(&mbar, phase, status);
-                // epilogue 2: G, dG/ds and the FP64 contractions with gT of the row's atom
+                // epilogue 2: G, dG/ds and the contractions with gT of the row's atom in
+                // double-float arithmetic (exact products with gT's FP32 parts)
                 double fo[3] = {0.0, 0.0, 0.0}, vir[9];
 #pragma unroll
                 for (int q = 0; q < 9; ++q) vir[q] = 0.0;
                 if (alive && warp_live) {
-                    const double *gT = gTs + j * 4 * E3;
-                    double ra[4] = {0.0, 0.0, 0.0, 0.0}, rb[4] = {0.0, 0.0, 0.0, 0.0};
+                    const float *gh = gTh + j * 4 * E3, *gl = gTl + j * 4 * E3;
+                    float rah[4] = {0.f, 0.f, 0.f, 0.f}, ral[4] = {0.f, 0.f, 0.f, 0.f};
+                    float rbh[4] = {0.f, 0.f, 0.f, 0.f}, rbl[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
                     for (int cc = 0; cc < N2p; cc += 16) {
                         float v[16], dv[16];
@@ -582,16 +616,22 @@ __global__ void __launch_bounds__(MXT, 1) k_embed_bwd_mx(
                             if (o < E3) {
                                 const int os = o < E2 ? o : o - E2;
                                 const float t = tanhf(v[q] + b2[o]);
-                                const double G2 = (double)(h1[os] + t);
-                                const double dG = (double)fmaf(fmaf(-t, t, 1.f), dv[q], dh1[os]);
+                                const float G2 = h1[os] + t;
+                                const float dG = fmaf(fmaf(-t, t, 1.f), dv[q], dh1[os]);
 #pragma unroll
                                 for (int c = 0; c < 4; ++c) {
-                                    const double gt = gT[c * E3 + o];
-                                    ra[c] = fma(G2, gt, ra[c]);
-                                    rb[c] = fma(dG, gt, rb[c]);
+                                    const float bh = gh[c * E3 + o], bl = gl[c * E3 + o];
+                                    df_fma(rah[c], ral[c], G2, bh, bl);
+                                    df_fma(rbh[c], rbl[c], dG, bh, bl);
                                 }
                             }
                         }
+                    }
+                    double ra[4], rb[4];
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        ra[c] = df_value(rah[c], ral[c]);
+                        rb[c] = df_value(rbh[c], rbl[c]);
                     }
                     if (valid) {
                         double gR0 = ra[0];
@@ -959,16 +999,16 @@ size_t fwd_smem()
 {
     using S = EmbShape<E1>;
     constexpr int X = SPLIT ? 2 : 1;
-    return X * (S::A0B + S::A1B + S::B1B + S::B2B) +
-           sizeof(double) * (4 * 32 * 17 + 4 * 32 * 4 + 4 * 4 * S::E3 + AB * 4 * S::E3);
+    return X * (S::A0B + S::A1B + S::B1B + S::B2B) + sizeof(double) * (4 * 4 * S::E3 + AB * 4 * S::E3) +
+           sizeof(float) * (4 * 32 * 17 + 2 * 4 * 32 * 4);
 }
 template <int E1, bool SPLIT>
 size_t bwd_smem()
 {
     using S = EmbShape<E1>;
     constexpr int X = SPLIT ? 2 : 1;
-    return X * (2 * S::A0B + 2 * S::A1B + S::B1B + S::B2B) +
-           sizeof(double) * (AB * 4 * S::E3 + 4 * S::E3 + 48 + AB * 12);
+    return X * (2 * S::A0B + 2 * S::A1B + S::B1B + S::B2B) + sizeof(double) * (4 * S::E3 + 48 + AB * 12) +
+           sizeof(float) * 2 * AB * 4 * S::E3;
 }
 
 // CTAs per SM that fit next to each other (shared memory; a 1 KB reserve per CTA)

@@ -973,8 +973,10 @@ dp_status dp_ctx_create(const dp_model *model, int64_t natoms_max, int32_t cand_
     ALLOC(c->d_inv_mass_conv, DP_MAX_TYPES);
     ALLOC(c->d_mass, DP_MAX_TYPES);
     if (is_mixed(precision)) {
-        ALLOC(c->eb.fit_t, N * (size_t)c->m.n_fit * 256);
-        ALLOC(c->eb.fit_h, N * 256);
+        // one [rows][128] block per 128-atom tile of one type (N / 128 + ntypes tiles at most)
+        const size_t fit_rows = (size_t)N + 128 * (size_t)c->m.ntypes;
+        ALLOC(c->eb.fit_t, fit_rows * c->m.n_fit * 256);
+        ALLOC(c->eb.fit_h, fit_rows * 256);
     }
     c->use_oz = false;
     c->oz_version = -1;

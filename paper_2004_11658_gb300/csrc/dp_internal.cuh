@@ -179,8 +179,8 @@ struct EvalBuffers {
     double *pair_g;    // [N][nm][3]
     double *f_own;     // [N][3]
     double *vir_part;  // [N][9]
-    float *fit_t;      // mixed mode: tanh values of the fitting layers [N][n_fit][256]
-    float *fit_h;      // mixed mode: fitting activation / gradient [N][256]
+    float *fit_t;      // mixed mode: tanh values of the fitting layers [tile][n_fit][256][128]
+    float *fit_h;      // mixed mode: fitting activation / gradient [tile][256][128]
 };
 
 // Mixed-precision operands: BF16 copies of the weight matrices in the

@@ -447,6 +447,9 @@ __global__ void __launch_bounds__(MXT, 1) k_embed_bwd_mx(
     double *facc = red + 4 * 12;                             // [AB][12]
     float *gTh = reinterpret_cast<float *>(facc + AB * 12);  // [AB][4][E3], scaled: gT = gTh + gTl
     float *gTl = gTh + AB * 4 * E3;
+    // dE/dD of one atom [M2][E3] in the operand buffers (A0 .. dA1), when it fits there
+    double *gds = reinterpret_cast<double *>(smraw);
+    const bool gd_fits = (size_t)m.m2 * E3 * sizeof(double) <= (size_t)X * (2 * S::A0B + 2 * S::A1B);
     __shared__ __align__(8) uint64_t mbar;
     __shared__ uint32_t tslot;
     __shared__ BatchInfo bi;
@@ -474,18 +477,28 @@ __global__ void __launch_bounds__(MXT, 1) k_embed_bwd_mx(
         for (int q = tid; q < AB * 12; q += MXT) facc[q] = 0.0;
         __syncthreads();
         // gT[c][x] = [x < M2] sum_b gD[x][b] T[c][b] + sum_{a<M2} gD[a][x] T[c][a], times the scale
+        // (dE/dD of the atom staged in the operand buffers, idle between tiles, when it fits)
         for (int j = 0; j < k; ++j) {
             const int i = bi.ids[j];
             for (int p = tid; p < 4 * E3; p += MXT) Ts[p] = Tin[(size_t)i * 4 * E3 + p];
-            __syncthreads();
             const double *gd = gD + (size_t)i * m2 * E3;
+            if (gd_fits) {
+                const double2 *src = reinterpret_cast<const double2 *>(gd);
+                double2 *dst = reinterpret_cast<double2 *>(gds);
+                for (int p = tid; p < m2 * E3 / 2; p += MXT) dst[p] = src[p];
+                gd = gds;
+            }
+            __syncthreads();
             for (int p = tid; p < 4 * E3; p += MXT) {
                 const int cc = p / E3, xx = p - cc * E3;
-                double acc = 0.0;
+                double acc = 0.0, acc2 = 0.0;
                 if (xx < m2)
-                    for (int b2i = 0; b2i < E3; ++b2i) acc = fma(gd[xx * E3 + b2i], Ts[cc * E3 + b2i], acc);
+                    for (int b2i = 0; b2i < E3; b2i += 2) {  // two chains (E3 = 4 e1 is even)
+                        acc = fma(gd[xx * E3 + b2i], Ts[cc * E3 + b2i], acc);
+                        acc2 = fma(gd[xx * E3 + b2i + 1], Ts[cc * E3 + b2i + 1], acc2);
+                    }
                 for (int a2 = 0; a2 < m2; ++a2) acc = fma(gd[a2 * E3 + xx], Ts[cc * E3 + a2], acc);
-                df_split(acc * m.desc_scale, gTh[j * 4 * E3 + p], gTl[j * 4 * E3 + p]);
+                df_split((acc + acc2) * m.desc_scale, gTh[j * 4 * E3 + p], gTl[j * 4 * E3 + p]);
             }
             __syncthreads();
         }
@@ -605,6 +618,11 @@ __global__ void __launch_bounds__(MXT, 1) k_embed_bwd_mx(
                     const float *gh = gTh + j * 4 * E3, *gl = gTl + j * 4 * E3;
                     float rah[4] = {0.f, 0.f, 0.f, 0.f}, ral[4] = {0.f, 0.f, 0.f, 0.f};
                     float rbh[4] = {0.f, 0.f, 0.f, 0.f}, rbl[4] = {0.f, 0.f, 0.f, 0.f};
+                    // G and dG/ds of 16 features go through this thread's column of the layer-2
+                    // operand buffer (idle once its MMA is done), so that the contraction is one
+                    // compact loop rather than unrolled code for every feature
+                    static_assert(2 * 16 * MXT * sizeof(float) <= 2 * S::A1B, "G, dG/ds staging fits in A1, dA1");
+                    float *Gst = reinterpret_cast<float *>(A1) + tid, *dGst = Gst + 16 * MXT;
 #pragma unroll
                     for (int cc = 0; cc < N2p; cc += 16) {
                         float v[16], dv[16];
@@ -616,14 +634,20 @@ __global__ void __launch_bounds__(MXT, 1) k_embed_bwd_mx(
                             if (o < E3) {
                                 const int os = o < E2 ? o : o - E2;
                                 const float t = tanhf(v[q] + b2[o]);
-                                const float G2 = h1[os] + t;
-                                const float dG = fmaf(fmaf(-t, t, 1.f), dv[q], dh1[os]);
+                                Gst[q * MXT] = h1[os] + t;
+                                dGst[q * MXT] = fmaf(fmaf(-t, t, 1.f), dv[q], dh1[os]);
+                            }
+                        }
+                        const int nq = E3 - cc < 16 ? E3 - cc : 16;
+#pragma unroll 1
+                        for (int q = 0; q < nq; ++q) {
+                            const float G2 = Gst[q * MXT], dG = dGst[q * MXT];
+                            const int o = cc + q;
 #pragma unroll
-                                for (int c = 0; c < 4; ++c) {
-                                    const float bh = gh[c * E3 + o], bl = gl[c * E3 + o];
-                                    df_fma(rah[c], ral[c], G2, bh, bl);
-                                    df_fma(rbh[c], rbl[c], dG, bh, bl);
-                                }
+                            for (int c = 0; c < 4; ++c) {
+                                const float bh = gh[c * E3 + o], bl = gl[c * E3 + o];
+                                df_fma(rah[c], ral[c], G2, bh, bl);
+                                df_fma(rbh[c], rbl[c], dG, bh, bl);
                             }
                         }
                     }
@@ -761,6 +785,7 @@ __global__ void __launch_bounds__(MXT, 1) k_fit_mx(DevModel m, MixedModel mx, in
     unsigned char *Ab = smraw;                               // [FIT_NS][128][64] bf16 (layer-1 input chunks)
     unsigned char *Bb = Ab + FIT_NS * MXT * FIT_KC * 2;      // [FIT_NS][256][64] bf16 (weight chunks)
     unsigned char *Hb = Bb + FIT_NS * 256 * FIT_KC * 2;      // [128][256] bf16 (activation / gradient)
+    static_assert(MXT * 17 * sizeof(double) <= FIT_NS * MXT * FIT_KC * 2, "the dE/dD staging fits in the A ring");
     __shared__ __align__(8) uint64_t full[FIT_NS], empty[FIT_NS], dbar;
     __shared__ uint32_t tslot;
     __shared__ int pfail;
@@ -803,8 +828,10 @@ __global__ void __launch_bounds__(MXT, 1) k_fit_mx(DevModel m, MixedModel mx, in
     const bool warp_live = 32 * warp < cnt;
     bool alive = true;
     const float *P32 = mx.p32 + m.fit_base[a];
-    float *tb = tbuf + (size_t)(my < 0 ? 0 : my) * nf * HK;
-    float *hb = hbuf + (size_t)(my < 0 ? 0 : my) * HK;
+    // per-tile activation buffers, column-major over the tile's 128 rows so that a warp's
+    // accesses are contiguous: t of layer l, feature n at tb[(l HK + n) MXT]; h at hb[n MXT]
+    float *tb = tbuf + (size_t)tile_id * nf * HK * MXT + tid;
+    float *hb = hbuf + (size_t)tile_id * HK * MXT + tid;
 
     // Streamed GEMM into TMEM columns [0, Np): K-chunks of FIT_KC.  B (weights,
     // K-chunked, chunk kc at Bsrc + kc * chunk_bytes + row_off_bytes) always comes
@@ -906,8 +933,8 @@ __global__ void __launch_bounds__(MXT, 1) k_fit_mx(DevModel m, MixedModel mx, in
                         const int n = cc + q;
                         if (n < F) {
                             const float t = tanhf(v[q] + bias[n]);
-                            tb[l * HK + n] = t;
-                            hb[n] = (l > 0 ? hb[n] : 0.f) + t;  // equal-width skip after the first layer
+                            tb[(l * HK + n) * MXT] = t;
+                            hb[n * MXT] = (l > 0 ? hb[n * MXT] : 0.f) + t;  // equal-width skip after the first layer
                         }
                     }
                 }
@@ -918,7 +945,7 @@ __global__ void __launch_bounds__(MXT, 1) k_fit_mx(DevModel m, MixedModel mx, in
         for (int k8 = 0; k8 < HK; k8 += 8) {
             float v[8];
 #pragma unroll
-            for (int q = 0; q < 8; ++q) v[q] = (my >= 0 && k8 + q < F) ? hb[k8 + q] : 0.f;
+            for (int q = 0; q < 8; ++q) v[q] = (my >= 0 && k8 + q < F) ? hb[(k8 + q) * MXT] : 0.f;
             st8(Hb, tid, k8, HK, v);
         }
         tc_sync();
@@ -937,13 +964,13 @@ __global__ void __launch_bounds__(MXT, 1) k_fit_mx(DevModel m, MixedModel mx, in
     }
     if (alive && my >= 0) {
         double e = (double)wo[Kin];
-        for (int n = 0; n < Kin; ++n) e = fma((double)hb[n], (double)wo[n], e);
+        for (int n = 0; n < Kin; ++n) e = fma((double)hb[n * MXT], (double)wo[n], e);
         Ei[my] = e;
     }
 
     // ---------------- backward: gh = w_out; gz_l = gh * (1 - t_l^2)
     if (my >= 0)
-        for (int n = 0; n < Kin; ++n) hb[n] = wo[n];
+        for (int n = 0; n < Kin; ++n) hb[n * MXT] = wo[n];
     for (int l = nf - 1; l >= 0 && alive; --l) {
         const int F = m.fit[l];
         const int Kl = (l == 0) ? K1 : m.fit[l - 1];
@@ -954,8 +981,8 @@ __global__ void __launch_bounds__(MXT, 1) k_fit_mx(DevModel m, MixedModel mx, in
                 const int n = k8 + q;
                 float gz = 0.f;
                 if (my >= 0 && n < F) {
-                    const float t = tb[l * HK + n];
-                    gz = hb[n] * fmaf(-t, t, 1.f);
+                    const float t = tb[(l * HK + n) * MXT];
+                    gz = hb[n * MXT] * fmaf(-t, t, 1.f);
                 }
                 v[q] = gz;
             }
@@ -971,7 +998,26 @@ __global__ void __launch_bounds__(MXT, 1) k_fit_mx(DevModel m, MixedModel mx, in
             const int nb = min(NB, Kinp - n0);
             alive = gemm(false, nK, Bsrc, (int64_t)Kinp * 128, (int64_t)(n0 / 8) * 1024, nb);
             if (!alive) break;
-            if (warp_live) {
+            if (l == 0) {
+                // dE/dD through shared memory (the A ring is idle in the backward), 16 columns at
+                // a time, so that each half-warp stores 128 contiguous bytes of one atom's row
+                double *stage = reinterpret_cast<double *>(Ab);  // [MXT][17]
+                for (int cc = 0; cc < nb; cc += 16) {
+                    if (warp_live) {
+                        float v[16];
+                        tc::tmem_ld16(tlane + cc, v);
+#pragma unroll
+                        for (int q = 0; q < 16; ++q) stage[tid * 17 + q] = (double)v[q];
+                    }
+                    __syncthreads();
+                    for (int p = tid; p < MXT * 16; p += MXT) {
+                        const int row = p >> 4, q = p & 15, n = n0 + cc + q;
+                        const int at = rows_atom[row];
+                        if (at >= 0 && n < Kl) gD[(size_t)at * K1 + n] = stage[row * 17 + q];
+                    }
+                    __syncthreads();
+                }
+            } else if (warp_live) {
                 for (int cc = 0; cc < nb; cc += 16) {
                     float v[16];
                     tc::tmem_ld16(tlane + cc, v);
@@ -979,10 +1025,7 @@ __global__ void __launch_bounds__(MXT, 1) k_fit_mx(DevModel m, MixedModel mx, in
 #pragma unroll
                         for (int q = 0; q < 16; ++q) {
                             const int n = n0 + cc + q;
-                            if (n < Kl) {
-                                if (l == 0) gD[(size_t)my * K1 + n] = (double)v[q];
-                                else hb[n] = v[q] + hb[n];  // equal widths: the skip passes gh through
-                            }
+                            if (n < Kl) hb[n * MXT] = v[q] + hb[n * MXT];  // equal widths: the skip passes gh through
                         }
                     }
                 }

@@ -226,8 +226,8 @@ class FastPathMD:
     def _check(self, x, t, box):
         dp.dp_build_nlist(self.refc, x, t, box, 0.0)
         ref = dp.dp_eval(self.refc, x, t, box)["force"].clone()
-        dp.dp_build_nlist(self.fast, x, t, box, 0.0)
-        f = dp.dp_eval(self.fast, x, t, box)["force"]
+        # the student's force of these coordinates, kept by its last MD step
+        f = dp.dp_md_get_force(self.fast, x.shape[0], device=x.device)
         d = (f - ref).double()
         return float(d.pow(2).mean().sqrt()), float(d.norm(dim=1).max()), float(ref.pow(2).mean().sqrt())
 
@@ -253,9 +253,6 @@ class FastPathMD:
                     self.on_full = True
                     self.switched_at = self.done
                     dp.dp_md_reset(self.full)  # forces of the current configuration on the next step
-                else:
-                    # the check rebuilt the student's lists; its next step recomputes its forces
-                    dp.dp_md_reset(self.fast)
                 new.append(dict(step=self.done, force_rmse=rmse, max_atom_err=worst, force_rms_full=frms,
                                 model="full" if self.on_full else "student"))
         self.checks.extend(new)

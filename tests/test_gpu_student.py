@@ -124,6 +124,19 @@ def test_fast_path_with_full_model_fallback(synth):
     print("loose:", checks)
     assert sw is None and len(checks) == 4
     assert all(c["model"] == "student" and c["force_rmse"] < 1.0 for c in checks)
+    # the checks read the student's MD force and leave its run untouched: the same
+    # trajectory as a plain student run, and that force is the student's force of
+    # the final coordinates
+    xp = torch.tensor(w["coords"], device="cuda")
+    vp = torch.tensor(v0, device="cuda")
+    plain = dp.Context(stud, N, precision=dp.DP_PREC_MIXED)
+    dp.dp_md_step(plain, xp, vp, t, w["box"], w["masses"], 0.5, 20, **kw)
+    assert torch.equal(x, xp) and torch.equal(v, vp)
+    fresh = dp.Context(stud, N, precision=dp.DP_PREC_MIXED)
+    dp.dp_build_nlist(fresh, x, t, w["box"], 0.0)
+    f_eval = dp.dp_eval(fresh, x, t, w["box"])["force"]
+    f_md = dp.dp_md_get_force(loose.fast, N)
+    assert torch.allclose(f_md, f_eval, rtol=0, atol=1e-12 * float(f_eval.abs().max()))
 
     x = torch.tensor(w["coords"], device="cuda")
     v = torch.tensor(v0, device="cuda")

@@ -110,9 +110,20 @@ __device__ __forceinline__ double dp_tanh64(double x, const double *__restrict__
     // |x| >= 19.125: +-1 is tanh correctly rounded (1 - tanh(19.125) < 2^-54)
     const long long bits = __double_as_longlong(ax);
     if (bits >= 0x4033200000000000ll) return bits > 0x7ff0000000000000ll ? x : copysign(1.0, x);  // NaN stays NaN
-    // k = round(20 |x|) from the low bits of 20|x| + 1.5 * 2^52
-    const double v = fma(ax, 20.0, 6755399441055744.0);
-    const int k = (int)(__double_as_longlong(v) & 0xffffffffll);
+    // k = round-half-even(20 |x|) from the bits of |x| = m 2^(e - 1075) on the
+    // integer pipe (the value fma(|x|, 20, 1.5 2^52) would give in its low bits)
+    int k = 0;
+    {
+        const int e = (int)(bits >> 52);
+        const int sh = 1075 - e;  // >= 48 below the cutoff
+        if (e != 0 && sh < 62) {
+            const long long m20 = ((bits & 0xFFFFFFFFFFFFFll) | 0x10000000000000ll) * 20;  // < 2^58
+            long long r = m20 >> sh;
+            const long long rem = m20 & ((1ll << sh) - 1), half = 1ll << (sh - 1);
+            if (rem > half || (rem == half && (r & 1))) r += 1;
+            k = (int)r;
+        }
+    }
     const double *c = tab + k * DP_TANH_STRIDE;
     const double t = ax - c[0];
     double p = c[DP_TANH_NCOEF];

@@ -76,11 +76,13 @@ constexpr int XTB = 512;                   // threads of the embedding kernels
 constexpr int XRB = XNR * 4 / (XTB / 32);  // rows per thread in the last layer's epilogue (8)
 constexpr int XQB = XRB / 2;               // rows per thread per lane-half in layer 1's epilogue (4)
 
-// y[q] = sum_{g=2}^{8} C_g[q] 2^(8 (8 - g)) for the 8 columns at taddr (group g
-// at column offset (g - 2) * XNR): the group sums are integers below 2^24, so
-// they are combined exactly in two int64 Horner chains (g = 2..4 and g = 5..8,
-// below 2^41 and 2^49) and converted once: y = hi 2^32 + lo, one rounding.
-__device__ __forceinline__ void combine_groups_8(uint32_t taddr, double (&y)[8])
+// y[q] = 2^p_q sum_{g=2}^{8} C_g[q] 2^(8 (8 - g)) for the 8 columns at taddr
+// (group g at column offset (g - 2) * XNR), with p_q = p0 + (rowexp ? rowexp[q] :
+// 0): the group sums are integers below 2^24, so they are combined exactly in
+// two int64 Horner chains (g = 2..4 and g = 5..8, below 2^41 and 2^49) and
+// converted once, y = (hi 2^32 + lo) 2^p_q with one rounding -- on the integer
+// pipe (oz_i64x2_scaled), bit for bit fma((double)hi, 2^32, (double)lo) 2^p_q.
+__device__ __forceinline__ void combine_groups_8(uint32_t taddr, double (&y)[8], int p0, const int *rowexp)
 {
     static_assert(XS == 7 && XBETA == 8, "combine_groups_8 assumes 7 digits of 8 bits");
     long long hi[8], lo[8];
@@ -98,12 +100,13 @@ __device__ __forceinline__ void combine_groups_8(uint32_t taddr, double (&y)[8])
         }
     }
 #pragma unroll
-    for (int q = 0; q < 8; ++q) y[q] = fma((double)hi[q], 4294967296.0, (double)lo[q]);
+    for (int q = 0; q < 8; ++q) y[q] = oz_i64x2_scaled(hi[q], lo[q], p0 + (rowexp ? rowexp[q] : 0));
 }
 
 // combine_groups_8 for an M = 64 accumulator: the 4 columns that
-// tc::tmem_ld16x2_4 (second half 16 columns on) gives this thread.
-__device__ __forceinline__ void combine_groups4(uint32_t taddr, double (&y)[4])
+// tc::tmem_ld16x2_4 (second half 16 columns on) gives this thread, scaled by
+// 2^(p0 + rowexp[j]).
+__device__ __forceinline__ void combine_groups4(uint32_t taddr, double (&y)[4], int p0, const int *rowexp)
 {
     long long hi[4], lo[4];
 #pragma unroll
@@ -120,7 +123,7 @@ __device__ __forceinline__ void combine_groups4(uint32_t taddr, double (&y)[4])
         }
     }
 #pragma unroll
-    for (int q = 0; q < 4; ++q) y[q] = fma((double)hi[q], 4294967296.0, (double)lo[q]);
+    for (int q = 0; q < 4; ++q) y[q] = oz_i64x2_scaled(hi[q], lo[q], p0 + (rowexp ? rowexp[q] : 0));
 }
 
 template <int E1>
@@ -230,7 +233,7 @@ __global__ void __launch_bounds__(XTB, 1) k_embed_fwd_x(DevModel m, const unsign
                 }
                 staged = net;
             }
-            const double cscale = f < E3 ? oz_pow2(1 + fexp[f] - XBETA * (XS + 1)) : 0.0;
+            const int cexp = 1 + (f < E3 ? fexp[f] : 0) - XBETA * (XS + 1);  // scale of the group sums
             for (int c0 = 0; c0 < nb && alive; c0 += XNR) {
                 const int nv = min(XNR, nb - c0);  // valid rows of the chunk
                 // geometry of the next XGR rows of the block, one row per thread
@@ -274,7 +277,7 @@ __global__ void __launch_bounds__(XTB, 1) k_embed_fwd_x(DevModel m, const unsign
 #pragma unroll
                         for (int q = 0; q < 8; ++q) {
                             const double v = (k0 + q < E1) ? H0[row * LD0 + k0 + q] : 0.0;
-                            I[q] = __double2ll_rn(v * 36028797018963968.0);  // 2^55
+                            I[q] = oz_rint_pow2(v, 55);  // round(v 2^55)
                         }
                         const uint32_t ofs = tc::kmajor_offset(row, k0, K1p);
                         for (int sd = XS - 1; sd >= 0; --sd) {
@@ -327,15 +330,15 @@ __global__ void __launch_bounds__(XTB, 1) k_embed_fwd_x(DevModel m, const unsign
                     const int f1 = 16 * (warp & 3) + (lane & 15);
                     const int r0 = 16 * (lane >> 4) + XQB * (warp >> 2);
                     double y1[XQB];
-                    combine_groups4(tlane + XQB * (uint32_t)(warp >> 2), y1);
+                    combine_groups4(tlane + XQB * (uint32_t)(warp >> 2), y1,
+                                    1 + (f1 < E2 ? fexp1[f1] : 0) - XBETA * (XS + 1), nullptr);
                     if (f1 < E2) {
-                        const double cv1 = oz_pow2(1 + fexp1[f1] - XBETA * (XS + 1));
                         const double bb = b1s[f1];
                         const int os = f1 < E1 ? f1 : f1 - E1;
 #pragma unroll
                         for (int j = 0; j < XQB; ++j) {
                             const int row = r0 + j;
-                            H1[row * LD1 + f1] = H0[row * LD0 + os] + dp_tanh64(fma(y1[j], cv1, bb), m.tanh_tab);
+                            H1[row * LD1 + f1] = H0[row * LD0 + os] + dp_tanh64(y1[j] + bb, m.tanh_tab);
                         }
                     }
                     tc::fence_before_sync();
@@ -356,7 +359,7 @@ __global__ void __launch_bounds__(XTB, 1) k_embed_fwd_x(DevModel m, const unsign
 #pragma unroll
                     for (int q = 0; q < 8; ++q) {
                         const double v = (k0 + q < E2) ? H1[row * LD1 + k0 + q] : 0.0;
-                        I[q] = __double2ll_rn(v * 36028797018963968.0);  // 2^55
+                        I[q] = oz_rint_pow2(v, 55);  // round(v 2^55)
                     }
                     const uint32_t ofs = tc::kmajor_offset(row, k0, K2p);
                     for (int sd = XS - 1; sd >= 0; --sd) {
@@ -408,7 +411,7 @@ __global__ void __launch_bounds__(XTB, 1) k_embed_fwd_x(DevModel m, const unsign
                 }
                 // epilogue: feature f of rows XRB grp .. XRB grp + XRB - 1 of the chunk
                 double y[XRB];
-                combine_groups_8(tlane + XRB * grp, y);
+                combine_groups_8(tlane + XRB * grp, y, cexp, nullptr);
                 if (f < E3) {
                     const double bf = b2s[f];
                     const int fs = f < E2 ? f : f - E2;
@@ -416,7 +419,7 @@ __global__ void __launch_bounds__(XTB, 1) k_embed_fwd_x(DevModel m, const unsign
                     for (int qq = 0; qq < XRB; ++qq) {
                         const int q = XRB * grp + qq;
                         if (q < nv) {
-                            const double z = fma(y[qq], cscale, bf);
+                            const double z = y[qq] + bf;
                             const double G = H1[q * LD1 + fs] + dp_tanh64(z, m.tanh_tab);
 #pragma unroll
                             for (int c = 0; c < 4; ++c) tacc[c] = fma(Rt[q * 4 + c], G, tacc[c]);
@@ -618,10 +621,10 @@ __global__ void __launch_bounds__(XTB, 1) k_embed_bwd_x(DevModel m, const unsign
     auto make_digits = [&](const double *src, bool fixed) {
         for (int p = tid; p < XNR * (K2p / 8); p += XTB) {
             const int row = p % XNR, k0 = (p / XNR) * 8;  // lanes on consecutive rows
-            const double sc = oz_pow2(XBETA * XS - (fixed ? 1 : erow[row]));
+            const int sk = XBETA * XS - (fixed ? 1 : erow[row]);  // round(v 2^sk)
             long long I[8];
 #pragma unroll
-            for (int q = 0; q < 8; ++q) I[q] = (k0 + q < E2) ? __double2ll_rn(src[row * LD1 + k0 + q] * sc) : 0ll;
+            for (int q = 0; q < 8; ++q) I[q] = (k0 + q < E2) ? oz_rint_pow2(src[row * LD1 + k0 + q], sk) : 0ll;
             const uint32_t ofs = tc::kmajor_offset(row, k0, K2p);
             for (int sd = XS - 1; sd >= 0; --sd) {
                 int dg[8];
@@ -648,10 +651,10 @@ __global__ void __launch_bounds__(XTB, 1) k_embed_bwd_x(DevModel m, const unsign
             const int which = p / NP, pp = p - which * NP;
             const int row = pp % XNR, k0 = (pp / XNR) * 8;
             const double *src = which ? dH0 : H0;
-            const double sc = oz_pow2(XBETA * XS - (which ? erow0[row] : 1));
+            const int sk = XBETA * XS - (which ? erow0[row] : 1);  // round(v 2^sk)
             long long I[8];
 #pragma unroll
-            for (int q = 0; q < 8; ++q) I[q] = (k0 + q < E1) ? __double2ll_rn(src[row * LD0 + k0 + q] * sc) : 0ll;
+            for (int q = 0; q < 8; ++q) I[q] = (k0 + q < E1) ? oz_rint_pow2(src[row * LD0 + k0 + q], sk) : 0ll;
             const uint32_t ofs = tc::kmajor_offset(row, k0, K1p);
             unsigned char *dst = Bd + (size_t)which * XS * XNR * K1p * 2;
             for (int sd = XS - 1; sd >= 0; --sd) {
@@ -834,19 +837,18 @@ __global__ void __launch_bounds__(XTB, 1) k_embed_bwd_x(DevModel m, const unsign
                     const int f1 = 16 * (warp & 3) + (lane & 15);
                     const int r0 = 16 * (lane >> 4) + XQB * (warp >> 2);
                     const uint32_t ta = tlane + XQB * (uint32_t)(warp >> 2);
+                    const int fx1 = f1 < E2 ? fexp1[f1] : 0;
                     double y1[XQB], dy1[XQB];
-                    combine_groups4(ta, y1);
-                    combine_groups4(ta + 256, dy1);
+                    combine_groups4(ta, y1, 1 + fx1 - XBETA * (XS + 1), nullptr);
+                    combine_groups4(ta + 256, dy1, fx1 - XBETA * (XS + 1), erow0 + r0);
                     if (f1 < E2) {
-                        const int fx1 = fexp1[f1];
-                        const double cv1 = oz_pow2(1 + fx1 - XBETA * (XS + 1));
                         const double bb = b1s[f1];
                         const int os = f1 < E1 ? f1 : f1 - E1;
 #pragma unroll
                         for (int j = 0; j < XQB; ++j) {
                             const int row = r0 + j;
-                            const double t = dp_tanh64(fma(y1[j], cv1, bb), m.tanh_tab);
-                            const double dz = dy1[j] * oz_pow2(erow0[row] + fx1 - XBETA * (XS + 1));
+                            const double t = dp_tanh64(y1[j] + bb, m.tanh_tab);
+                            const double dz = dy1[j];
                             H1[row * LD1 + f1] = H0[row * LD0 + os] + t;
                             dH1[row * LD1 + f1] = fma(fma(-t, t, 1.0), dz, dH0[row * LD0 + os]);
                         }
@@ -900,9 +902,8 @@ __global__ void __launch_bounds__(XTB, 1) k_embed_bwd_x(DevModel m, const unsign
                 }
                 // epilogue: feature f of rows XRB grp .. XRB grp + XRB - 1
                 double yv[XRB], yt[XRB];
-                combine_groups_8(tlane + XRB * grp, yv);
-                combine_groups_8(tlane + 256 + XRB * grp, yt);
-                const double cv = oz_pow2(1 + fx - XBETA * (XS + 1));
+                combine_groups_8(tlane + XRB * grp, yv, 1 + fx - XBETA * (XS + 1), nullptr);
+                combine_groups_8(tlane + 256 + XRB * grp, yt, fx - XBETA * (XS + 1), erow + XRB * grp);
                 const double bf = f < E3 ? b2s[f] : 0.0;
                 const int fs = f < E2 ? f : (f < E3 ? f - E2 : 0);
                 double *rw = red + (warp * XRB) * 8;  // this warp's [XRB rows][8]
@@ -917,9 +918,9 @@ __global__ void __launch_bounds__(XTB, 1) k_embed_bwd_x(DevModel m, const unsign
                         const int qq = q4 + r4, q = XRB * grp + qq;
                         double G = 0.0, dG = 0.0;
                         if (q < nv && f < E3) {
-                            const double t = dp_tanh64(fma(yv[qq], cv, bf), m.tanh_tab);
+                            const double t = dp_tanh64(yv[qq] + bf, m.tanh_tab);
                             G = H1[q * LD1 + fs] + t;
-                            const double dz2 = yt[qq] * oz_pow2(erow[q] + fx - XBETA * (XS + 1));
+                            const double dz2 = yt[qq];
                             dG = fma(fma(-t, t, 1.0), dz2, dH1[q * LD1 + fs]);
                         }
 #pragma unroll

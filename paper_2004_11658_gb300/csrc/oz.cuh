@@ -55,3 +55,82 @@ static __host__ __device__ __forceinline__ double oz_pow2(int e)
 #endif
 }
 
+
+// ---------------------------------------------------------------------------
+// Integer-pipe versions of the two conversions around the digit products, so
+// that they leave the FP64 pipe free (results bit for bit those of the FP64
+// instructions they replace).
+
+// round-half-even(v 2^k) for finite v with |v 2^k| < 2^62: the value of
+// __double2ll_rn(v * 2^k) (the product being exact), from v's bit pattern.
+static __host__ __device__ __forceinline__ long long oz_rint_pow2(double v, int k)
+{
+#ifdef __CUDA_ARCH__
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+#else
+    unsigned long long b;
+    std::memcpy(&b, &v, 8);
+#endif
+    const int e = (int)((b >> 52) & 0x7ffull);
+    if (e == 0) return 0;  // zero or subnormal: far below 1/2 after any scale used here
+    const long long m = (long long)((b & 0xFFFFFFFFFFFFFull) | 0x10000000000000ull);  // v = m 2^(e - 1075)
+    const int s = e - 1075 + k;
+    long long r;
+    if (s >= 0) {
+        r = m << s;
+    } else if (s < -53) {
+        r = 0;  // m 2^s < 1/2
+    } else {
+        const int sh = -s;
+        r = m >> sh;
+        const long long rem = m & ((1ll << sh) - 1), half = 1ll << (sh - 1);
+        if (rem > half || (rem == half && (r & 1))) r += 1;
+    }
+    return (b >> 63) ? -r : r;
+}
+
+// The double nearest (ties to even) to (hi 2^32 + lo) 2^p, for |hi| < 2^62,
+// |lo| < 2^62 and a result in the normal range: the value of
+// fma((double)hi, 2^32, (double)lo) * 2^p (one rounding, an exact power-of-two
+// scale), built from the integer bits.
+static __host__ __device__ __forceinline__ double oz_i64x2_scaled(long long hi, long long lo, int p)
+{
+    // X = hi 2^32 + lo, |X| < 2^95, as a sign and a magnitude of at most 95 bits
+    const __int128 X = (__int128)hi * ((__int128)1 << 32) + (__int128)lo;
+    if (X == 0) return 0.0;
+    const bool neg = X < 0;
+    const unsigned __int128 u = neg ? (unsigned __int128)(-X) : (unsigned __int128)X;
+    const unsigned long long uh = (unsigned long long)(u >> 64), ul = (unsigned long long)u;
+#ifdef __CUDA_ARCH__
+    const int lz = uh ? __clzll((long long)uh) : 64 + __clzll((long long)ul);
+#else
+    const int lz = uh ? __builtin_clzll(uh) : 64 + __builtin_clzll(ul);
+#endif
+    const int nb = 128 - lz;  // bits of |X|
+    unsigned long long m;
+    int e2;  // |X| rounded = m 2^e2, 2^52 <= m < 2^53
+    if (nb <= 53) {
+        m = ul << (53 - nb);
+        e2 = nb - 53;
+    } else {
+        int sh = nb - 53;
+        const unsigned __int128 one = 1;
+        m = (unsigned long long)(u >> sh);
+        const unsigned __int128 rem = u & ((one << sh) - 1), half = one << (sh - 1);
+        if (rem > half || (rem == half && (m & 1ull))) m += 1;
+        if (m == (1ull << 53)) {
+            m >>= 1;
+            sh += 1;
+        }
+        e2 = sh;
+    }
+    unsigned long long bits = ((unsigned long long)(e2 + p + 52 + 1023) << 52) | (m & 0xFFFFFFFFFFFFFull);
+    if (neg) bits |= 1ull << 63;
+#ifdef __CUDA_ARCH__
+    return __longlong_as_double((long long)bits);
+#else
+    double d;
+    std::memcpy(&d, &bits, 8);
+    return d;
+#endif
+}

@@ -332,7 +332,24 @@ __global__ void __launch_bounds__(XTB, 1) k_embed_fwd_x(DevModel m, const unsign
                     double y1[XQB];
                     combine_groups4(tlane + XQB * (uint32_t)(warp >> 2), y1,
                                     1 + (f1 < E2 ? fexp1[f1] : 0) - XBETA * (XS + 1), nullptr);
-                    if (f1 < E2) {
+                    const int n1 = E2 - 16 * (warp & 3);  // real features of this warp's quarter
+                    static_assert(XQB == 4, "the sparse-quarter path maps 4 features x 8 rows to the lanes");
+                    if (n1 > 0 && n1 <= 4) {
+                        // at most 4 real features: one (feature, row) item per lane -- feature L / 8 of
+                        // the quarter, row (L / 4) % 2 lane-half, row L % 4 of the warp's block
+                        const int fi = lane >> 3, hf = (lane >> 2) & 1, j = lane & 3;
+                        double ys = 0.0;
+#pragma unroll
+                        for (int k = 0; k < XQB; ++k) {
+                            const double a = __shfl_sync(0xffffffffu, y1[k], fi + 16 * hf);
+                            if (k == j) ys = a;
+                        }
+                        if (fi < n1) {
+                            const int fq = 16 * (warp & 3) + fi, row = 16 * hf + XQB * (warp >> 2) + j;
+                            const int os = fq < E1 ? fq : fq - E1;
+                            H1[row * LD1 + fq] = H0[row * LD0 + os] + dp_tanh64(ys + b1s[fq], m.tanh_tab);
+                        }
+                    } else if (f1 < E2) {
                         const double bb = b1s[f1];
                         const int os = f1 < E1 ? f1 : f1 - E1;
 #pragma unroll
@@ -412,7 +429,38 @@ __global__ void __launch_bounds__(XTB, 1) k_embed_fwd_x(DevModel m, const unsign
                 // epilogue: feature f of rows XRB grp .. XRB grp + XRB - 1 of the chunk
                 double y[XRB];
                 combine_groups_8(tlane + XRB * grp, y, cexp, nullptr);
-                if (f < E3) {
+                const int nq = E3 - 32 * (warp & 3);  // real features of this warp's TMEM quarter
+                static_assert(XRB == 8, "the sparse-quarter path maps 4 features x 8 rows to the lanes");
+                if (nq > 0 && nq <= 32 / XRB) {
+                    // a quarter with at most 4 real features: one (feature, row) item per lane (feature
+                    // L / 8 of the quarter, row L % 8), so the FP64 work runs once, not once per row
+                    const int fi = lane >> 3, r = lane & 7;
+                    double ys = 0.0;
+#pragma unroll
+                    for (int k = 0; k < XRB; ++k) {
+                        const double a = __shfl_sync(0xffffffffu, y[k], fi);
+                        if (k == r) ys = a;
+                    }
+                    const int fq = 32 * (warp & 3) + fi, q = XRB * grp + r;
+                    double pc[4] = {0.0, 0.0, 0.0, 0.0};
+                    if (fi < nq && q < nv) {
+                        const int fsq = fq < E2 ? fq : fq - E2;
+                        const double G = H1[q * LD1 + fsq] + dp_tanh64(ys + b2s[fq], m.tanh_tab);
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) pc[c] = Rt[q * 4 + c] * G;
+                    }
+                    // sum over the 8 rows (lanes 8 fi .. 8 fi + 7), then lane fi, which holds the
+                    // T column of feature fq, adds it
+#pragma unroll
+                    for (int o = 1; o < 8; o <<= 1)
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) pc[c] += __shfl_xor_sync(0xffffffffu, pc[c], o);
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        const double v = __shfl_sync(0xffffffffu, pc[c], 8 * (lane & 3));
+                        if (lane < nq) tacc[c] += v;
+                    }
+                } else if (f < E3) {
                     const double bf = b2s[f];
                     const int fs = f < E2 ? f : f - E2;
 #pragma unroll
@@ -841,7 +889,29 @@ __global__ void __launch_bounds__(XTB, 1) k_embed_bwd_x(DevModel m, const unsign
                     double y1[XQB], dy1[XQB];
                     combine_groups4(ta, y1, 1 + fx1 - XBETA * (XS + 1), nullptr);
                     combine_groups4(ta + 256, dy1, fx1 - XBETA * (XS + 1), erow0 + r0);
-                    if (f1 < E2) {
+                    const int n1 = E2 - 16 * (warp & 3);  // real features of this warp's quarter
+                    static_assert(XQB == 4, "the sparse-quarter path maps 4 features x 8 rows to the lanes");
+                    if (n1 > 0 && n1 <= 4) {
+                        // at most 4 real features: one (feature, row) item per lane (as in the forward)
+                        const int fi = lane >> 3, hf = (lane >> 2) & 1, j = lane & 3;
+                        double ys = 0.0, dzs = 0.0;
+#pragma unroll
+                        for (int k = 0; k < XQB; ++k) {
+                            const double a = __shfl_sync(0xffffffffu, y1[k], fi + 16 * hf);
+                            const double b = __shfl_sync(0xffffffffu, dy1[k], fi + 16 * hf);
+                            if (k == j) {
+                                ys = a;
+                                dzs = b;
+                            }
+                        }
+                        if (fi < n1) {
+                            const int fq = 16 * (warp & 3) + fi, row = 16 * hf + XQB * (warp >> 2) + j;
+                            const int os = fq < E1 ? fq : fq - E1;
+                            const double t = dp_tanh64(ys + b1s[fq], m.tanh_tab);
+                            H1[row * LD1 + fq] = H0[row * LD0 + os] + t;
+                            dH1[row * LD1 + fq] = fma(fma(-t, t, 1.0), dzs, dH0[row * LD0 + os]);
+                        }
+                    } else if (f1 < E2) {
                         const double bb = b1s[f1];
                         const int os = f1 < E1 ? f1 : f1 - E1;
 #pragma unroll
@@ -907,6 +977,65 @@ __global__ void __launch_bounds__(XTB, 1) k_embed_bwd_x(DevModel m, const unsign
                 const double bf = f < E3 ? b2s[f] : 0.0;
                 const int fs = f < E2 ? f : (f < E3 ? f - E2 : 0);
                 double *rw = red + (warp * XRB) * 8;  // this warp's [XRB rows][8]
+                const int nq = E3 - 32 * (warp & 3);  // real features of this warp's TMEM quarter
+                static_assert(XRB == 8, "the sparse-quarter path maps 4 features x 8 rows to the lanes");
+                if (nq <= 0) {
+                    // padding only: zero partials
+                    rw[lane] = 0.0;
+                    rw[32 + lane] = 0.0;
+                } else if (nq <= 32 / XRB) {
+                    // a quarter with at most 4 real features (e.g. 96..99 of 100): its 4 x 8 (feature,
+                    // row) items go one per lane, so the FP64 work runs once instead of once per row on
+                    // mostly idle lanes; lane L takes feature L / 8 of the quarter and row L % 8
+                    const int fi = lane >> 3, r = lane & 7;
+                    double ys = 0.0, ts = 0.0;
+#pragma unroll
+                    for (int k = 0; k < XRB; ++k) {
+                        const double a = __shfl_sync(0xffffffffu, yv[k], fi);
+                        const double b = __shfl_sync(0xffffffffu, yt[k], fi);
+                        if (k == r) {
+                            ys = a;
+                            ts = b;
+                        }
+                    }
+                    double g4[4];
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) g4[c] = __shfl_sync(0xffffffffu, gt[c], fi);
+                    const int fq = 32 * (warp & 3) + fi, q = XRB * grp + r;
+                    double p[8];
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) p[c] = 0.0;
+                    if (fi < nq && q < nv) {
+                        const int fsq = fq < E2 ? fq : fq - E2;
+                        const double t = dp_tanh64(ys + b2s[fq], m.tanh_tab);
+                        const double G = H1[q * LD1 + fsq] + t;
+                        const double dG = fma(fma(-t, t, 1.0), ts, dH1[q * LD1 + fsq]);
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) {
+                            p[c] = G * g4[c];
+                            p[4 + c] = dG * g4[c];
+                        }
+                    }
+                    // sum over the quarter's features (lanes r, r + 8, r + 16, r + 24)
+#pragma unroll
+                    for (int o = 8; o < 32; o <<= 1)
+#pragma unroll
+                        for (int c = 0; c < 8; ++c) p[c] += __shfl_xor_sync(0xffffffffu, p[c], o);
+                    // lane L writes components 2 (L / 8) and 2 (L / 8) + 1 of row L % 8
+                    double w0 = p[0], w1 = p[1];
+                    if (fi == 1) {
+                        w0 = p[2];
+                        w1 = p[3];
+                    } else if (fi == 2) {
+                        w0 = p[4];
+                        w1 = p[5];
+                    } else if (fi == 3) {
+                        w0 = p[6];
+                        w1 = p[7];
+                    }
+                    rw[r * 8 + 2 * fi] = w0;
+                    rw[r * 8 + 2 * fi + 1] = w1;
+                } else {
                 // partials p[r][c] = G gT[c] (c < 4), dG gT[c - 4] for 4 rows at a time, summed over
                 // the warp's 32 features by a transposing shuffle tree (31 adds per lane): lane L ends
                 // with the sum of row L / 8, component L % 8
@@ -940,6 +1069,7 @@ __global__ void __launch_bounds__(XTB, 1) k_embed_bwd_x(DevModel m, const unsign
                         }
                     }
                     rw[(q4 + (lane >> 3)) * 8 + (lane & 7)] = p[0];
+                }
                 }
                 __syncthreads();
                 // chain rule through R~(r_ij), one lane per row (warp 0)

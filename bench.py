@@ -69,15 +69,15 @@ FORCE_RMSE_TARGET = 1e-3   # eV/A, against the FP64 full model
 #                     (smsp__sass_thread_inst_executed_op_d{fma,add,mul}_pred_on.sum)
 #                     per real neighbour row
 TRAFFIC = {
-    "embed_bwd": {"bytes_per_launch": 206.73152e6 + 21.489664e6, "file": "embed_x.cu", "src_sha": "26282166356cad25"},
-    "embed_bwd_mx<25>": {"bytes_per_launch": 204.68352e6 + 16.390912e6, "file": "mixed.cu", "src_sha": "22da7b23c12ddc0f"},
+    "embed_bwd": {"bytes_per_launch": 206.925056e6 + 21.675264e6, "file": "embed_x.cu", "src_sha": "4954f89e6792262d"},
+    "embed_bwd_mx<25>": {"bytes_per_launch": 204.77056e6 + 17.105152e6, "file": "mixed.cu", "src_sha": "1bc49a405925719e"},
 }
 FP64_ISSUED = {
     # ncu on one evaluation of the 12,288-atom water box (bench.py --workload
-    # water12288 --profile-eval 1), 1,046,154 real rows: dfma 2.173e9, dadd
-    # 1.743e9, dmul 1.020e9 thread instructions; FP64 pipe busy 47.5%
-    "embed_bwd": {"fp64_flop_per_row": 6794.9, "pipe_busy": 0.475, "file": "embed_x.cu",
-                  "src_sha": "26282166356cad25"},
+    # water12288 --profile-eval 1), 1,046,154 real rows: dfma 2.434e9, dadd
+    # 1.289e9, dmul 0.566e9 thread instructions; FP64 pipe busy 45.0%
+    "embed_bwd": {"fp64_flop_per_row": 6425.5, "pipe_busy": 0.450, "file": "embed_x.cu",
+                  "src_sha": "4954f89e6792262d"},
 }
 
 

@@ -97,9 +97,10 @@ __device__ __forceinline__ void dp_switch(double r, double rs, double rc, double
 }
 
 // FP64 tanh by piecewise Taylor polynomials (tanh64.cu): interval k is
-// centred at k/20, k = 0..DP_TANH_NINT-1, and stores [centre, a_0 .. a_8].
-#define DP_TANH_NINT 383
-#define DP_TANH_NCOEF 9
+// centred at k/40, k = 0..DP_TANH_NINT-1, and stores [centre, a_0 .. a_7].
+#define DP_TANH_INV_H 40
+#define DP_TANH_NINT 766
+#define DP_TANH_NCOEF 8
 #define DP_TANH_STRIDE (DP_TANH_NCOEF + 1)
 // Fills the table on the current device (once) and returns its device address.
 cudaError_t dp_tanh_setup(const double **table);
@@ -110,16 +111,16 @@ __device__ __forceinline__ double dp_tanh64(double x, const double *__restrict__
     // |x| >= 19.125: +-1 is tanh correctly rounded (1 - tanh(19.125) < 2^-54)
     const long long bits = __double_as_longlong(ax);
     if (bits >= 0x4033200000000000ll) return bits > 0x7ff0000000000000ll ? x : copysign(1.0, x);  // NaN stays NaN
-    // k = round-half-even(20 |x|) from the bits of |x| = m 2^(e - 1075) on the
-    // integer pipe (the value fma(|x|, 20, 1.5 2^52) would give in its low bits)
+    // k = round-half-even(40 |x|) from the bits of |x| = m 2^(e - 1075) on the
+    // integer pipe (the value fma(|x|, 40, 1.5 2^52) would give in its low bits)
     int k = 0;
     {
         const int e = (int)(bits >> 52);
         const int sh = 1075 - e;  // >= 48 below the cutoff
         if (e != 0 && sh < 62) {
-            const long long m20 = ((bits & 0xFFFFFFFFFFFFFll) | 0x10000000000000ll) * 20;  // < 2^58
-            long long r = m20 >> sh;
-            const long long rem = m20 & ((1ll << sh) - 1), half = 1ll << (sh - 1);
+            const long long mk = ((bits & 0xFFFFFFFFFFFFFll) | 0x10000000000000ll) * DP_TANH_INV_H;  // < 2^59
+            long long r = mk >> sh;
+            const long long rem = mk & ((1ll << sh) - 1), half = 1ll << (sh - 1);
             if (rem > half || (rem == half && (r & 1))) r += 1;
             k = (int)r;
         }

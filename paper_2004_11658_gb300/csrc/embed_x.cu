@@ -775,9 +775,11 @@ __global__ void __launch_bounds__(XTB, 1) k_embed_bwd_x(DevModel m, const unsign
             }
             __syncthreads();
         }
-        double gt[4];
+        double gt[4], gtp[4];  // dE/dT of this thread's feature, and of lane ^ 16's
 #pragma unroll
         for (int c = 0; c < 4; ++c) gt[c] = f < E3 ? gTs[c * XM + f] : 0.0;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) gtp[c] = __shfl_xor_sync(0xffffffffu, gt[c], 16);
         double fo[3] = {0.0, 0.0, 0.0}, vir[9];
 #pragma unroll
         for (int q = 0; q < 9; ++q) vir[q] = 0.0;
@@ -1041,25 +1043,43 @@ __global__ void __launch_bounds__(XTB, 1) k_embed_bwd_x(DevModel m, const unsign
                 // with the sum of row L / 8, component L % 8
 #pragma unroll 1
                 for (int q4 = 0; q4 < XRB; q4 += 4) {
-                    double p[32];
+                    double G[4], dG[4];
 #pragma unroll
                     for (int r4 = 0; r4 < 4; ++r4) {
                         const int qq = q4 + r4, q = XRB * grp + qq;
-                        double G = 0.0, dG = 0.0;
+                        G[r4] = 0.0;
+                        dG[r4] = 0.0;
                         if (q < nv && f < E3) {
                             const double t = dp_tanh64(yv[qq] + bf, m.tanh_tab);
-                            G = H1[q * LD1 + fs] + t;
+                            G[r4] = H1[q * LD1 + fs] + t;
                             const double dz2 = yt[qq];
-                            dG = fma(fma(-t, t, 1.0), dz2, dH1[q * LD1 + fs]);
-                        }
-#pragma unroll
-                        for (int c = 0; c < 4; ++c) {
-                            p[r4 * 8 + c] = G * gt[c];
-                            p[r4 * 8 + 4 + c] = dG * gt[c];
+                            dG[r4] = fma(fma(-t, t, 1.0), dz2, dH1[q * LD1 + fs]);
                         }
                     }
+                    // first level of the tree on the factors: lanes below 16 keep rows 0, 1 of the four,
+                    // the others rows 2, 3; each receives its partner's G and dG of its kept rows and
+                    // forms both features' products itself (with the partner's dE/dT, gtp)
+                    const bool hi16 = (lane & 16) != 0;
+                    double p[16];
+                    {
+                        double kG[2], kD[2], rG[2], rD[2];
 #pragma unroll
-                    for (int w = 16, n = 16; w >= 1; w >>= 1, n >>= 1) {
+                        for (int r = 0; r < 2; ++r) {
+                            kG[r] = hi16 ? G[2 + r] : G[r];
+                            kD[r] = hi16 ? dG[2 + r] : dG[r];
+                            rG[r] = __shfl_xor_sync(0xffffffffu, hi16 ? G[r] : G[2 + r], 16);
+                            rD[r] = __shfl_xor_sync(0xffffffffu, hi16 ? dG[r] : dG[2 + r], 16);
+                        }
+#pragma unroll
+                        for (int r = 0; r < 2; ++r)
+#pragma unroll
+                            for (int c = 0; c < 4; ++c) {
+                                p[r * 8 + c] = fma(rG[r], gtp[c], kG[r] * gt[c]);
+                                p[r * 8 + 4 + c] = fma(rD[r], gtp[c], kD[r] * gt[c]);
+                            }
+                    }
+#pragma unroll
+                    for (int w = 8, n = 8; w >= 1; w >>= 1, n >>= 1) {
                         const bool up = (lane & w) != 0;
 #pragma unroll
                         for (int k = 0; k < n; ++k) {

@@ -1,17 +1,19 @@
 // tanh64.cu -- FP64 tanh for the FP64 kernels: piecewise Taylor polynomials.
 //
-// tanh(|x|) on [0, 19.125) is split into intervals of width 1/20; on interval
-// k (centre c_k = k/20, k = round(20 |x|)) it is the degree-8 Taylor polynomial
-//   sum_n a_{k,n} t^n,  t = |x| - c_k,  |t| <= 1/40,
+// tanh(|x|) on [0, 19.125) is split into intervals of width 1/40; on interval
+// k (centre c_k = k/40, k = round(40 |x|)) it is the degree-7 Taylor polynomial
+//   sum_n a_{k,n} t^n,  t = |x| - c_k,  |t| <= 1/80,
 // and tanh(|x|) = 1 beyond (1 - tanh(19.125) < 2^-54, below half the spacing
 // of the doubles under 1, so 1 is tanh correctly rounded).  The coefficients come
 // from the derivatives of tanh, which are polynomials in T = tanh:
 //   d/dx P(T) = P'(T) (1 - T^2),   a_{k,n} = P_n(tanh(c_k)) / n!,
 // so each interval needs only tanh(c_k).  The Taylor remainder is bounded by
-// (1/40)^9 max|tanh^(9)| / 9! < 1e-16 (tanh's nearest singularities are at
-// +-i pi/2), so the result is within a few units in the last place of tanh
-// in absolute terms.  Evaluation: one interval index, one subtraction and
-// 8 FMAs in FP64 -- about a third of the FP64 pipe slots of the library tanh.
+// (1/80)^8 max|tanh^(8)| / 8! = 1.8e-17 (tanh's nearest singularities are at
+// +-i pi/2); on the interval at 0, where tanh is odd, the first neglected term
+// is of degree 9, so the relative error there stays near one unit in the last
+// place.  Evaluation: one interval index (integer pipe), one subtraction and
+// 7 FMAs in FP64 -- about a quarter of the FP64 pipe slots of the library
+// tanh.  The table (766 intervals x 9 doubles, 55 KB) is read through L1.
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -65,7 +67,7 @@ cudaError_t dp_tanh_setup(const double **table)
     }
     std::vector<double> tab((size_t)DP_TANH_NINT * DP_TANH_STRIDE);
     for (int k = 0; k < DP_TANH_NINT; ++k) {
-        const double c = k / 20.0;
+        const double c = (double)k / DP_TANH_INV_H;
         tab[(size_t)k * DP_TANH_STRIDE] = c;
         taylor_coeffs(c, tab.data() + (size_t)k * DP_TANH_STRIDE + 1);
     }

@@ -1,8 +1,8 @@
 """The FP64 tanh method of the FP64 kernels, checked on the CPU against
 high-precision tanh (mpmath), independently of the device table.
 
-tanh(|x|) on [0, 19.125) is a degree-8 Taylor polynomial around the nearest
-multiple of 1/20, with coefficients a_n = P_n(tanh(c)) / n! from the derivative
+tanh(|x|) on [0, 19.125) is a degree-7 Taylor polynomial around the nearest
+multiple of 1/40, with coefficients a_n = P_n(tanh(c)) / n! from the derivative
 recursion P_0(T) = T, P_{n+1}(T) = P_n'(T) (1 - T^2); beyond 19.125 it is 1.
 """
 import math
@@ -12,8 +12,8 @@ import pytest
 
 mpmath = pytest.importorskip("mpmath")
 
-NCOEF = 9       # a_0 .. a_8
-H = 1.0 / 20    # interval width
+NCOEF = 8       # a_0 .. a_7
+H = 1.0 / 40    # interval width
 XMAX = 19.125
 
 
@@ -51,11 +51,11 @@ def test_derivative_recursion_matches_series():
 
 def test_remainder_and_cutoff_bounds():
     mpmath.mp.dps = 40
-    P9 = _poly_derivs(NCOEF + 1)[NCOEF]
+    Pn = _poly_derivs(NCOEF + 1)[NCOEF]
     ts = [mpmath.mpf(i) / 2000 for i in range(-2000, 2001)]
-    m9 = max(abs(mpmath.polyval(list(reversed(P9)), t)) for t in ts)   # max |tanh^(9)| over T in [-1, 1]
-    rem = (mpmath.mpf(1) / 40) ** 9 * m9 / math.factorial(9)
-    assert rem < 1e-16
+    mn = max(abs(mpmath.polyval(list(reversed(Pn)), t)) for t in ts)   # max |tanh^(8)| over T in [-1, 1]
+    rem = (mpmath.mpf(H) / 2) ** NCOEF * mn / math.factorial(NCOEF)
+    assert rem < 3e-17
     # beyond XMAX, +-1 is the correctly rounded tanh: 1 - tanh(XMAX) is below half
     # the spacing (2^-53) of the doubles just under 1
     assert 1 - mpmath.tanh(XMAX) < mpmath.mpf(2) ** -54
@@ -71,7 +71,7 @@ def test_piecewise_taylor_accuracy():
     xs = np.concatenate([rng.uniform(0, XMAX, 4000), np.arange(0, XMAX, H / 2)[:-1], [0.0, 1e-300, 1e-8]])
     worst = 0.0
     for x in xs:
-        k = int(round(20.0 * x))
+        k = int(round(40.0 * x))
         assert abs(x - k * H) <= H / 2 + 1e-14
         a = table[k]
         t = x - k * H

@@ -16,9 +16,11 @@
 // Split operands (DP_PREC_MIXED_SPLIT, template flag SPLIT of the embedding
 // kernels): every FP32 row operand and weight is stored as a BF16 high part
 // and the BF16 value of its remainder, and each K-slice issues hi*hi + hi*lo +
-// lo*hi into the same FP32 accumulator (~16 bits per operand instead of 8);
-// the operand buffers double, so these kernels run one CTA per SM.  That mode
-// runs its fitting net on fit_oz.cu's exact digit kernels, not on k_fit_mx.
+// lo*hi into the same FP32 accumulator (~16 bits per operand instead of 8).
+// The operand buffers double; layer 1's operands and weights share one region
+// with the layer-2 row operands (EmbPlan) and batches hold fewer atoms, so two
+// CTAs still fit per SM.  That mode runs its fitting net on fit_oz.cu's exact
+// digit kernels, not on k_fit_mx.
 //
 // Supported shapes: embedding widths (e1, 2 e1, 4 e1) with e1 in {16, 25, 32}
 // (the paper's doubling nets), fitting layers of equal width <= 256 after the
@@ -182,8 +184,8 @@ __device__ __forceinline__ void geometry(const DevModel &m, const double *__rest
 // Per-warp partial sums are merged into per-atom accumulators in warp order
 // after each tile, which keeps every result reproducible bit for bit.
 
-constexpr int AB = 8;                        // atoms per batch
-constexpr int MAXG = AB * (DP_MAX_NM / 32);  // 32-row groups per batch and type (upper bound)
+constexpr int AB_MAX = 8;                        // atoms per batch (at most)
+constexpr int MAXG = AB_MAX * (DP_MAX_NM / 32);  // 32-row groups per batch and type (upper bound)
 
 template <int E1>
 struct EmbShape {
@@ -193,19 +195,50 @@ struct EmbShape {
     static constexpr int B1B = N1p * K1p * 2, B2B = N2p * K2p * 2;
 };
 
+constexpr size_t zmax(size_t a, size_t b) { return a > b ? a : b; }
+
+// Shared-memory plan of the embedding kernels (byte offsets from the dynamic
+// buffer).  Plain BF16: every operand has its own buffer and batches hold 8
+// atoms.  Split operands (two copies of everything): layer 1's operands and
+// weights (A0, dA0, B1) and the layer-2 row operands (A1, dA1) share one region
+// R -- layer 1's MMAs are complete before the layer-2 operands are written, and
+// B1 is copied again for every tile -- and batches hold 4 atoms (2 for e1 = 32),
+// so that two CTAs fit per SM.
+template <int E1, bool SPLIT>
+struct EmbPlan {
+    using S = EmbShape<E1>;
+    static constexpr int X = SPLIT ? 2 : 1;
+    static constexpr int AB = SPLIT ? (E1 >= 32 ? 2 : 4) : AB_MAX;
+    static constexpr size_t a0 = (size_t)X * S::A0B, a1 = (size_t)X * S::A1B;
+    static constexpr size_t b1 = (size_t)X * S::B1B, b2 = (size_t)X * S::B2B;
+    // forward.  Plain: A0, A1, B1, B2.  Split: region R = [A0, B1 | A1], then B2.
+    static constexpr size_t FA0 = 0, FA1 = SPLIT ? 0 : a0, FB1 = SPLIT ? a0 : a0 + a1;
+    static constexpr size_t FB2 = SPLIT ? zmax(a0 + b1, a1) : a0 + a1 + b1;
+    static constexpr size_t FEND = FB2 + b2;
+    // backward.  Plain: A0, dA0, A1, dA1, B1, B2.  Split: R = [A0, dA0, B1 | A1, dA1], then B2.
+    static constexpr size_t BA0 = 0, BdA0 = a0;
+    static constexpr size_t BA1 = SPLIT ? 0 : 2 * a0, BdA1 = BA1 + a1;
+    static constexpr size_t BB1 = SPLIT ? 2 * a0 : 2 * a0 + 2 * a1;
+    static constexpr size_t BB2 = SPLIT ? zmax(2 * a0 + b1, 2 * a1) : 2 * a0 + 2 * a1 + b1;
+    static constexpr size_t BEND = BB2 + b2;
+    // bytes from the start that are free between tiles (dE/dD of one atom is staged
+    // there): the region R when split, the row operands otherwise (B1 stays resident)
+    static constexpr size_t BFREE = SPLIT ? BB2 : 2 * a0 + 2 * a1;
+};
+
 struct BatchInfo {
-    int ids[AB];             // atom indices of the batch
+    int ids[AB_MAX];         // atom indices of the batch
     int grp_atom[MAXG];      // batch index of each 32-row group
     int grp_r0[MAXG];        // first row of each group
     int ngroups;
 };
 
-// Next batch [first, first + k) of one type inside [first, hi).
-__device__ __forceinline__ int batch_size(int first, int hi, const int *tstart, int T, int &a)
+// Next batch [first, first + k) of one type inside [first, hi), k <= ab.
+__device__ __forceinline__ int batch_size(int first, int hi, const int *tstart, int T, int ab, int &a)
 {
     a = 0;
     while (a + 1 < T && first >= tstart[a + 1]) ++a;
-    return min(AB, min(hi, tstart[a + 1]) - first);
+    return min(ab, min(hi, tstart[a + 1]) - first);
 }
 
 // Group list of neighbour type b for the batch (one thread builds it).
@@ -230,15 +263,17 @@ __global__ void __launch_bounds__(MXT, 1) k_embed_fwd_mx(
     const int32_t *__restrict__ nreal, double *__restrict__ Tout, double *__restrict__ Dout, int32_t *status)
 {
     using S = EmbShape<E1>;
+    using P = EmbPlan<E1, SPLIT>;
     constexpr int E2 = S::E2, E3 = S::E3, K1p = S::K1p, N1p = S::N1p, K2p = S::K2p, N2p = S::N2p;
     constexpr int TCOLS = tcols_for(N2p);
-    constexpr int X = SPLIT ? 2 : 1;  // operand copies: high (and low) parts
+    constexpr int X = P::X;  // operand copies: high (and low) parts
+    constexpr int AB = P::AB;
     extern __shared__ __align__(1024) unsigned char smraw[];
-    unsigned char *A0 = smraw;
-    unsigned char *A1 = A0 + X * S::A0B;
-    unsigned char *B1 = A1 + X * S::A1B;
-    unsigned char *B2 = B1 + X * S::B1B;
-    double *Tw = reinterpret_cast<double *>(B2 + X * S::B2B);  // [4][4][E3] per-warp partial of one tile
+    unsigned char *A0 = smraw + P::FA0;
+    unsigned char *A1 = smraw + P::FA1;
+    unsigned char *B1 = smraw + P::FB1;
+    unsigned char *B2 = smraw + P::FB2;
+    double *Tw = reinterpret_cast<double *>(smraw + P::FEND);  // [4][4][E3] per-warp partial of one tile
     double *Tacc = Tw + 4 * 4 * E3;                         // [AB][4][E3] per-atom sums
     float *Gt = reinterpret_cast<float *>(Tacc + AB * 4 * E3);  // [4][32][17]
     float *Rth = Gt + 4 * 32 * 17;                          // [4][32][4]: R~ = Rth + Rtl
@@ -267,7 +302,7 @@ __global__ void __launch_bounds__(MXT, 1) k_embed_fwd_mx(
 
     for (int first = lo; first < hi && alive;) {
         int a;
-        const int k = batch_size(first, hi, tstart, T, a);
+        const int k = batch_size(first, hi, tstart, T, AB, a);
         __syncthreads();
         if (tid < AB) bi.ids[tid] = tid < k ? type_perm[first + tid] : 0;
         for (int q = tid; q < AB * 4 * E3; q += MXT) Tacc[q] = 0.0;
@@ -280,13 +315,15 @@ __global__ void __launch_bounds__(MXT, 1) k_embed_fwd_mx(
             if (G == 0) continue;
             const int net = a * T + b;
             if (net != staged) {
-                copy16(B1, mx.emb_ops + mx.emb_off[net][0], X * S::B1B);
+                if constexpr (!SPLIT) copy16(B1, mx.emb_ops + mx.emb_off[net][0], X * S::B1B);
                 copy16(B2, mx.emb_ops + mx.emb_off[net][1], X * S::B2B);
                 staged = net;
             }
             const float *P32 = mx.p32 + m.emb_base[net];
             const float *W0 = P32, *b0 = P32 + E1, *b1 = P32 + 2 * E1 + E1 * E2, *b2 = b1 + E2 + E2 * E3;
             for (int t0 = 0; t0 < G && alive; t0 += 4) {
+                // split operands: B1 shares its region with the layer-2 operands of the last tile
+                if constexpr (SPLIT) copy16(B1, mx.emb_ops + mx.emb_off[net][0], X * S::B1B);
                 const int g = t0 + warp;
                 const bool warp_live = g < G;
                 const int j = warp_live ? bi.grp_atom[g] : 0;
@@ -434,22 +471,24 @@ __global__ void __launch_bounds__(MXT, 1) k_embed_bwd_mx(
     constexpr int E2 = S::E2, E3 = S::E3, K1p = S::K1p, N1p = S::N1p, K2p = S::K2p, N2p = S::N2p;
     constexpr int TOFF = N2p;                 // tangent accumulator column offset
     constexpr int TCOLS = tcols_for(2 * N2p);
-    constexpr int X = SPLIT ? 2 : 1;          // operand copies: high (and low) parts
+    using P = EmbPlan<E1, SPLIT>;
+    constexpr int X = P::X;                   // operand copies: high (and low) parts
+    constexpr int AB = P::AB;
     extern __shared__ __align__(1024) unsigned char smraw[];
-    unsigned char *A0 = smraw;
-    unsigned char *dA0 = A0 + X * S::A0B;
-    unsigned char *A1 = dA0 + X * S::A0B;
-    unsigned char *dA1 = A1 + X * S::A1B;
-    unsigned char *B1 = dA1 + X * S::A1B;
-    unsigned char *B2 = B1 + X * S::B1B;
-    double *Ts = reinterpret_cast<double *>(B2 + X * S::B2B);  // [4][E3]
+    unsigned char *A0 = smraw + P::BA0;
+    unsigned char *dA0 = smraw + P::BdA0;
+    unsigned char *A1 = smraw + P::BA1;
+    unsigned char *dA1 = smraw + P::BdA1;
+    unsigned char *B1 = smraw + P::BB1;
+    unsigned char *B2 = smraw + P::BB2;
+    double *Ts = reinterpret_cast<double *>(smraw + P::BEND);  // [4][E3]
     double *red = Ts + 4 * E3;                               // [4][12]
     double *facc = red + 4 * 12;                             // [AB][12]
     float *gTh = reinterpret_cast<float *>(facc + AB * 12);  // [AB][4][E3], scaled: gT = gTh + gTl
     float *gTl = gTh + AB * 4 * E3;
-    // dE/dD of one atom [M2][E3] in the operand buffers (A0 .. dA1), when it fits there
+    // dE/dD of one atom [M2][E3] in the operand buffers, when it fits there
     double *gds = reinterpret_cast<double *>(smraw);
-    const bool gd_fits = (size_t)m.m2 * E3 * sizeof(double) <= (size_t)X * (2 * S::A0B + 2 * S::A1B);
+    const bool gd_fits = (size_t)m.m2 * E3 * sizeof(double) <= P::BFREE;
     __shared__ __align__(8) uint64_t mbar;
     __shared__ uint32_t tslot;
     __shared__ BatchInfo bi;
@@ -471,7 +510,7 @@ __global__ void __launch_bounds__(MXT, 1) k_embed_bwd_mx(
 
     for (int first = lo; first < hi && alive;) {
         int a;
-        const int k = batch_size(first, hi, tstart, T, a);
+        const int k = batch_size(first, hi, tstart, T, AB, a);
         __syncthreads();
         if (tid < AB) bi.ids[tid] = tid < k ? type_perm[first + tid] : 0;
         for (int q = tid; q < AB * 12; q += MXT) facc[q] = 0.0;
@@ -510,13 +549,15 @@ __global__ void __launch_bounds__(MXT, 1) k_embed_bwd_mx(
             if (G == 0) continue;
             const int net = a * T + b;
             if (net != staged) {
-                copy16(B1, mx.emb_ops + mx.emb_off[net][0], X * S::B1B);
+                if constexpr (!SPLIT) copy16(B1, mx.emb_ops + mx.emb_off[net][0], X * S::B1B);
                 copy16(B2, mx.emb_ops + mx.emb_off[net][1], X * S::B2B);
                 staged = net;
             }
             const float *P32 = mx.p32 + m.emb_base[net];
             const float *W0 = P32, *b0 = P32 + E1, *b1 = P32 + 2 * E1 + E1 * E2, *b2 = b1 + E2 + E2 * E3;
             for (int t0 = 0; t0 < G && alive; t0 += 4) {
+                // split operands: B1 shares its region with the layer-2 operands of the last tile
+                if constexpr (SPLIT) copy16(B1, mx.emb_ops + mx.emb_off[net][0], X * S::B1B);
                 const int g = t0 + warp;
                 const bool warp_live = g < G;
                 const int j = warp_live ? bi.grp_atom[g] : 0;
@@ -1041,17 +1082,15 @@ template <int E1, bool SPLIT>
 size_t fwd_smem()
 {
     using S = EmbShape<E1>;
-    constexpr int X = SPLIT ? 2 : 1;
-    return X * (S::A0B + S::A1B + S::B1B + S::B2B) + sizeof(double) * (4 * 4 * S::E3 + AB * 4 * S::E3) +
-           sizeof(float) * (4 * 32 * 17 + 2 * 4 * 32 * 4);
+    using P = EmbPlan<E1, SPLIT>;
+    return P::FEND + sizeof(double) * (4 * 4 * S::E3 + P::AB * 4 * S::E3) + sizeof(float) * (4 * 32 * 17 + 2 * 4 * 32 * 4);
 }
 template <int E1, bool SPLIT>
 size_t bwd_smem()
 {
     using S = EmbShape<E1>;
-    constexpr int X = SPLIT ? 2 : 1;
-    return X * (2 * S::A0B + 2 * S::A1B + S::B1B + S::B2B) + sizeof(double) * (4 * S::E3 + 48 + AB * 12) +
-           sizeof(float) * 2 * AB * 4 * S::E3;
+    using P = EmbPlan<E1, SPLIT>;
+    return P::BEND + sizeof(double) * (4 * S::E3 + 48 + P::AB * 12) + sizeof(float) * 2 * P::AB * 4 * S::E3;
 }
 
 // CTAs per SM that fit next to each other (shared memory; a 1 KB reserve per CTA)

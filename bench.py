@@ -60,6 +60,12 @@ WORKLOADS = {
 # FP64 pipe peak of a GB300: 152 SMs x 2 FP64 FMA/clk/SM x 2 FLOP x 2.07 GHz.
 # The per-SM rate is the one that reproduces the nominal 1.25 TFLOP/s.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# FP32 pipe peak: 152 SMs x 128 FMA/clk/SM x 2 FLOP x 2.07 GHz (nominal).
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# FP32 instructions per multiply-add of the mixed kernels' double-float
+# contractions (mixed.cu df_fma: 2 multiplies/FMAs for the exact product, 6
+# adds for the two-sum, 2 for the error terms)
+DF_FP32_INST_PER_FMA = 10
 FORCE_RMSE_TARGET = 1e-3   # eV/A, against the FP64 full model
 
 # Per-kernel counters from one ncu capture, reported only while the kernel
@@ -70,7 +76,19 @@ FORCE_RMSE_TARGET = 1e-3   # eV/A, against the FP64 full model
 #                     per real neighbour row
 TRAFFIC = {
     "embed_bwd": {"bytes_per_launch": 206.925056e6 + 21.675264e6, "file": "embed_x.cu", "src_sha": "4954f89e6792262d"},
-    "embed_bwd_mx<25>": {"bytes_per_launch": 204.77056e6 + 17.105152e6, "file": "mixed.cu", "src_sha": "1bc49a405925719e"},
+    "embed_bwd_mx<25>": {"bytes_per_launch": 204.772096e6 + 16.526848e6, "file": "mixed.cu", "src_sha": "8933a8cc793ba857"},
+    "embed_bwd_mx<25, split>": {"bytes_per_launch": 204.763904e6 + 17.992704e6, "file": "mixed.cu",
+                                "src_sha": "8933a8cc793ba857"},
+}
+# Pipe shares of the mixed embedding kernels (ncu, one evaluation of the
+# 12,288-atom water box, --profile-precision mixed / split): active-cycle
+# busy fractions of the FP64, FP32 (fma), integer (alu) and tensor pipes and
+# the schedulers' issue-active share.
+MODE_PIPES = {
+    "embed_bwd_mx<25>": {"fp64": 0.480, "fma": 0.190, "alu": 0.085, "tensor": 0.010, "issue_active": 0.311,
+                         "file": "mixed.cu", "src_sha": "8933a8cc793ba857"},
+    "embed_bwd_mx<25, split>": {"fp64": 0.448, "fma": 0.180, "alu": 0.094, "tensor": 0.028, "issue_active": 0.302,
+                                "file": "mixed.cu", "src_sha": "8933a8cc793ba857"},
 }
 FP64_ISSUED = {
     # ncu on one evaluation of the 12,288-atom water box (bench.py --workload
@@ -331,13 +349,15 @@ def run_reference(args, rank, world):
 
 def mixed_kernel_flops(desc, rows, natoms):
     """Per-launch work of the mixed-precision kernels, split by unit:
-    tensor-core FLOPs (BF16 GEMMs, unpadded) and FP64 FLOPs (contractions)."""
+    tensor-core FLOPs (BF16 GEMMs, unpadded), the per-row contractions with
+    R~ and dE/dT (double-float arithmetic on the FP32 pipe) and the per-atom
+    FP64 FLOPs (D = T_<^T T forward, dE/dT backward)."""
     M, m2 = desc["emb"][-1], desc["m2"]
     g = emb_row_flops(desc) - 2 * desc["emb"][0]   # layer 0 runs on the CUDA cores
     return {
-        "embed_fwd": {"tensor": rows * g, "fp64": rows * 8 * M + natoms * 8 * m2 * M},
-        "embed_bwd": {"tensor": rows * 2 * g, "fp64": rows * 16 * M + natoms * 16 * m2 * M},
-        "fit": {"tensor": natoms * 2 * fit_atom_flops(desc), "fp64": 0},
+        "embed_fwd": {"tensor": rows * g, "df": rows * 8 * M, "fp64": natoms * 8 * m2 * M},
+        "embed_bwd": {"tensor": rows * 2 * g, "df": rows * 16 * M, "fp64": natoms * 16 * m2 * M},
+        "fit": {"tensor": natoms * 2 * fit_atom_flops(desc), "df": 0, "fp64": 0},
     }
 
 
@@ -372,21 +392,39 @@ def _accuracy(dp, ctx, refc, x, t, box):
 
 
 def _mode_roofline(fl, groups, dom, tag, traffic):
+    """Roofline of a mode's dominant kernel by unit: BF16 tensor FLOPs, the
+    double-float contractions as FP32 instructions issued (an estimate from
+    the instruction count per multiply-add) and the per-atom FP64 FLOPs; the
+    top-level entry is the busiest of the three."""
     sec = groups[dom]["ms"] / groups[dom]["launches"] / 1000.0
     pk = measured_peaks()
     bf16_peak = pk.get("bf16_tflops_sustained", pk.get("bf16_tflops", 1720.9))
     ach_t = fl[dom]["tensor"] / sec / 1e12
+    ach_c = fl[dom]["df"] / sec / 1e12
+    ach_f32 = ach_c / 2 * DF_FP32_INST_PER_FMA * 2   # FP32 FLOP-equivalents (an instruction counts 2)
     ach_d = fl[dom]["fp64"] / sec / 1e12
-    ft, fd = ach_t / bf16_peak, ach_d / FP64_PEAK_TFLOPS
-    return {"bound": "alu" if fd >= ft else "tensor", "kernel": tag,
-            "achieved": ach_d if fd >= ft else ach_t,
-            "peak": FP64_PEAK_TFLOPS if fd >= ft else bf16_peak, "unit": "TFLOP/s",
-            "frac": max(fd, ft), "traffic": traffic,
-            "fp64": {"achieved": ach_d, "peak": FP64_PEAK_TFLOPS, "frac": fd,
-                     "what": "algorithmic FP64 FLOPs (T = R~^T G / N_m, D and their backward)"},
-            "tensor_bf16": {"achieved": ach_t, "peak": bf16_peak, "frac": ft,
-                            "what": "algorithmic BF16 GEMM FLOPs (unpadded)",
-                            "peak_source": "MEASURED_PEAKS bf16_tflops_sustained (of measured)"}}
+    units = {
+        "tensor_bf16": {"achieved": ach_t, "peak": bf16_peak, "frac": ach_t / bf16_peak,
+                        "what": "algorithmic BF16 GEMM FLOPs (unpadded)",
+                        "peak_source": "MEASURED_PEAKS bf16_tflops_sustained (of measured)"},
+        "fp32_double_float": {"achieved": ach_f32, "peak": FP32_PEAK_TFLOPS, "frac": ach_f32 / FP32_PEAK_TFLOPS,
+                              "contraction_tflops": ach_c,
+                              "what": "the contractions with R~ and dE/dT (algorithmic contraction_tflops) in "
+                                      "double-float arithmetic, as FP32 pipe work: %d FP32 instructions per "
+                                      "multiply-add, 2 FLOP each (estimate)" % DF_FP32_INST_PER_FMA,
+                              "peak_source": "152 SMs x 128 FMA/clk x 2 x 2.07 GHz (nominal)"},
+        "fp64": {"achieved": ach_d, "peak": FP64_PEAK_TFLOPS, "frac": ach_d / FP64_PEAK_TFLOPS,
+                 "what": "algorithmic per-atom FP64 FLOPs (D = T_<^T T, dE/dT)"},
+    }
+    top = max(units, key=lambda u: units[u]["frac"])
+    out = {"bound": "tensor" if top == "tensor_bf16" else "alu", "kernel": tag, "unit": "TFLOP/s",
+           "achieved": units[top]["achieved"], "peak": units[top]["peak"], "frac": units[top]["frac"],
+           "traffic": traffic}
+    out.update(units)
+    pipes = _counter(MODE_PIPES, tag)
+    if pipes:
+        out["pipes_ncu"] = {k: v for k, v in pipes.items() if k not in ("file", "src_sha")}
+    return out
 
 
 def measure_mode(args, dp, w, run_desc, run_P, ref_model, v0, dev, world, flush, dtype, fast_path=False,
@@ -473,7 +511,7 @@ def measure_mode(args, dp, w, run_desc, run_P, ref_model, v0, dev, world, flush,
     dom = max(groups, key=lambda g: groups[g]["ms"])
     roof = None
     if dom in fl:
-        tag = f"{dom}_mx<{run_desc['emb'][0]}>"
+        tag = f"{dom}_mx<{run_desc['emb'][0]}" + (", split>" if prec == dp.DP_PREC_MIXED_SPLIT else ">")
         tr = _counter(TRAFFIC, tag)
         roof = _mode_roofline(fl, groups, dom, tag, tr["bytes_per_launch"] if tr else None)
     out = {"value": world * N * wl["md_per_step"] * args.steps / (total_ms / 1000.0), "unit": METRIC,

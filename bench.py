@@ -139,16 +139,25 @@ def fit_atom_flops(desc):
     return f + 2 * prev
 
 
-def kernel_flops(desc, rows, natoms):
+def kernel_flops(desc, rows, natoms, store=False):
     """FLOPs per launch of each kernel group, counted from the algorithm
     (multiply-add = 2, tanh not counted):
       embed_fwd: embedding GEMMs per real row + T = R~^T G (8 M per row)
                  + D = T_<^T T (8 M2 M per atom)
       embed_bwd: embedding recomputed + its s-tangent (2x GEMMs) + the two
                  4 x M contractions with gT (16 M per row) + gT (16 M2 M per atom)
-      fit:       fitting forward + backward to the descriptor (2x forward)."""
+      fit:       fitting forward + backward to the descriptor (2x forward).
+    store: G and dG/ds kept between the two (k_embed_tan_x, k_embed_bwd_st):
+      the forward evaluates the GEMMs with the s-tangent (2x GEMMs) + T + D,
+      the backward only the contractions and gT."""
     M, m2 = desc["emb"][-1], desc["m2"]
     g = emb_row_flops(desc)
+    if store:
+        return {
+            "embed_fwd": rows * (2 * g + 8 * M) + natoms * 8 * m2 * M,
+            "embed_bwd": rows * 16 * M + natoms * 16 * m2 * M,
+            "fit": natoms * 2 * fit_atom_flops(desc),
+        }
     return {
         "embed_fwd": rows * (g + 8 * M) + natoms * 8 * m2 * M,
         "embed_bwd": rows * (2 * g + 16 * M) + natoms * 16 * m2 * M,
@@ -538,25 +547,34 @@ def measure_mode(args, dp, w, run_desc, run_P, ref_model, v0, dev, world, flush,
 STUDENT_PARAMS = os.path.join(ROOT, "paper_2004_11658_gb300", "data", "student_water12288.npy")
 
 
-def fp64_roofline(desc, groups, dom, rows, nreal, N):
+def fp64_kernel_key(dom, store):
+    """Counter-table key of an FP64 kernel group: with the G store the
+    groups run k_embed_tan_x (embed_fwd) and k_embed_bwd_st (embed_bwd)."""
+    if store and dom in ("embed_fwd", "embed_bwd"):
+        return {"embed_fwd": "embed_tan", "embed_bwd": "embed_bwd_st"}[dom]
+    return dom
+
+
+def fp64_roofline(desc, groups, dom, rows, nreal, N, store=False):
     """Roofline of the FP64 path's dominant kernel, by unit: the FP64 pipe
     (FP64 FLOPs issued, from the kernel's ncu instruction counts per row),
     the tensor cores (digit-MMA FLOPs issued), and the algorithmic FP64
     FLOPs as an FP64-equivalent rate."""
-    flops = kernel_flops(desc, rows, N)
+    flops = kernel_flops(desc, rows, N, store)
     per_launch_s = groups[dom]["ms"] / groups[dom]["launches"] / 1000.0
     pk = measured_peaks()
     bf16_peak = pk.get("bf16_tflops_sustained", pk.get("bf16_tflops", 1720.9))
-    tr = _counter(TRAFFIC, dom)
-    issued = _counter(FP64_ISSUED, dom)
+    key = fp64_kernel_key(dom, store)
+    tr = _counter(TRAFFIC, key)
+    issued = _counter(FP64_ISSUED, key)
     equiv = flops[dom] / per_launch_s / 1e12 if dom in flops else None
-    roof = {"bound": "alu", "kernel": dom, "unit": "TFLOP/s", "traffic": tr["bytes_per_launch"] if tr else None,
+    roof = {"bound": "alu", "kernel": key, "unit": "TFLOP/s", "traffic": tr["bytes_per_launch"] if tr else None,
             "rows_per_launch": rows,
             "fp64_equivalent": {"achieved": equiv, "peak": FP64_PEAK_TFLOPS,
                                 "frac": equiv / FP64_PEAK_TFLOPS if equiv else None,
                                 "what": "algorithmic FP64 FLOPs per launch / time; part of them run on the "
                                         "tensor cores as exact digit products, so this may exceed 1"}}
-    if dom == "embed_bwd":
+    if dom == ("embed_fwd" if store else "embed_bwd"):
         mma = digit_mma_flops_bwd(desc, nreal)
         roof["tensor_bf16"] = {"achieved": mma / per_launch_s / 1e12, "peak": bf16_peak,
                                "frac": mma / per_launch_s / 1e12 / bf16_peak,
@@ -594,6 +612,7 @@ def run_ours(args, rank, world, local_rank):
     N = len(m)
     model = dp.Model(desc, P)
     ctx = dp.Context(model, N)
+    store = ctx.embed_store
     x = torch.tensor(w["coords"], dtype=torch.float64, device=dev)
     v = torch.tensor(v0, dtype=torch.float64, device=dev)
     t = torch.tensor(w["types"], dtype=torch.int32, device=dev)
@@ -661,7 +680,7 @@ def run_ours(args, rank, world, local_rank):
     groups = {g: {"ms": ms, "launches": n} for g, (ms, n) in kt.items()}
     timed_groups = {g: d for g, d in groups.items() if d["launches"] > 0}
     dom = max(timed_groups, key=lambda g: timed_groups[g]["ms"])
-    roof = fp64_roofline(desc, groups, dom, rows, nreal, N)
+    roof = fp64_roofline(desc, groups, dom, rows, nreal, N, store=store)
     th_all = torch.stack(thermo_all).cpu().numpy().reshape(-1, 4)
     etot = th_all[:, 0] + th_all[:, 1]
 

@@ -168,6 +168,24 @@ void dp_model_free(dp_model *model);
 dp_status dp_ctx_create(const dp_model *model, int64_t natoms_max, int32_t cand_cap,
                         int32_t precision, void *stream, dp_ctx **out);
 void dp_ctx_free(dp_ctx *ctx);
+
+/* FP64 contexts of the tensor-core embedding kernels (3-layer doubling nets,
+ * s_1 in {16, 25, 32}): the back-propagation of Sec. 2 (Eq. embedding through
+ * the chain rule of the environment matrix, Sec. 3.2) needs, for every real
+ * neighbour row, G and its derivative dG/ds with respect to the row's s(r).
+ * With the store on, the forward computes both once and keeps them in device
+ * memory (natoms_max * N_m * 2 * M doubles: 86.8 GB for 393,216 water atoms
+ * with N_m = 138, M = 100), and the backward reads them instead of evaluating
+ * the embedding net a second time; off, the backward recomputes them.  Both
+ * give the same energy, forces and virial up to the order of the sums over
+ * the M features.  dp_ctx_create turns the store on when it takes at most half
+ * of the device memory free at that moment.  on = 1 allocates it
+ * (DP_ERR_NOMEM if that fails, the context unchanged), on = 0 frees it;
+ * DP_ERR_UNSUPPORTED for other contexts when on = 1.  Synchronises the
+ * context's stream.  dp_ctx_embed_store returns 1 when the store is on, 0
+ * when off, -1 for NULL. */
+dp_status dp_ctx_set_embed_store(dp_ctx *ctx, int32_t on);
+int32_t dp_ctx_embed_store(const dp_ctx *ctx);
 /* sync = 1 (default): every call reads the device status word at its end.
  * sync = 0: calls only enqueue; dp_ctx_status reads the accumulated word. */
 dp_status dp_ctx_set_sync(dp_ctx *ctx, int32_t sync);

@@ -562,6 +562,9 @@ dp_status enqueue_eval(dp_ctx *c, const double *coords, const int32_t *types, co
             GroupTimer tm(c, G_EMBED_FWD);
             e = mixed       ? dp_launch_embed_fwd_mx(c->stream, c->m, c->mx, coords, types, b, n, c->fb, c->nb,
                                                      c->eb, c->num_sms, c->d_status, &c->launches)
+                : c->use_ex && c->eb.Gst
+                    ? dp_launch_embed_tan_x(c->stream, c->m, c->d_ex_w, coords, types, b, n, c->fb, c->nb, c->eb,
+                                            c->num_sms, c->d_status, &c->launches)
                 : c->use_ex ? dp_launch_embed_fwd_x(c->stream, c->m, c->d_ex_w, coords, types, b, n, c->fb, c->nb,
                                                     c->eb, c->num_sms, c->d_status, &c->launches)
                             : dp_launch_embed_fwd(c->stream, c->m, coords, types, b, n, c->fb, c->nb, c->eb,
@@ -582,6 +585,9 @@ dp_status enqueue_eval(dp_ctx *c, const double *coords, const int32_t *types, co
             GroupTimer tm(c, G_EMBED_BWD);
             e = mixed       ? dp_launch_embed_bwd_mx(c->stream, c->m, c->mx, coords, types, b, n, c->fb, c->nb,
                                                      c->eb, c->num_sms, c->d_status, &c->launches)
+                : c->use_ex && c->eb.Gst
+                    ? dp_launch_embed_bwd_st(c->stream, c->m, coords, types, b, n, c->fb, c->eb, c->num_sms,
+                                             &c->launches)
                 : c->use_ex ? dp_launch_embed_bwd_x(c->stream, c->m, c->d_ex_w, coords, types, b, n, c->fb, c->nb,
                                                     c->eb, c->num_sms, c->d_status, &c->launches)
                             : dp_launch_embed_bwd(c->stream, c->m, coords, types, b, n, c->fb, c->nb, c->eb,
@@ -908,7 +914,8 @@ void dp_ctx_free(dp_ctx *c)
                     c->d_energy, c->d_virial, c->md_force, c->ke_part, c->d_inv_mass_conv, c->d_mass,
                     c->eb.fit_t, c->eb.fit_h, c->d_p32, c->d_emb_ops, c->d_fit_fwd, c->d_fit_bwd,
                     c->pb.dT, c->pb.dD, c->pb.Db, c->pb.dDb, c->pb.fit_scr, c->pb.rowscr, c->pb.slices,
-                    c->d_oz_w, c->d_oz_e, c->ob.a, c->ob.aexp, c->ob.t, c->ob.h, c->ob.g, c->d_dtile, c->d_ex_w};
+                    c->d_oz_w, c->d_oz_e, c->ob.a, c->ob.aexp, c->ob.t, c->ob.h, c->ob.g, c->d_dtile, c->d_ex_w,
+                    c->eb.Gst};
     for (void *p : bufs) dev_free(p);
     delete c;
 }
@@ -985,6 +992,16 @@ dp_status dp_ctx_create(const dp_model *model, int64_t natoms_max, int32_t cand_
     if (precision == DP_PREC_FP64 && dp_ex_supported(c->m)) {
         ALLOC(c->d_ex_w, dp_ex_bytes(c->m));
         c->use_ex = true;
+        // G and dG/ds stored by the forward, when that takes at most half of the free memory
+        size_t fr = 0, tot = 0;
+        const size_t gb = dp_ex_store_bytes(c->m, (int64_t)N);
+        if (!s && cudaMemGetInfo(&fr, &tot) == cudaSuccess && gb <= fr / 2) {
+            if (cudaMalloc((void **)&c->eb.Gst, gb) != cudaSuccess) {
+                c->eb.Gst = nullptr;
+                cudaGetLastError();
+            }
+        }
+        cudaGetLastError();
     }
     // the split mixed mode runs its fitting net as exact products of 28-bit digit
     // expansions (FP32-level accuracy, a quarter of the FP64 plans' MMAs)
@@ -1031,6 +1048,23 @@ dp_status dp_ctx_create(const dp_model *model, int64_t natoms_max, int32_t cand_
     *out = c;
     return DP_OK;
 }
+
+dp_status dp_ctx_set_embed_store(dp_ctx *c, int32_t on)
+{
+    if (!c) return fail(DP_ERR_ARG, "context is NULL");
+    if (on && !c->use_ex) return fail(DP_ERR_UNSUPPORTED, "the store needs an FP64 context of the tensor-core "
+                                                          "embedding kernels");
+    if ((on != 0) == (c->eb.Gst != nullptr)) return DP_OK;
+    DP_CUDA(cudaStreamSynchronize(c->stream), "dp_ctx_set_embed_store");
+    if (!on) {
+        dev_free(c->eb.Gst);
+        c->eb.Gst = nullptr;
+        return DP_OK;
+    }
+    return dev_alloc(&c->eb.Gst, dp_ex_store_bytes(c->m, c->natoms_max) / sizeof(double), "G and dG/ds rows");
+}
+
+int32_t dp_ctx_embed_store(const dp_ctx *c) { return c ? (c->eb.Gst != nullptr ? 1 : 0) : -1; }
 
 dp_status dp_ctx_set_sync(dp_ctx *c, int32_t sync)
 {

@@ -193,6 +193,7 @@ struct EvalBuffers {
     double *vir_part;  // [N][9]
     float *fit_t;      // mixed mode: tanh values of the fitting layers [tile][n_fit][256][128]
     float *fit_h;      // mixed mode: fitting activation / gradient [tile][256][128]
+    double *Gst;       // FP64 mode, when it fits: G and dG/ds of every neighbour slot [N nm][2 M]
 };
 
 // Mixed-precision operands: BF16 copies of the weight matrices in the
@@ -292,6 +293,16 @@ cudaError_t dp_launch_embed_bwd_x(cudaStream_t st, const DevModel &m, const unsi
                                   const int32_t *types, Box3 box, int N, const FormatBuffers &fb,
                                   const NlistBuffers &nb, EvalBuffers eb, int num_sms, int32_t *status,
                                   int64_t *launches);
+// The same forward with the s-tangent, G and dG/ds stored in eb.Gst (bytes for
+// natoms atoms: dp_ex_store_bytes), and the streaming backward that reads them.
+size_t dp_ex_store_bytes(const DevModel &m, int64_t natoms);
+cudaError_t dp_launch_embed_tan_x(cudaStream_t st, const DevModel &m, const unsigned char *wx, const double *x,
+                                  const int32_t *types, Box3 box, int N, const FormatBuffers &fb,
+                                  const NlistBuffers &nb, EvalBuffers eb, int num_sms, int32_t *status,
+                                  int64_t *launches);
+cudaError_t dp_launch_embed_bwd_st(cudaStream_t st, const DevModel &m, const double *x, const int32_t *types,
+                                   Box3 box, int N, const FormatBuffers &fb, EvalBuffers eb, int num_sms,
+                                   int64_t *launches);
 
 // Mixed precision (BF16 tensor-core GEMMs, FP64 environment / contractions).
 cudaError_t dp_launch_embed_fwd_mx(cudaStream_t st, const DevModel &m, const MixedModel &mx, const double *x,

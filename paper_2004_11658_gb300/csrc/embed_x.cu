@@ -580,16 +580,22 @@ struct XBShape {
     static_assert(SMEM + 1024 <= 232448, "dynamic plus static shared memory above the 227 KB opt-in limit");
 };
 
-template <int E1>
-__global__ void __launch_bounds__(XTB, 1) k_embed_bwd_x(DevModel m, const unsigned char *__restrict__ wx,
-                                                       const double *__restrict__ x,
-                                                       const int32_t *__restrict__ types, Box3 box, int N,
-                                                       const int32_t *__restrict__ type_perm,
-                                                       const int32_t *__restrict__ nlist,
-                                                       const int32_t *__restrict__ nreal,
-                                                       const double *__restrict__ Tin, const double *__restrict__ gD,
-                                                       double *__restrict__ pair_g, double *__restrict__ f_own,
-                                                       double *__restrict__ vir_part, int32_t *status)
+// TAN = false: the backward (k_embed_bwd_x).  TAN = true: the forward with the
+// s-tangent (k_embed_tan_x): the same value and tangent products, but instead of
+// contracting G and dG/ds with dE/dT (not known yet) the epilogue stores both
+// rows in HBM (Gst: [N nm][2 M], slot i nm + sel_off[b] + r, G then dG/ds) and
+// accumulates T = R~^T G; the atom's T and D = T_<^T T leave as in k_embed_fwd_x.
+template <int E1, bool TAN>
+__device__ __forceinline__ void embed_tangent_body(const DevModel &m, const unsigned char *__restrict__ wx,
+                                                   const double *__restrict__ x,
+                                                   const int32_t *__restrict__ types, Box3 box, int N,
+                                                   const int32_t *__restrict__ type_perm,
+                                                   const int32_t *__restrict__ nlist,
+                                                   const int32_t *__restrict__ nreal, double *__restrict__ Tio,
+                                                   const double *__restrict__ gD, double *__restrict__ pair_g,
+                                                   double *__restrict__ f_own, double *__restrict__ vir_part,
+                                                   double *__restrict__ Dout, double *__restrict__ Gst,
+                                                   int32_t *status)
 {
     using X = XBShape<E1>;
     constexpr int E2 = X::E2, E3 = X::E3, K2p = X::K2p, K1p = X::K1p, LD0 = X::LD0, LD1 = X::LD1, GR = X::GR,
@@ -760,9 +766,9 @@ __global__ void __launch_bounds__(XTB, 1) k_embed_bwd_x(DevModel m, const unsign
         const int a = types[i];
         const double xi[3] = {x[3 * i], x[3 * i + 1], x[3 * i + 2]};
         // gT[c][x] = scale ([x < M2] sum_b gD[x][b] T[c][b] + sum_{a<M2} gD[a][x] T[c][a])
-        {
+        if constexpr (!TAN) {
             double *Ts = H1;  // T of this atom, [4][E3]
-            for (int p = tid; p < 4 * E3; p += XTB) Ts[p] = Tin[(size_t)i * 4 * E3 + p];
+            for (int p = tid; p < 4 * E3; p += XTB) Ts[p] = Tio[(size_t)i * 4 * E3 + p];
             __syncthreads();
             const double *g = gD + (size_t)i * m2 * E3;
             for (int p = tid; p < 4 * E3; p += XTB) {
@@ -775,11 +781,15 @@ __global__ void __launch_bounds__(XTB, 1) k_embed_bwd_x(DevModel m, const unsign
             }
             __syncthreads();
         }
-        double gt[4], gtp[4];  // dE/dT of this thread's feature, and of lane ^ 16's
+        double gt[4] = {0.0, 0.0, 0.0, 0.0}, gtp[4] = {0.0, 0.0, 0.0, 0.0};  // dE/dT of this thread's
+                                                                            // feature, and of lane ^ 16's
+        if constexpr (!TAN) {
 #pragma unroll
-        for (int c = 0; c < 4; ++c) gt[c] = f < E3 ? gTs[c * XM + f] : 0.0;
+            for (int c = 0; c < 4; ++c) gt[c] = f < E3 ? gTs[c * XM + f] : 0.0;
 #pragma unroll
-        for (int c = 0; c < 4; ++c) gtp[c] = __shfl_xor_sync(0xffffffffu, gt[c], 16);
+            for (int c = 0; c < 4; ++c) gtp[c] = __shfl_xor_sync(0xffffffffu, gt[c], 16);
+        }
+        double tacc[4] = {0.0, 0.0, 0.0, 0.0};  // TAN: this thread's column of T over its rows
         double fo[3] = {0.0, 0.0, 0.0}, vir[9];
 #pragma unroll
         for (int q = 0; q < 9; ++q) vir[q] = 0.0;
@@ -978,6 +988,64 @@ __global__ void __launch_bounds__(XTB, 1) k_embed_bwd_x(DevModel m, const unsign
                 combine_groups_8(tlane + 256 + XRB * grp, yt, fx - XBETA * (XS + 1), erow + XRB * grp);
                 const double bf = f < E3 ? b2s[f] : 0.0;
                 const int fs = f < E2 ? f : (f < E3 ? f - E2 : 0);
+                if constexpr (TAN) {
+                // G and dG/ds of the chunk's rows to HBM, this thread's column of T over its rows
+                double *gro = Gst + ((size_t)i * nm + m.sel_off[b] + c0) * (2 * E3);
+                const int nq = E3 - 32 * (warp & 3);  // real features of this warp's TMEM quarter
+                static_assert(XRB == 8, "the sparse-quarter path maps 4 features x 8 rows to the lanes");
+                if (nq > 0 && nq <= 32 / XRB) {
+                    // at most 4 real features: one (feature, row) item per lane (feature L / 8 of the
+                    // quarter, row L % 8), as in the backward
+                    const int fi = lane >> 3, r = lane & 7;
+                    double ys = 0.0, ts = 0.0;
+#pragma unroll
+                    for (int k = 0; k < XRB; ++k) {
+                        const double a = __shfl_sync(0xffffffffu, yv[k], fi);
+                        const double b = __shfl_sync(0xffffffffu, yt[k], fi);
+                        if (k == r) {
+                            ys = a;
+                            ts = b;
+                        }
+                    }
+                    const int fq = 32 * (warp & 3) + fi, q = XRB * grp + r;
+                    double pc[4] = {0.0, 0.0, 0.0, 0.0};
+                    if (fi < nq && q < nv) {
+                        const int fsq = fq < E2 ? fq : fq - E2;
+                        const double t = dp_tanh64(ys + b2s[fq], m.tanh_tab);
+                        const double G = H1[q * LD1 + fsq] + t;
+                        const double dG = fma(fma(-t, t, 1.0), ts, dH1[q * LD1 + fsq]);
+                        gro[(size_t)q * (2 * E3) + fq] = G;
+                        gro[(size_t)q * (2 * E3) + E3 + fq] = dG;
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) pc[c] = gc[q * GS + 2 + c] * G;
+                    }
+                    // sum over the 8 rows (lanes 8 fi .. 8 fi + 7); lane fi, which owns feature fq's
+                    // column of T, adds it
+#pragma unroll
+                    for (int o = 1; o < 8; o <<= 1)
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) pc[c] += __shfl_xor_sync(0xffffffffu, pc[c], o);
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        const double v = __shfl_sync(0xffffffffu, pc[c], 8 * (lane & 3));
+                        if (lane < nq) tacc[c] += v;
+                    }
+                } else if (nq > 0 && f < E3) {
+#pragma unroll
+                    for (int qq = 0; qq < XRB; ++qq) {
+                        const int q = XRB * grp + qq;
+                        if (q < nv) {
+                            const double t = dp_tanh64(yv[qq] + bf, m.tanh_tab);
+                            const double G = H1[q * LD1 + fs] + t;
+                            const double dG = fma(fma(-t, t, 1.0), yt[qq], dH1[q * LD1 + fs]);
+                            gro[(size_t)q * (2 * E3) + f] = G;
+                            gro[(size_t)q * (2 * E3) + E3 + f] = dG;
+#pragma unroll
+                            for (int c = 0; c < 4; ++c) tacc[c] = fma(gc[q * GS + 2 + c], G, tacc[c]);
+                        }
+                    }
+                }
+                } else {
                 double *rw = red + (warp * XRB) * 8;  // this warp's [XRB rows][8]
                 const int nq = E3 - 32 * (warp & 3);  // real features of this warp's TMEM quarter
                 static_assert(XRB == 8, "the sparse-quarter path maps 4 features x 8 rows to the lanes");
@@ -1125,13 +1193,44 @@ __global__ void __launch_bounds__(XTB, 1) k_embed_bwd_x(DevModel m, const unsign
                         for (int bb = 0; bb < 3; ++bb) vir[aa * 3 + bb] -= gd[aa] * gv[bb];
                     }
                 }
+                }
                 tc::fence_before_sync();
                 __syncthreads();
                 tc::fence_after_sync();
             }
         }
         if (!alive) break;
-        if (warp == 0) {
+        if constexpr (TAN) {
+            // T (the four row groups' partials summed in group order, scaled) and D = T_<^T T,
+            // as k_embed_fwd_x; the partials go through the h1 / dh1 rows
+            double *Tsm = H1;
+            if (grp > 0 && f < E3) {
+#pragma unroll
+                for (int c = 0; c < 4; ++c) Tsm[4 * XM * grp + c * E3 + f] = tacc[c];
+            }
+            __syncthreads();
+            if (grp == 0 && f < E3) {
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    double v = tacc[c];
+#pragma unroll
+                    for (int g = 1; g < XTB / XM; ++g) v += Tsm[4 * XM * g + c * E3 + f];
+                    v *= m.desc_scale;
+                    Tsm[c * E3 + f] = v;
+                    Tio[(size_t)i * 4 * E3 + c * E3 + f] = v;
+                }
+            }
+            __syncthreads();
+            const int nd = m2 * E3;
+            for (int q = tid; q < nd; q += XTB) {
+                const int a2 = q / E3, b2 = q - a2 * E3;
+                double acc = Tsm[a2] * Tsm[b2];
+                acc = fma(Tsm[E3 + a2], Tsm[E3 + b2], acc);
+                acc = fma(Tsm[2 * E3 + a2], Tsm[2 * E3 + b2], acc);
+                acc = fma(Tsm[3 * E3 + a2], Tsm[3 * E3 + b2], acc);
+                Dout[(size_t)i * nd + q] = acc;
+            }
+        } else if (warp == 0) {
 #pragma unroll
             for (int off = 16; off > 0; off >>= 1) {
 #pragma unroll
@@ -1156,23 +1255,233 @@ __global__ void __launch_bounds__(XTB, 1) k_embed_bwd_x(DevModel m, const unsign
 }
 
 template <int E1>
-cudaError_t launch_bwd_x(cudaStream_t st, const DevModel &m, const unsigned char *wx, const double *x,
-                         const int32_t *types, Box3 box, int N, const FormatBuffers &fb, const NlistBuffers &nb,
-                         EvalBuffers eb, int num_sms, int32_t *status)
+__global__ void __launch_bounds__(XTB, 1) k_embed_bwd_x(DevModel m, const unsigned char *__restrict__ wx,
+                                                       const double *__restrict__ x,
+                                                       const int32_t *__restrict__ types, Box3 box, int N,
+                                                       const int32_t *__restrict__ type_perm,
+                                                       const int32_t *__restrict__ nlist,
+                                                       const int32_t *__restrict__ nreal, double *__restrict__ Tin,
+                                                       const double *__restrict__ gD, double *__restrict__ pair_g,
+                                                       double *__restrict__ f_own, double *__restrict__ vir_part,
+                                                       int32_t *status)
+{
+    embed_tangent_body<E1, false>(m, wx, x, types, box, N, type_perm, nlist, nreal, Tin, gD, pair_g, f_own,
+                                  vir_part, nullptr, nullptr, status);
+}
+
+template <int E1>
+__global__ void __launch_bounds__(XTB, 1) k_embed_tan_x(DevModel m, const unsigned char *__restrict__ wx,
+                                                       const double *__restrict__ x,
+                                                       const int32_t *__restrict__ types, Box3 box, int N,
+                                                       const int32_t *__restrict__ type_perm,
+                                                       const int32_t *__restrict__ nlist,
+                                                       const int32_t *__restrict__ nreal, double *__restrict__ Tout,
+                                                       double *__restrict__ Dout, double *__restrict__ Gst,
+                                                       int32_t *status)
+{
+    embed_tangent_body<E1, true>(m, wx, x, types, box, N, type_perm, nlist, nreal, Tout, nullptr, nullptr, nullptr,
+                                 nullptr, Dout, Gst, status);
+}
+
+template <int E1, bool TAN>
+cudaError_t launch_tangent_x(cudaStream_t st, const DevModel &m, const unsigned char *wx, const double *x,
+                             const int32_t *types, Box3 box, int N, const FormatBuffers &fb, const NlistBuffers &nb,
+                             EvalBuffers eb, int num_sms, int32_t *status)
 {
     using X = XBShape<E1>;
     static bool configured = false;
     if (!configured) {
-        cudaError_t e =
-            cudaFuncSetAttribute(k_embed_bwd_x<E1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)X::SMEM);
+        cudaError_t e;
+        if constexpr (TAN)
+            e = cudaFuncSetAttribute(k_embed_tan_x<E1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)X::SMEM);
+        else
+            e = cudaFuncSetAttribute(k_embed_bwd_x<E1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)X::SMEM);
         if (e != cudaSuccess) return e;
         configured = true;
     }
     int grid = num_sms;
     if (grid > N) grid = N;
     if (grid < 1) grid = 1;
-    k_embed_bwd_x<E1><<<grid, XTB, X::SMEM, st>>>(m, wx, x, types, box, N, nb.type_perm, fb.nlist, fb.nreal, eb.T,
-                                                 eb.gD, eb.pair_g, eb.f_own, eb.vir_part, status);
+    if constexpr (TAN)
+        k_embed_tan_x<E1><<<grid, XTB, X::SMEM, st>>>(m, wx, x, types, box, N, nb.type_perm, fb.nlist, fb.nreal,
+                                                     eb.T, eb.D, eb.Gst, status);
+    else
+        k_embed_bwd_x<E1><<<grid, XTB, X::SMEM, st>>>(m, wx, x, types, box, N, nb.type_perm, fb.nlist, fb.nreal,
+                                                     eb.T, eb.gD, eb.pair_g, eb.f_own, eb.vir_part, status);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------ streaming backward --
+//
+// k_embed_bwd_st: the backward once k_embed_tan_x has stored G and dG/ds of
+// every real row, so nothing of the embedding net is recomputed.  One warp per
+// atom: dE/dT of the atom (as k_embed_bwd_x computes it) into shared memory,
+// then the atom's real rows (its type blocks one after the other) 32 at a
+// time: lane q takes the geometry of row q; in 8 steps of 4 rows, 8 lanes per
+// row form sa[c] = sum_f G[f] gT[c][f] and sa[4 + c] = sum_f dG[f] gT[c][f]
+// (lane u of the 8 over the features u, u + 8, ...), summed over the 8 lanes by
+// a transposing shuffle tree (7 adds; lane u ends with component u); lane q
+// then applies the chain rule through R~(r_ij) to its row: pair gradient, and
+// the atom's own force and virial parts.  Every sum runs in a fixed order: the
+// results are bit-reproducible.
+constexpr int STW = 4;  // warps (atoms in flight) per CTA
+
+template <int E1>
+__global__ void __launch_bounds__(STW * 32, 4) k_embed_bwd_st(DevModel m, const double *__restrict__ x,
+                                                             const int32_t *__restrict__ types, Box3 box, int N,
+                                                             const int32_t *__restrict__ nlist,
+                                                             const int32_t *__restrict__ nreal,
+                                                             const double *__restrict__ Tin,
+                                                             const double *__restrict__ gD,
+                                                             const double *__restrict__ Gst,
+                                                             double *__restrict__ pair_g, double *__restrict__ f_own,
+                                                             double *__restrict__ vir_part)
+{
+    constexpr int E3 = 4 * E1, KF = (E3 + 7) / 8;
+    static_assert(4 * E3 >= 32 * 8, "the row sums [32][8] fit in the T buffer");
+    __shared__ double Tsh[STW][4 * E3];  // T of the warp's atom, then the row sums [32][8]
+    __shared__ double gTsh[STW][4 * E3];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int sub = lane & 7, gq = lane >> 3;
+    const int T = m.ntypes, nm = m.nm, m2 = m.m2;
+    double *Ts = Tsh[w], *sa_s = Tsh[w];
+    double *gTw = gTsh[w];
+
+    for (int i = blockIdx.x * STW + w; i < N; i += gridDim.x * STW) {
+        const int a = types[i];
+        const bool a_ok = (unsigned)a < (unsigned)T;
+        // gT[c][x] = scale ([x < M2] sum_b gD[x][b] T[c][b] + sum_{a<M2} gD[a][x] T[c][a])
+        for (int p = lane; p < 4 * E3; p += 32) Ts[p] = Tin[(size_t)i * 4 * E3 + p];
+        __syncwarp();
+        {
+            const double *g = gD + (size_t)i * m2 * E3;
+            for (int p = lane; p < 4 * E3; p += 32) {
+                const int cc = p / E3, xx = p - cc * E3;
+                double acc = 0.0;
+                if (xx < m2)
+                    for (int b2 = 0; b2 < E3; ++b2) acc = fma(g[xx * E3 + b2], Ts[cc * E3 + b2], acc);
+                for (int a2 = 0; a2 < m2; ++a2) acc = fma(g[a2 * E3 + xx], Ts[cc * E3 + a2], acc);
+                gTw[p] = acc * m.desc_scale;
+            }
+        }
+        __syncwarp();
+        int nr = 0;
+        if (a_ok)
+            for (int b = 0; b < T; ++b) nr += nreal[(size_t)i * T + b];
+        const double xi[3] = {x[3 * i], x[3 * i + 1], x[3 * i + 2]};
+        double fo[3] = {0.0, 0.0, 0.0}, vir[9];
+#pragma unroll
+        for (int q = 0; q < 9; ++q) vir[q] = 0.0;
+        for (int q0 = 0; q0 < nr; q0 += 32) {
+            // row q0 + lane: its slot (type block and rank) and geometry
+            int slot = -1;
+            if (q0 + lane < nr) {
+                int rem = q0 + lane;
+                for (int b = 0; b < T; ++b) {
+                    const int nb = nreal[(size_t)i * T + b];
+                    if (slot < 0 && rem < nb) slot = m.sel_off[b] + rem;
+                    rem -= nb;
+                }
+            }
+            double s = 0.0, ds = 0.0, d[3] = {0.0, 0.0, 0.0}, rr = 1.0;
+            if (slot >= 0) {
+                const int j = nlist[(size_t)i * nm + slot];
+                const double xj[3] = {x[3 * j], x[3 * j + 1], x[3 * j + 2]};
+                rr = dp_pinned_dist(xi, xj, box, d);
+                dp_switch(rr, m.rcut_smth, m.rcut, s, ds);
+            }
+            // the 8 sums of rows q0 + 4 it + gq, 8 lanes per row
+            for (int it = 0; it < 8 && q0 + 4 * it < nr; ++it) {
+                const int sl = __shfl_sync(0xffffffffu, slot, 4 * it + gq);
+                double p[8];
+#pragma unroll
+                for (int c = 0; c < 8; ++c) p[c] = 0.0;
+                if (sl >= 0) {
+                    const double *gr = Gst + ((size_t)i * nm + sl) * (2 * E3);
+#pragma unroll
+                    for (int k = 0; k < KF; ++k) {
+                        const int ff = sub + 8 * k;
+                        if (8 * k + 8 <= E3 || ff < E3) {
+                            const double G = gr[ff], dG = gr[E3 + ff];
+#pragma unroll
+                            for (int c = 0; c < 4; ++c) {
+                                const double gt = gTw[c * E3 + ff];
+                                p[c] = fma(G, gt, p[c]);
+                                p[4 + c] = fma(dG, gt, p[4 + c]);
+                            }
+                        }
+                    }
+                }
+                // transposing tree over the row's 8 lanes: lane u ends with component u
+#pragma unroll
+                for (int o = 4, n = 4; o >= 1; o >>= 1, n >>= 1) {
+                    const bool up = (sub & o) != 0;
+#pragma unroll
+                    for (int k = 0; k < n; ++k) {
+                        const double send = up ? p[k] : p[n + k];
+                        const double keep = up ? p[n + k] : p[k];
+                        p[k] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+                    }
+                }
+                sa_s[(4 * it + gq) * 8 + sub] = p[0];
+            }
+            __syncwarp();
+            // chain rule through R~(r_ij), lane q on row q0 + q
+            if (slot >= 0) {
+                double sa[8];
+#pragma unroll
+                for (int c = 0; c < 8; ++c) sa[c] = sa_s[lane * 8 + c];
+                const double inv = 1.0 / rr;
+                const double R[4] = {s, s * d[0] * inv, s * d[1] * inv, s * d[2] * inv};
+                double gR0 = sa[0];
+#pragma unroll
+                for (int c = 0; c < 4; ++c) gR0 = fma(R[c], sa[4 + c], gR0);
+                const double u[3] = {d[0] * inv, d[1] * inv, d[2] * inv};
+                const double dot = sa[1] * u[0] + sa[2] * u[1] + sa[3] * u[2];
+                const double sr = s * inv;
+                const double coef = gR0 * ds + ds * dot - sr * dot;
+                double gv[3];
+#pragma unroll
+                for (int bb = 0; bb < 3; ++bb) gv[bb] = fma(u[bb], coef, sr * sa[1 + bb]);
+                double *pg = pair_g + ((size_t)i * nm + slot) * 3;
+                pg[0] = gv[0];
+                pg[1] = gv[1];
+                pg[2] = gv[2];
+#pragma unroll
+                for (int aa = 0; aa < 3; ++aa) {
+                    fo[aa] += gv[aa];
+#pragma unroll
+                    for (int bb = 0; bb < 3; ++bb) vir[aa * 3 + bb] -= d[aa] * gv[bb];
+                }
+            }
+            __syncwarp();
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+#pragma unroll
+            for (int q = 0; q < 3; ++q) fo[q] += __shfl_xor_sync(0xffffffffu, fo[q], off);
+#pragma unroll
+            for (int q = 0; q < 9; ++q) vir[q] += __shfl_xor_sync(0xffffffffu, vir[q], off);
+        }
+        if (lane == 0) {
+#pragma unroll
+            for (int q = 0; q < 3; ++q) f_own[(size_t)i * 3 + q] = fo[q];
+#pragma unroll
+            for (int q = 0; q < 9; ++q) vir_part[(size_t)i * 9 + q] = vir[q];
+        }
+        __syncwarp();
+    }
+}
+
+template <int E1>
+cudaError_t launch_bwd_st(cudaStream_t st, const DevModel &m, const double *x, const int32_t *types, Box3 box,
+                          int N, const FormatBuffers &fb, EvalBuffers eb, int num_sms)
+{
+    int grid = (N + STW - 1) / STW;
+    if (grid > 4 * num_sms) grid = 4 * num_sms;
+    if (grid < 1) grid = 1;
+    k_embed_bwd_st<E1><<<grid, STW * 32, 0, st>>>(m, x, types, box, N, fb.nlist, fb.nreal, eb.T, eb.gD, eb.Gst,
+                                                  eb.pair_g, eb.f_own, eb.vir_part);
     return cudaGetLastError();
 }
 
@@ -1244,9 +1553,9 @@ cudaError_t dp_launch_embed_bwd_x(cudaStream_t st, const DevModel &m, const unsi
 {
     *launches += 1;
     switch (m.emb[0]) {
-    case 16: return launch_bwd_x<16>(st, m, wx, x, types, box, N, fb, nb, eb, num_sms, status);
-    case 25: return launch_bwd_x<25>(st, m, wx, x, types, box, N, fb, nb, eb, num_sms, status);
-    case 32: return launch_bwd_x<32>(st, m, wx, x, types, box, N, fb, nb, eb, num_sms, status);
+    case 16: return launch_tangent_x<16, false>(st, m, wx, x, types, box, N, fb, nb, eb, num_sms, status);
+    case 25: return launch_tangent_x<25, false>(st, m, wx, x, types, box, N, fb, nb, eb, num_sms, status);
+    case 32: return launch_tangent_x<32, false>(st, m, wx, x, types, box, N, fb, nb, eb, num_sms, status);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -1261,6 +1570,38 @@ cudaError_t dp_launch_embed_fwd_x(cudaStream_t st, const DevModel &m, const unsi
     case 16: return launch_fwd_x<16>(st, m, wx, x, types, box, N, fb, nb, eb, num_sms, status);
     case 25: return launch_fwd_x<25>(st, m, wx, x, types, box, N, fb, nb, eb, num_sms, status);
     case 32: return launch_fwd_x<32>(st, m, wx, x, types, box, N, fb, nb, eb, num_sms, status);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+size_t dp_ex_store_bytes(const DevModel &m, int64_t natoms)
+{
+    return (size_t)natoms * (size_t)m.nm * 2 * (size_t)m.M * sizeof(double);
+}
+
+cudaError_t dp_launch_embed_tan_x(cudaStream_t st, const DevModel &m, const unsigned char *wx, const double *x,
+                                  const int32_t *types, Box3 box, int N, const FormatBuffers &fb,
+                                  const NlistBuffers &nb, EvalBuffers eb, int num_sms, int32_t *status,
+                                  int64_t *launches)
+{
+    *launches += 1;
+    switch (m.emb[0]) {
+    case 16: return launch_tangent_x<16, true>(st, m, wx, x, types, box, N, fb, nb, eb, num_sms, status);
+    case 25: return launch_tangent_x<25, true>(st, m, wx, x, types, box, N, fb, nb, eb, num_sms, status);
+    case 32: return launch_tangent_x<32, true>(st, m, wx, x, types, box, N, fb, nb, eb, num_sms, status);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t dp_launch_embed_bwd_st(cudaStream_t st, const DevModel &m, const double *x, const int32_t *types,
+                                   Box3 box, int N, const FormatBuffers &fb, EvalBuffers eb, int num_sms,
+                                   int64_t *launches)
+{
+    *launches += 1;
+    switch (m.emb[0]) {
+    case 16: return launch_bwd_st<16>(st, m, x, types, box, N, fb, eb, num_sms);
+    case 25: return launch_bwd_st<25>(st, m, x, types, box, N, fb, eb, num_sms);
+    case 32: return launch_bwd_st<32>(st, m, x, types, box, N, fb, eb, num_sms);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -80,6 +80,10 @@ def lib():
             L.dp_ctx_status.argtypes = [_vp]
             L.dp_ctx_launches.restype = _i64
             L.dp_ctx_launches.argtypes = [_vp]
+            L.dp_ctx_set_embed_store.restype = _i32
+            L.dp_ctx_set_embed_store.argtypes = [_vp, _i32]
+            L.dp_ctx_embed_store.restype = _i32
+            L.dp_ctx_embed_store.argtypes = [_vp]
             L.dp_build_nlist.restype = _i32
             L.dp_build_nlist.argtypes = [_vp, _vp, _vp, _vp, _i64, _dbl]
             L.dp_format_nlist.restype = _i32
@@ -272,6 +276,15 @@ class Context:
     @property
     def launches(self):
         return int(lib().dp_ctx_launches(self._h))
+
+    def set_embed_store(self, on):
+        """dp_ctx_set_embed_store: keep G and dG/ds of every row between the
+        forward and the backward (on) or recompute them (off)."""
+        _check(lib().dp_ctx_set_embed_store(self._h, int(bool(on))))
+
+    @property
+    def embed_store(self):
+        return bool(lib().dp_ctx_embed_store(self._h) == 1)
 
     def set_timing(self, on):
         _check(lib().dp_ctx_set_timing(self._h, int(bool(on))))

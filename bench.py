@@ -68,16 +68,27 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 DF_FP32_INST_PER_FMA = 10
 FORCE_RMSE_TARGET = 1e-3   # eV/A, against the FP64 full model
 
-# Per-kernel counters from one ncu capture, reported only while the kernel
-# source is the one captured (hash of the .cu file and the shared header):
-#   bytes_per_launch  dram__bytes_read.sum + dram__bytes_write.sum
+# Per-kernel counters from one ncu capture of one evaluation of the 12,288-atom
+# water box (bench.py --workload water12288 --profile-eval 1, 1,046,154 real
+# neighbour rows), reported only while the kernel source is the one captured
+# (hash of the .cu file and the shared header):
+#   bytes_per_row     (dram__bytes_read.sum + dram__bytes_write.sum) / rows: the
+#                     traffic of a launch grows with its rows (G and dG/ds rows,
+#                     per-atom T, D and dE/dD at ~91 rows per atom), so the bench
+#                     reports bytes_per_row x the rows of its own launch
 #   fp64_flop_per_row 2 x dfma + dadd + dmul thread instructions
 #                     (smsp__sass_thread_inst_executed_op_d{fma,add,mul}_pred_on.sum)
 #                     per real neighbour row
+#   pipe_busy         sm__inst_executed_pipe_fp64 share of the active cycles
+PROFILE_ROWS = 1046154
 TRAFFIC = {
-    "embed_bwd": {"bytes_per_launch": 206.925056e6 + 21.675264e6, "file": "embed_x.cu", "src_sha": "4954f89e6792262d"},
-    "embed_bwd_mx<25>": {"bytes_per_launch": 204.772096e6 + 16.526848e6, "file": "mixed.cu", "src_sha": "8933a8cc793ba857"},
-    "embed_bwd_mx<25, split>": {"bytes_per_launch": 204.763904e6 + 17.992704e6, "file": "mixed.cu",
+    "embed_tan": {"bytes_per_row": (10.062592e6 + 1811.035136e6) / PROFILE_ROWS, "file": "embed_x.cu",
+                  "src_sha": "258215490136614b"},
+    "embed_bwd_st": {"bytes_per_row": (1883.308288e6 + 28.450304e6) / PROFILE_ROWS, "file": "embed_x.cu",
+                     "src_sha": "258215490136614b"},
+    "embed_bwd_mx<25>": {"bytes_per_row": (204.772096e6 + 16.526848e6) / PROFILE_ROWS, "file": "mixed.cu",
+                         "src_sha": "8933a8cc793ba857"},
+    "embed_bwd_mx<25, split>": {"bytes_per_row": (204.763904e6 + 17.992704e6) / PROFILE_ROWS, "file": "mixed.cu",
                                 "src_sha": "8933a8cc793ba857"},
 }
 # Pipe shares of the mixed embedding kernels (ncu, one evaluation of the
@@ -91,11 +102,13 @@ MODE_PIPES = {
                                 "file": "mixed.cu", "src_sha": "8933a8cc793ba857"},
 }
 FP64_ISSUED = {
-    # ncu on one evaluation of the 12,288-atom water box (bench.py --workload
-    # water12288 --profile-eval 1), 1,046,154 real rows: dfma 2.434e9, dadd
-    # 1.289e9, dmul 0.566e9 thread instructions; FP64 pipe busy 45.0%
-    "embed_bwd": {"fp64_flop_per_row": 6425.5, "pipe_busy": 0.450, "file": "embed_x.cu",
-                  "src_sha": "4954f89e6792262d"},
+    # k_embed_tan_x<25>: dfma 2.257e9, dadd 0.818e9, dmul 0.106e9 thread
+    # instructions; FP64 pipe busy 41.2% (issue active 24.3%)
+    "embed_tan": {"fp64_flop_per_row": (2 * 2.257052574e9 + 0.817909986e9 + 0.105703644e9) / PROFILE_ROWS,
+                  "pipe_busy": 0.412, "file": "embed_x.cu", "src_sha": "258215490136614b"},
+    # k_embed_bwd_st<25>: dfma 1.070e9, dadd 0.100e9, dmul 0.044e9; FP64 pipe busy 94.4%
+    "embed_bwd_st": {"fp64_flop_per_row": (2 * 1.069532688e9 + 0.099939616e9 + 0.043622898e9) / PROFILE_ROWS,
+                     "pipe_busy": 0.944, "file": "embed_x.cu", "src_sha": "258215490136614b"},
 }
 
 
@@ -450,7 +463,6 @@ def measure_mode(args, dp, w, run_desc, run_P, ref_model, v0, dev, world, flush,
     wl = WORKLOADS[args.workload]
     N = len(v0)
     model = dp.Model(run_desc, run_P)
-    refc = dp.Context(ref_model, N)
     x = torch.tensor(w["coords"], dtype=torch.float64, device=dev)
     v = torch.tensor(v0, dtype=torch.float64, device=dev)
     t = torch.tensor(w["types"], dtype=torch.int32, device=dev)
@@ -462,6 +474,9 @@ def measure_mode(args, dp, w, run_desc, run_P, ref_model, v0, dev, world, flush,
         ctx = fp.fast
     else:
         ctx = dp.Context(model, N, precision=prec)
+    # after the fast path's FP64 context, which then takes the G store first when device memory
+    # holds only one (its checks run inside the timed region)
+    refc = dp.Context(ref_model, N)
     acc_first = _accuracy(dp, ctx, refc, x, t, w["box"])
     dp.dp_md_reset(ctx)
     done = 0
@@ -522,7 +537,7 @@ def measure_mode(args, dp, w, run_desc, run_P, ref_model, v0, dev, world, flush,
     if dom in fl:
         tag = f"{dom}_mx<{run_desc['emb'][0]}" + (", split>" if prec == dp.DP_PREC_MIXED_SPLIT else ">")
         tr = _counter(TRAFFIC, tag)
-        roof = _mode_roofline(fl, groups, dom, tag, tr["bytes_per_launch"] if tr else None)
+        roof = _mode_roofline(fl, groups, dom, tag, tr["bytes_per_row"] * rows if tr else None)
     out = {"value": world * N * wl["md_per_step"] * args.steps / (total_ms / 1000.0), "unit": METRIC,
            "ms_per_step": total_ms / args.steps, "dtype": dtype,
            "model": "se_a %s / M2 %d / fit %s" % ("-".join(map(str, run_desc["emb"])), run_desc["m2"],
@@ -568,7 +583,7 @@ def fp64_roofline(desc, groups, dom, rows, nreal, N, store=False):
     tr = _counter(TRAFFIC, key)
     issued = _counter(FP64_ISSUED, key)
     equiv = flops[dom] / per_launch_s / 1e12 if dom in flops else None
-    roof = {"bound": "alu", "kernel": key, "unit": "TFLOP/s", "traffic": tr["bytes_per_launch"] if tr else None,
+    roof = {"bound": "alu", "kernel": key, "unit": "TFLOP/s", "traffic": tr["bytes_per_row"] * rows if tr else None,
             "rows_per_launch": rows,
             "fp64_equivalent": {"achieved": equiv, "peak": FP64_PEAK_TFLOPS,
                                 "frac": equiv / FP64_PEAK_TFLOPS if equiv else None,
@@ -593,6 +608,22 @@ def fp64_roofline(desc, groups, dom, rows, nreal, N, store=False):
         roof.update(achieved=equiv, peak=FP64_PEAK_TFLOPS, frac=equiv / FP64_PEAK_TFLOPS if equiv else None,
                     peak_source="FP64 pipe: 152 SMs x 2 FMA/clk x 2 FLOP x 2.07 GHz (nominal 1.25 TFLOP/s)",
                     note="FP64-equivalent rate (no ncu count of the issued FP64 FLOPs for this source)")
+    if store and dom == "embed_fwd" and groups.get("embed_bwd", {}).get("launches"):
+        # the streaming backward beside it: FP64 work issued, and its G / dG/ds reads against HBM
+        bs = groups["embed_bwd"]["ms"] / groups["embed_bwd"]["launches"] / 1000.0
+        iss = _counter(FP64_ISSUED, "embed_bwd_st")
+        trb = _counter(TRAFFIC, "embed_bwd_st")
+        other = {"kernel": "embed_bwd_st", "ms_per_launch": bs * 1e3}
+        if iss:
+            a = iss["fp64_flop_per_row"] * rows / bs / 1e12
+            other["fp64_pipe"] = {"achieved": a, "peak": FP64_PEAK_TFLOPS, "frac": a / FP64_PEAK_TFLOPS,
+                                  "busy_ncu": iss["pipe_busy"], "unit": "TFLOP/s"}
+        if trb:
+            gbs = trb["bytes_per_row"] * rows / bs / 1e9
+            other["hbm"] = {"achieved": gbs, "peak": measured_peaks().get("hbm_gbs", 6712.6),
+                            "frac": gbs / measured_peaks().get("hbm_gbs", 6712.6), "unit": "GB/s",
+                            "traffic": trb["bytes_per_row"] * rows}
+        roof["backward"] = other
     return roof
 
 
@@ -750,6 +781,9 @@ def run_ours(args, rank, world, local_rank):
             "config": workload_config(args.workload, w, world),
             "gpu_launches": launches,
             "roofline": roof,
+            "embed_store": {"on": bool(store),
+                            "what": "G and dG/ds of every real row kept in HBM between the embedding forward "
+                                    "(k_embed_tan_x) and the streaming backward (k_embed_bwd_st)"},
             "kernels_ms_per_step": {g: d["ms"] / args.steps for g, d in timed_groups.items()},
             "nve": {"etot_first": float(etot[0]), "etot_last": float(etot[-1]),
                     "max_abs_drift_eV_per_atom": float(np.abs(etot - etot[0]).max() / N),

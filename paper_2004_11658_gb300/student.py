@@ -214,8 +214,10 @@ class FastPathMD:
     def __init__(self, full_model, student_model, natoms_max, tol=1e-3, check_every=10,
                  precision=dp.DP_PREC_MIXED):
         self.fast = dp.Context(student_model, natoms_max, precision=precision)
+        # one FP64 context serves the checks and, after a switch, the MD run (no check follows a
+        # switch; dp_md_reset at the switch clears what the checks left in it)
         self.full = dp.Context(full_model, natoms_max)
-        self.refc = dp.Context(full_model, natoms_max)
+        self.refc = self.full
         self.tol = float(tol)
         self.check_every = int(check_every)
         self.on_full = False

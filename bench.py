@@ -369,13 +369,21 @@ def run_reference(args, rank, world):
 
 # ------------------------------------------------------------------ ours --
 
-def mixed_kernel_flops(desc, rows, natoms):
+def mixed_kernel_flops(desc, rows, natoms, store=False):
     """Per-launch work of the mixed-precision kernels, split by unit:
     tensor-core FLOPs (BF16 GEMMs, unpadded), the per-row contractions with
     R~ and dE/dT (double-float arithmetic on the FP32 pipe) and the per-atom
-    FP64 FLOPs (D = T_<^T T forward, dE/dT backward)."""
+    FP64 FLOPs (D = T_<^T T forward, dE/dT backward).  store: G and dG/ds
+    kept between the two (k_embed_tan_mx evaluates the GEMMs with the
+    s-tangent, k_embed_bwd_stmx only the contractions)."""
     M, m2 = desc["emb"][-1], desc["m2"]
     g = emb_row_flops(desc) - 2 * desc["emb"][0]   # layer 0 runs on the CUDA cores
+    if store:
+        return {
+            "embed_fwd": {"tensor": rows * 2 * g, "df": rows * 8 * M, "fp64": natoms * 8 * m2 * M},
+            "embed_bwd": {"tensor": 0, "df": rows * 16 * M, "fp64": natoms * 16 * m2 * M},
+            "fit": {"tensor": natoms * 2 * fit_atom_flops(desc), "df": 0, "fp64": 0},
+        }
     return {
         "embed_fwd": {"tensor": rows * g, "df": rows * 8 * M, "fp64": natoms * 8 * m2 * M},
         "embed_bwd": {"tensor": rows * 2 * g, "df": rows * 16 * M, "fp64": natoms * 16 * m2 * M},
@@ -474,6 +482,7 @@ def measure_mode(args, dp, w, run_desc, run_P, ref_model, v0, dev, world, flush,
         ctx = fp.fast
     else:
         ctx = dp.Context(model, N, precision=prec)
+    store = ctx.embed_store
     # after the fast path's FP64 context, which then takes the G store first when device memory
     # holds only one (its checks run inside the timed region)
     refc = dp.Context(ref_model, N)
@@ -530,12 +539,13 @@ def measure_mode(args, dp, w, run_desc, run_P, ref_model, v0, dev, world, flush,
         done += n
     last_ctx = fp.context if fast_path else ctx
     acc_last = _accuracy(dp, last_ctx, refc, x, t, w["box"])
-    fl = mixed_kernel_flops(run_desc, rows, N)
+    fl = mixed_kernel_flops(run_desc, rows, N, store)
     groups = {g: {"ms": ms, "launches": n} for g, (ms, n) in kt.items() if n > 0}
     dom = max(groups, key=lambda g: groups[g]["ms"])
     roof = None
     if dom in fl:
-        tag = f"{dom}_mx<{run_desc['emb'][0]}" + (", split>" if prec == dp.DP_PREC_MIXED_SPLIT else ">")
+        kname = fp64_kernel_key(dom, store)   # embed_tan / embed_bwd_st with the store
+        tag = f"{kname}_mx<{run_desc['emb'][0]}" + (", split>" if prec == dp.DP_PREC_MIXED_SPLIT else ">")
         tr = _counter(TRAFFIC, tag)
         roof = _mode_roofline(fl, groups, dom, tag, tr["bytes_per_row"] * rows if tr else None)
     out = {"value": world * N * wl["md_per_step"] * args.steps / (total_ms / 1000.0), "unit": METRIC,
@@ -544,6 +554,7 @@ def measure_mode(args, dp, w, run_desc, run_P, ref_model, v0, dev, world, flush,
                                                    "x".join(map(str, run_desc["fit"]))),
            "kernels_ms_per_step": {g: d["ms"] / args.steps for g, d in groups.items()},
            "roofline": roof,
+           "embed_store": bool(store),
            "accuracy_vs_fp64_full_model": {"target_force_rmse_eV_per_A": FORCE_RMSE_TARGET,
                                            "first_config": acc_first,
                                            "last_config": dict(acc_last, md_step=done)}}

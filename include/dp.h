@@ -169,17 +169,19 @@ dp_status dp_ctx_create(const dp_model *model, int64_t natoms_max, int32_t cand_
                         int32_t precision, void *stream, dp_ctx **out);
 void dp_ctx_free(dp_ctx *ctx);
 
-/* FP64 contexts of the tensor-core embedding kernels (3-layer doubling nets,
- * s_1 in {16, 25, 32}): the back-propagation of Sec. 2 (Eq. embedding through
+/* FP64 contexts of the tensor-core embedding kernels and mixed-precision
+ * contexts with plain BF16 operands (DP_PREC_MIXED), 3-layer doubling nets with
+ * s_1 in {16, 25, 32}: the back-propagation of Sec. 2 (Eq. embedding through
  * the chain rule of the environment matrix, Sec. 3.2) needs, for every real
  * neighbour row, G and its derivative dG/ds with respect to the row's s(r).
  * With the store on, the forward computes both once and keeps them in device
- * memory (natoms_max * N_m * 2 * M doubles: 86.8 GB for 393,216 water atoms
- * with N_m = 138, M = 100), and the backward reads them instead of evaluating
- * the embedding net a second time; off, the backward recomputes them.  Both
- * give the same energy, forces and virial up to the order of the sums over
- * the M features.  dp_ctx_create turns the store on when it takes at most half
- * of the device memory free at that moment.  on = 1 allocates it
+ * memory (natoms_max * N_m * 2 * M values, FP64 or FP32 as the context
+ * computes them: 86.8 / 43.4 GB for 393,216 water atoms with N_m = 138,
+ * M = 100), and the backward reads them instead of evaluating the embedding
+ * net a second time; off, the backward recomputes them.  Both give the same
+ * atomic energies, and forces and virial equal up to the order of the sums
+ * over the M features.  dp_ctx_create turns the store on when it takes at most
+ * half of the device memory free at that moment.  on = 1 allocates it
  * (DP_ERR_NOMEM if that fails, the context unchanged), on = 0 frees it;
  * DP_ERR_UNSUPPORTED for other contexts when on = 1.  Synchronises the
  * context's stream.  dp_ctx_embed_store returns 1 when the store is on, 0

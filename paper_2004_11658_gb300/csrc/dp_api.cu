@@ -560,7 +560,10 @@ dp_status enqueue_eval(dp_ctx *c, const double *coords, const int32_t *types, co
         if (!mixed && c->use_ex && (s = ensure_ex(c))) return s;
         {
             GroupTimer tm(c, G_EMBED_FWD);
-            e = mixed       ? dp_launch_embed_fwd_mx(c->stream, c->m, c->mx, coords, types, b, n, c->fb, c->nb,
+            e = mixed && c->eb.Gmx
+                    ? dp_launch_embed_tan_mx(c->stream, c->m, c->mx, coords, types, b, n, c->fb, c->nb, c->eb,
+                                             c->num_sms, c->d_status, &c->launches)
+                : mixed     ? dp_launch_embed_fwd_mx(c->stream, c->m, c->mx, coords, types, b, n, c->fb, c->nb,
                                                      c->eb, c->num_sms, c->d_status, &c->launches)
                 : c->use_ex && c->eb.Gst
                     ? dp_launch_embed_tan_x(c->stream, c->m, c->d_ex_w, coords, types, b, n, c->fb, c->nb, c->eb,
@@ -583,7 +586,10 @@ dp_status enqueue_eval(dp_ctx *c, const double *coords, const int32_t *types, co
         }
         {
             GroupTimer tm(c, G_EMBED_BWD);
-            e = mixed       ? dp_launch_embed_bwd_mx(c->stream, c->m, c->mx, coords, types, b, n, c->fb, c->nb,
+            e = mixed && c->eb.Gmx
+                    ? dp_launch_embed_bwd_stmx(c->stream, c->m, coords, types, b, n, c->fb, c->eb, c->num_sms,
+                                               &c->launches)
+                : mixed     ? dp_launch_embed_bwd_mx(c->stream, c->m, c->mx, coords, types, b, n, c->fb, c->nb,
                                                      c->eb, c->num_sms, c->d_status, &c->launches)
                 : c->use_ex && c->eb.Gst
                     ? dp_launch_embed_bwd_st(c->stream, c->m, coords, types, b, n, c->fb, c->eb, c->num_sms,
@@ -915,7 +921,7 @@ void dp_ctx_free(dp_ctx *c)
                     c->eb.fit_t, c->eb.fit_h, c->d_p32, c->d_emb_ops, c->d_fit_fwd, c->d_fit_bwd,
                     c->pb.dT, c->pb.dD, c->pb.Db, c->pb.dDb, c->pb.fit_scr, c->pb.rowscr, c->pb.slices,
                     c->d_oz_w, c->d_oz_e, c->ob.a, c->ob.aexp, c->ob.t, c->ob.h, c->ob.g, c->d_dtile, c->d_ex_w,
-                    c->eb.Gst};
+                    c->eb.Gst, c->eb.Gmx};
     for (void *p : bufs) dev_free(p);
     delete c;
 }
@@ -1003,6 +1009,18 @@ dp_status dp_ctx_create(const dp_model *model, int64_t natoms_max, int32_t cand_
         }
         cudaGetLastError();
     }
+    // G and dG/ds (FP32) stored by the mixed forward (plain BF16 operands), on the same rule
+    if (!s && precision == DP_PREC_MIXED) {
+        size_t fr = 0, tot = 0;
+        const size_t gb = dp_mx_store_bytes(c->m, (int64_t)N);
+        if (cudaMemGetInfo(&fr, &tot) == cudaSuccess && gb <= fr / 2) {
+            if (cudaMalloc((void **)&c->eb.Gmx, gb) != cudaSuccess) {
+                c->eb.Gmx = nullptr;
+                cudaGetLastError();
+            }
+        }
+        cudaGetLastError();
+    }
     // the split mixed mode runs its fitting net as exact products of 28-bit digit
     // expansions (FP32-level accuracy, a quarter of the FP64 plans' MMAs)
     if ((precision == DP_PREC_FP64 || precision == DP_PREC_MIXED_SPLIT) &&
@@ -1052,19 +1070,28 @@ dp_status dp_ctx_create(const dp_model *model, int64_t natoms_max, int32_t cand_
 dp_status dp_ctx_set_embed_store(dp_ctx *c, int32_t on)
 {
     if (!c) return fail(DP_ERR_ARG, "context is NULL");
-    if (on && !c->use_ex) return fail(DP_ERR_UNSUPPORTED, "the store needs an FP64 context of the tensor-core "
-                                                          "embedding kernels");
-    if ((on != 0) == (c->eb.Gst != nullptr)) return DP_OK;
+    const bool mx = c->precision == DP_PREC_MIXED;
+    if (on && !c->use_ex && !mx)
+        return fail(DP_ERR_UNSUPPORTED, "the store needs an FP64 context of the tensor-core embedding kernels "
+                                        "or a mixed-precision context with plain BF16 operands");
+    const bool have = c->eb.Gst != nullptr || c->eb.Gmx != nullptr;
+    if ((on != 0) == have) return DP_OK;
     DP_CUDA(cudaStreamSynchronize(c->stream), "dp_ctx_set_embed_store");
     if (!on) {
         dev_free(c->eb.Gst);
+        dev_free(c->eb.Gmx);
         c->eb.Gst = nullptr;
+        c->eb.Gmx = nullptr;
         return DP_OK;
     }
+    if (mx) return dev_alloc(&c->eb.Gmx, dp_mx_store_bytes(c->m, c->natoms_max) / sizeof(float), "G and dG/ds rows");
     return dev_alloc(&c->eb.Gst, dp_ex_store_bytes(c->m, c->natoms_max) / sizeof(double), "G and dG/ds rows");
 }
 
-int32_t dp_ctx_embed_store(const dp_ctx *c) { return c ? (c->eb.Gst != nullptr ? 1 : 0) : -1; }
+int32_t dp_ctx_embed_store(const dp_ctx *c)
+{
+    return c ? ((c->eb.Gst != nullptr || c->eb.Gmx != nullptr) ? 1 : 0) : -1;
+}
 
 dp_status dp_ctx_set_sync(dp_ctx *c, int32_t sync)
 {

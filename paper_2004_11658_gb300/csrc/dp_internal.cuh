@@ -194,6 +194,7 @@ struct EvalBuffers {
     float *fit_t;      // mixed mode: tanh values of the fitting layers [tile][n_fit][256][128]
     float *fit_h;      // mixed mode: fitting activation / gradient [tile][256][128]
     double *Gst;       // FP64 mode, when it fits: G and dG/ds of every neighbour slot [N nm][2 M]
+    float *Gmx;        // mixed mode (plain BF16), when it fits: the same in FP32
 };
 
 // Mixed-precision operands: BF16 copies of the weight matrices in the
@@ -305,6 +306,16 @@ cudaError_t dp_launch_embed_bwd_st(cudaStream_t st, const DevModel &m, const dou
                                    int64_t *launches);
 
 // Mixed precision (BF16 tensor-core GEMMs, FP64 environment / contractions).
+// The tangent forward storing G and dG/ds (FP32) in eb.Gmx (bytes for natoms
+// atoms: dp_mx_store_bytes) and the streaming backward that reads them.
+size_t dp_mx_store_bytes(const DevModel &m, int64_t natoms);
+cudaError_t dp_launch_embed_tan_mx(cudaStream_t st, const DevModel &m, const MixedModel &mx, const double *x,
+                                   const int32_t *types, Box3 box, int N, const FormatBuffers &fb,
+                                   const NlistBuffers &nb, EvalBuffers eb, int num_sms, int32_t *status,
+                                   int64_t *launches);
+cudaError_t dp_launch_embed_bwd_stmx(cudaStream_t st, const DevModel &m, const double *x, const int32_t *types,
+                                     Box3 box, int N, const FormatBuffers &fb, EvalBuffers eb, int num_sms,
+                                     int64_t *launches);
 cudaError_t dp_launch_embed_fwd_mx(cudaStream_t st, const DevModel &m, const MixedModel &mx, const double *x,
                                    const int32_t *types, Box3 box, int N, const FormatBuffers &fb,
                                    const NlistBuffers &nb, EvalBuffers eb, int num_sms, int32_t *status,

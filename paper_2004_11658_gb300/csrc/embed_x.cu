@@ -1354,12 +1354,22 @@ __global__ void __launch_bounds__(STW * 32, 4) k_embed_bwd_st(DevModel m, const 
         for (int p = lane; p < 4 * E3; p += 32) Ts[p] = Tin[(size_t)i * 4 * E3 + p];
         __syncwarp();
         {
+            // the 4 M2 long sums first, two per lane with every lane busy (two chains each), then
+            // every entry's M2 short terms on top of them
             const double *g = gD + (size_t)i * m2 * E3;
+            for (int p = lane; p < 4 * m2; p += 32) {
+                const int cc = p / m2, xx = p - cc * m2;
+                double acc = 0.0, acc2 = 0.0;
+                for (int b2 = 0; b2 < E3; b2 += 2) {  // E3 = 4 e1 is even
+                    acc = fma(g[xx * E3 + b2], Ts[cc * E3 + b2], acc);
+                    acc2 = fma(g[xx * E3 + b2 + 1], Ts[cc * E3 + b2 + 1], acc2);
+                }
+                gTw[cc * E3 + xx] = acc + acc2;
+            }
+            __syncwarp();
             for (int p = lane; p < 4 * E3; p += 32) {
                 const int cc = p / E3, xx = p - cc * E3;
-                double acc = 0.0;
-                if (xx < m2)
-                    for (int b2 = 0; b2 < E3; ++b2) acc = fma(g[xx * E3 + b2], Ts[cc * E3 + b2], acc);
+                double acc = xx < m2 ? gTw[p] : 0.0;
                 for (int a2 = 0; a2 < m2; ++a2) acc = fma(g[a2 * E3 + xx], Ts[cc * E3 + a2], acc);
                 gTw[p] = acc * m.desc_scale;
             }

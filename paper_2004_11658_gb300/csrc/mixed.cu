@@ -460,20 +460,32 @@ __global__ void __launch_bounds__(MXT, 1) k_embed_fwd_mx(
     if (warp == 0) tc::tmem_dealloc(tbase, TCOLS);
 }
 
-template <int E1, bool SPLIT>
-__global__ void __launch_bounds__(MXT, 1) k_embed_bwd_mx(
-    DevModel m, MixedModel mx, const double *__restrict__ x, const int32_t *__restrict__ types, Box3 box, int N,
-    const int32_t *__restrict__ type_perm, const int32_t *__restrict__ type_start, const int32_t *__restrict__ nlist,
-    const int32_t *__restrict__ nreal, const double *__restrict__ Tin, const double *__restrict__ gD,
-    double *__restrict__ pair_g, double *__restrict__ f_own, double *__restrict__ vir_part, int32_t *status)
+// Atoms per batch of the tangent forward (its T sums take [AB][4][M] doubles of
+// shared memory; two CTAs per SM for every width).
+constexpr int tan_ab(int e1) { return e1 >= 32 ? 4 : AB_MAX; }
+
+// TAN = false: the backward (k_embed_bwd_mx).  TAN = true (plain BF16
+// operands only): the forward with the s-tangent (k_embed_tan_mx): the same
+// value and tangent products, but the last epilogue stores G and dG/ds of each
+// row in HBM (Gsto: [N nm][2 M] floats, slot i nm + sel_off[b] + r) and
+// accumulates T = R~^T G in double-float arithmetic as k_embed_fwd_mx does;
+// the batch's T and D = T_<^T T leave as in k_embed_fwd_mx.
+template <int E1, bool SPLIT, bool TAN>
+__device__ __forceinline__ void embed_mx_tangent_body(
+    const DevModel &m, const MixedModel &mx, const double *__restrict__ x, const int32_t *__restrict__ types,
+    Box3 box, int N, const int32_t *__restrict__ type_perm, const int32_t *__restrict__ type_start,
+    const int32_t *__restrict__ nlist, const int32_t *__restrict__ nreal, double *__restrict__ Tio,
+    const double *__restrict__ gD, double *__restrict__ pair_g, double *__restrict__ f_own,
+    double *__restrict__ vir_part, double *__restrict__ Dout, float *__restrict__ Gsto, int32_t *status)
 {
+    static_assert(!(TAN && SPLIT), "the tangent forward takes plain BF16 operands");
     using S = EmbShape<E1>;
     constexpr int E2 = S::E2, E3 = S::E3, K1p = S::K1p, N1p = S::N1p, K2p = S::K2p, N2p = S::N2p;
     constexpr int TOFF = N2p;                 // tangent accumulator column offset
     constexpr int TCOLS = tcols_for(2 * N2p);
     using P = EmbPlan<E1, SPLIT>;
     constexpr int X = P::X;                   // operand copies: high (and low) parts
-    constexpr int AB = P::AB;
+    constexpr int AB = TAN ? tan_ab(E1) : P::AB;
     extern __shared__ __align__(1024) unsigned char smraw[];
     unsigned char *A0 = smraw + P::BA0;
     unsigned char *dA0 = smraw + P::BdA0;
@@ -486,6 +498,16 @@ __global__ void __launch_bounds__(MXT, 1) k_embed_bwd_mx(
     double *facc = red + 4 * 12;                             // [AB][12]
     float *gTh = reinterpret_cast<float *>(facc + AB * 12);  // [AB][4][E3], scaled: gT = gTh + gTl
     float *gTl = gTh + AB * 4 * E3;
+    // TAN, in the same place: per-warp T partials of one tile, the batch's T sums, R~ parts
+    double *Tw = reinterpret_cast<double *>(smraw + P::BEND);  // [4][4][E3]
+    double *Tacc = Tw + 4 * 4 * E3;                           // [AB][4][E3]
+    float *Rth = reinterpret_cast<float *>(Tacc + AB * 4 * E3);  // [4][32][4]: R~ = Rth + Rtl
+    float *Rtl = Rth + 4 * 32 * 4;
+    // and G of 16 features x 32 rows per warp ([4][32][17]) in the layer-2 row operands A1, dA1
+    // (contiguous with plain operands), idle once their MMAs are done
+    float *Gt = reinterpret_cast<float *>(A1);
+    static_assert(!TAN || (P::BdA1 == P::BA1 + S::A1B && 4 * 32 * 17 * sizeof(float) <= 2 * (size_t)S::A1B),
+                  "the G staging fits in A1, dA1");
     // dE/dD of one atom [M2][E3] in the operand buffers, when it fits there
     double *gds = reinterpret_cast<double *>(smraw);
     const bool gd_fits = (size_t)m.m2 * E3 * sizeof(double) <= P::BFREE;
@@ -513,13 +535,16 @@ __global__ void __launch_bounds__(MXT, 1) k_embed_bwd_mx(
         const int k = batch_size(first, hi, tstart, T, AB, a);
         __syncthreads();
         if (tid < AB) bi.ids[tid] = tid < k ? type_perm[first + tid] : 0;
-        for (int q = tid; q < AB * 12; q += MXT) facc[q] = 0.0;
+        if constexpr (TAN)
+            for (int q = tid; q < AB * 4 * E3; q += MXT) Tacc[q] = 0.0;
+        else
+            for (int q = tid; q < AB * 12; q += MXT) facc[q] = 0.0;
         __syncthreads();
         // gT[c][x] = [x < M2] sum_b gD[x][b] T[c][b] + sum_{a<M2} gD[a][x] T[c][a], times the scale
         // (dE/dD of the atom staged in the operand buffers, idle between tiles, when it fits)
-        for (int j = 0; j < k; ++j) {
+        for (int j = 0; j < (TAN ? 0 : k); ++j) {
             const int i = bi.ids[j];
-            for (int p = tid; p < 4 * E3; p += MXT) Ts[p] = Tin[(size_t)i * 4 * E3 + p];
+            for (int p = tid; p < 4 * E3; p += MXT) Ts[p] = Tio[(size_t)i * 4 * E3 + p];
             const double *gd = gD + (size_t)i * m2 * E3;
             if (gd_fits) {
                 const double2 *src = reinterpret_cast<const double2 *>(gd);
@@ -650,6 +675,71 @@ __global__ void __launch_bounds__(MXT, 1) k_embed_bwd_mx(
                     tc::mma_commit(&mbar);
                 }
                 alive = tc_wait(&mbar, phase, status);
+                if constexpr (TAN) {
+                // epilogue 2: G and dG/ds of the row to HBM (16-byte stores, 16 features at a time);
+                // the warp's partial of T = R~^T G in double-float arithmetic, as k_embed_fwd_mx
+                if (alive && warp_live) {
+                    float *Gw = Gt + warp * 32 * 17;
+                    float *Rwh = Rth + warp * 32 * 4, *Rwl = Rtl + warp * 32 * 4;
+                    double *Tww = Tw + warp * 4 * E3;
+                    float *gro = Gsto + ((size_t)i * nm + slot) * (2 * E3);
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) df_split(valid ? gg.R[c] : 0.0, Rwh[lane * 4 + c], Rwl[lane * 4 + c]);
+#pragma unroll
+                    for (int cc = 0; cc < N2p; cc += 16) {
+                        float v[16], dv[16], Gv[16], dGv[16];
+                        tc::tmem_ld16(tlane + cc, v);
+                        tc::tmem_ld16(tlane + TOFF + cc, dv);
+#pragma unroll
+                        for (int q = 0; q < 16; ++q) {
+                            const int o = cc + q;
+                            Gv[q] = 0.f;
+                            dGv[q] = 0.f;
+                            if (o < E3 && valid) {
+                                const int os = o < E2 ? o : o - E2;
+                                const float t = tanhf(v[q] + b2[o]);
+                                Gv[q] = h1[os] + t;
+                                dGv[q] = fmaf(fmaf(-t, t, 1.f), dv[q], dh1[os]);
+                            }
+                            Gw[lane * 17 + q] = Gv[q];
+                        }
+                        if (valid) {
+                            // E3 = 4 e1: a group of 4 features is wholly inside or wholly outside
+#pragma unroll
+                            for (int q = 0; q < 16; q += 4)
+                                if (cc + q < E3) {
+                                    *reinterpret_cast<float4 *>(gro + cc + q) =
+                                        make_float4(Gv[q], Gv[q + 1], Gv[q + 2], Gv[q + 3]);
+                                    *reinterpret_cast<float4 *>(gro + E3 + cc + q) =
+                                        make_float4(dGv[q], dGv[q + 1], dGv[q + 2], dGv[q + 3]);
+                                }
+                        }
+                        __syncwarp();
+#pragma unroll
+                        for (int u = 0; u < 2; ++u) {
+                            const int p = lane + 32 * u, c = p >> 4, q = p & 15, o = cc + q;
+                            if (o < E3) {
+                                float sh = 0.f, sl = 0.f;
+#pragma unroll 8
+                                for (int rr = 0; rr < 32; ++rr)
+                                    df_fma(sh, sl, Gw[rr * 17 + q], Rwh[rr * 4 + c], Rwl[rr * 4 + c]);
+                                Tww[c * E3 + o] = df_value(sh, sl);
+                            }
+                        }
+                        __syncwarp();
+                    }
+                }
+                tc_sync();
+                // merge the tile's warp partials into the atoms' sums, warps in order
+                if (alive) {
+                    for (int p = tid; p < 4 * E3; p += MXT) {
+#pragma unroll
+                        for (int w = 0; w < 4; ++w)
+                            if (t0 + w < G) Tacc[bi.grp_atom[t0 + w] * 4 * E3 + p] += Tw[w * 4 * E3 + p];
+                    }
+                }
+                __syncthreads();
+                } else {
                 // epilogue 2: G, dG/ds and the contractions with gT of the row's atom in
                 // double-float arithmetic (exact products with gT's FP32 parts)
                 double fo[3] = {0.0, 0.0, 0.0}, vir[9];
@@ -743,20 +833,250 @@ __global__ void __launch_bounds__(MXT, 1) k_embed_bwd_mx(
                         if (t0 + w < G) facc[bi.grp_atom[t0 + w] * 12 + tid] += red[w * 12 + tid];
                 }
                 __syncthreads();
+                }
             }
         }
         if (!alive) break;
-        for (int q = tid; q < k * 12; q += MXT) {
-            const int j = q / 12, c = q - j * 12;
-            const int i = bi.ids[j];
-            if (c < 3) f_own[(size_t)i * 3 + c] = facc[q];
-            else vir_part[(size_t)i * 9 + c - 3] = facc[q];
+        if constexpr (TAN) {
+            // T = scale * sum; D = T_<^T T, per atom of the batch (as k_embed_fwd_mx)
+            const int nd = m2 * E3;
+            for (int j = 0; j < k; ++j) {
+                const int i = bi.ids[j];
+                double *Tj = Tacc + j * 4 * E3;
+                for (int p = tid; p < 4 * E3; p += MXT) {
+                    const double v = Tj[p] * m.desc_scale;
+                    Tj[p] = v;
+                    Tio[(size_t)i * 4 * E3 + p] = v;
+                }
+                __syncthreads();
+                for (int q = tid; q < nd; q += MXT) {
+                    const int a2 = q / E3, b2i = q - a2 * E3;
+                    double acc = Tj[a2] * Tj[b2i];
+                    acc = fma(Tj[E3 + a2], Tj[E3 + b2i], acc);
+                    acc = fma(Tj[2 * E3 + a2], Tj[2 * E3 + b2i], acc);
+                    acc = fma(Tj[3 * E3 + a2], Tj[3 * E3 + b2i], acc);
+                    Dout[(size_t)i * nd + q] = acc;
+                }
+            }
+        } else {
+            for (int q = tid; q < k * 12; q += MXT) {
+                const int j = q / 12, c = q - j * 12;
+                const int i = bi.ids[j];
+                if (c < 3) f_own[(size_t)i * 3 + c] = facc[q];
+                else vir_part[(size_t)i * 9 + c - 3] = facc[q];
+            }
         }
         first += k;
     }
     if (!alive) tc::mbar_wait(&mbar, phase ^ 1u);
     tc_sync();
     if (warp == 0) tc::tmem_dealloc(tbase, TCOLS);
+}
+
+template <int E1, bool SPLIT>
+__global__ void __launch_bounds__(MXT, 1) k_embed_bwd_mx(
+    DevModel m, MixedModel mx, const double *__restrict__ x, const int32_t *__restrict__ types, Box3 box, int N,
+    const int32_t *__restrict__ type_perm, const int32_t *__restrict__ type_start, const int32_t *__restrict__ nlist,
+    const int32_t *__restrict__ nreal, double *__restrict__ Tin, const double *__restrict__ gD,
+    double *__restrict__ pair_g, double *__restrict__ f_own, double *__restrict__ vir_part, int32_t *status)
+{
+    embed_mx_tangent_body<E1, SPLIT, false>(m, mx, x, types, box, N, type_perm, type_start, nlist, nreal, Tin, gD,
+                                            pair_g, f_own, vir_part, nullptr, nullptr, status);
+}
+
+template <int E1>
+__global__ void __launch_bounds__(MXT, 1) k_embed_tan_mx(
+    DevModel m, MixedModel mx, const double *__restrict__ x, const int32_t *__restrict__ types, Box3 box, int N,
+    const int32_t *__restrict__ type_perm, const int32_t *__restrict__ type_start, const int32_t *__restrict__ nlist,
+    const int32_t *__restrict__ nreal, double *__restrict__ Tout, double *__restrict__ Dout,
+    float *__restrict__ Gsto, int32_t *status)
+{
+    embed_mx_tangent_body<E1, false, true>(m, mx, x, types, box, N, type_perm, type_start, nlist, nreal, Tout,
+                                           nullptr, nullptr, nullptr, nullptr, Dout, Gsto, status);
+}
+
+// Error-free sum of two double-float numbers: (h, l) += (h2, l2).
+__device__ __forceinline__ void df_add(float &h, float &l, float h2, float l2)
+{
+    const float s = __fadd_rn(h, h2);
+    const float z = __fsub_rn(s, h);
+    const float err = __fadd_rn(__fsub_rn(h, __fsub_rn(s, z)), __fsub_rn(h2, z));
+    h = s;
+    l = __fadd_rn(l, __fadd_rn(l2, err));
+}
+
+// ------------------------------------------------------ streaming backward --
+//
+// k_embed_bwd_stmx: the mixed backward once k_embed_tan_mx has stored G and
+// dG/ds (FP32) of every real row.  One warp per atom: dE/dT in FP64 (as
+// k_embed_bwd_mx), split into two FP32 parts; the atom's real rows 32 at a
+// time, lane q on the geometry of row q; in 8 steps of 4 rows, 8 lanes per
+// row form sum_f G[f] gT[c][f] and sum_f dG[f] gT[c][f] in double-float
+// arithmetic over the features u, u + 8, ... (exact products with gT's parts),
+// a transposing shuffle tree of error-free double-float sums leaves component
+// u on lane u, and the row's lane applies the chain rule through R~(r_ij) in
+// FP64.  Fixed summation order: bit-reproducible.
+constexpr int SMW = 4;  // warps (atoms in flight) per CTA
+
+template <int E1>
+__global__ void __launch_bounds__(SMW * 32, 4) k_embed_bwd_stmx(
+    DevModel m, const double *__restrict__ x, const int32_t *__restrict__ types, Box3 box, int N,
+    const int32_t *__restrict__ nlist, const int32_t *__restrict__ nreal, const double *__restrict__ Tin,
+    const double *__restrict__ gD, const float *__restrict__ Gsto, double *__restrict__ pair_g,
+    double *__restrict__ f_own, double *__restrict__ vir_part)
+{
+    constexpr int E3 = 4 * E1, KF = (E3 + 7) / 8;
+    static_assert(4 * E3 >= 32 * 8, "the row sums [32][8] fit in the T buffer");
+    // per warp: R1 holds T of the atom, then dE/dT as FP32 parts (gth, gtl); R2 holds dE/dT in
+    // FP64 while it is formed, then the row sums [32][8]
+    __shared__ double R1sh[SMW][4 * E3];
+    __shared__ double R2sh[SMW][4 * E3];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int sub = lane & 7, gq = lane >> 3;
+    const int T = m.ntypes, nm = m.nm, m2 = m.m2;
+    double *Ts = R1sh[w], *gTd = R2sh[w], *sa_s = R2sh[w];
+    float *gth = reinterpret_cast<float *>(R1sh[w]), *gtl = gth + 4 * E3;
+
+    for (int i = blockIdx.x * SMW + w; i < N; i += gridDim.x * SMW) {
+        const int a = types[i];
+        const bool a_ok = (unsigned)a < (unsigned)T;
+        for (int p = lane; p < 4 * E3; p += 32) Ts[p] = Tin[(size_t)i * 4 * E3 + p];
+        __syncwarp();
+        {
+            // the 4 M2 long sums first, two per lane with every lane busy (two chains each), then
+            // every entry's M2 short terms on top of them; then the FP32 parts over T
+            const double *gd = gD + (size_t)i * m2 * E3;
+            for (int p = lane; p < 4 * m2; p += 32) {
+                const int cc = p / m2, xx = p - cc * m2;
+                double acc = 0.0, acc2 = 0.0;
+                for (int b2i = 0; b2i < E3; b2i += 2) {  // E3 = 4 e1 is even
+                    acc = fma(gd[xx * E3 + b2i], Ts[cc * E3 + b2i], acc);
+                    acc2 = fma(gd[xx * E3 + b2i + 1], Ts[cc * E3 + b2i + 1], acc2);
+                }
+                gTd[cc * E3 + xx] = acc + acc2;
+            }
+            __syncwarp();
+            for (int p = lane; p < 4 * E3; p += 32) {
+                const int cc = p / E3, xx = p - cc * E3;
+                double acc = xx < m2 ? gTd[p] : 0.0;
+                for (int a2 = 0; a2 < m2; ++a2) acc = fma(gd[a2 * E3 + xx], Ts[cc * E3 + a2], acc);
+                gTd[p] = acc * m.desc_scale;
+            }
+            __syncwarp();
+            for (int p = lane; p < 4 * E3; p += 32) df_split(gTd[p], gth[p], gtl[p]);
+        }
+        __syncwarp();
+        int nr = 0;
+        if (a_ok)
+            for (int b = 0; b < T; ++b) nr += nreal[(size_t)i * T + b];
+        const double xi[3] = {x[3 * i], x[3 * i + 1], x[3 * i + 2]};
+        double fo[3] = {0.0, 0.0, 0.0}, vir[9];
+#pragma unroll
+        for (int q = 0; q < 9; ++q) vir[q] = 0.0;
+        for (int q0 = 0; q0 < nr; q0 += 32) {
+            // row q0 + lane: its slot (type block and rank) and geometry
+            int slot = -1;
+            if (q0 + lane < nr) {
+                int rem = q0 + lane;
+                for (int b = 0; b < T; ++b) {
+                    const int nb = nreal[(size_t)i * T + b];
+                    if (slot < 0 && rem < nb) slot = m.sel_off[b] + rem;
+                    rem -= nb;
+                }
+            }
+            RowGeo gg;
+            gg.s = gg.ds = 0.0;
+            gg.R[0] = gg.R[1] = gg.R[2] = gg.R[3] = 0.0;
+            gg.d[0] = gg.d[1] = gg.d[2] = 0.0;
+            gg.r = 1.0;
+            if (slot >= 0) geometry(m, x, xi, nlist[(size_t)i * nm + slot], box, gg);
+            // the 8 sums of rows q0 + 4 it + gq, 8 lanes per row
+            for (int it = 0; it < 8 && q0 + 4 * it < nr; ++it) {
+                const int sl = __shfl_sync(0xffffffffu, slot, 4 * it + gq);
+                float ph[8], pl[8];
+#pragma unroll
+                for (int c = 0; c < 8; ++c) ph[c] = pl[c] = 0.f;
+                if (sl >= 0) {
+                    const float *gr = Gsto + ((size_t)i * nm + sl) * (2 * E3);
+#pragma unroll
+                    for (int k = 0; k < KF; ++k) {
+                        const int ff = sub + 8 * k;
+                        if (8 * k + 8 <= E3 || ff < E3) {
+                            const float G = gr[ff], dG = gr[E3 + ff];
+#pragma unroll
+                            for (int c = 0; c < 4; ++c) {
+                                const float bh = gth[c * E3 + ff], bl = gtl[c * E3 + ff];
+                                df_fma(ph[c], pl[c], G, bh, bl);
+                                df_fma(ph[4 + c], pl[4 + c], dG, bh, bl);
+                            }
+                        }
+                    }
+                }
+                // transposing tree over the row's 8 lanes: lane u ends with component u
+#pragma unroll
+                for (int o = 4, n = 4; o >= 1; o >>= 1, n >>= 1) {
+                    const bool up = (sub & o) != 0;
+#pragma unroll
+                    for (int k = 0; k < n; ++k) {
+                        const float sh = up ? ph[k] : ph[n + k], sl2 = up ? pl[k] : pl[n + k];
+                        float kh = up ? ph[n + k] : ph[k], kl = up ? pl[n + k] : pl[k];
+                        const float rh = __shfl_xor_sync(0xffffffffu, sh, o);
+                        const float rl = __shfl_xor_sync(0xffffffffu, sl2, o);
+                        df_add(kh, kl, rh, rl);
+                        ph[k] = kh;
+                        pl[k] = kl;
+                    }
+                }
+                sa_s[(4 * it + gq) * 8 + sub] = df_value(ph[0], pl[0]);
+            }
+            __syncwarp();
+            // chain rule through R~(r_ij) in FP64, lane q on row q0 + q
+            if (slot >= 0) {
+                double ra[4], rb[4];
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    ra[c] = sa_s[lane * 8 + c];
+                    rb[c] = sa_s[lane * 8 + 4 + c];
+                }
+                double gR0 = ra[0];
+#pragma unroll
+                for (int c = 0; c < 4; ++c) gR0 = fma(gg.R[c], rb[c], gR0);
+                const double inv = 1.0 / gg.r;
+                const double u[3] = {gg.d[0] * inv, gg.d[1] * inv, gg.d[2] * inv};
+                const double dot = ra[1] * u[0] + ra[2] * u[1] + ra[3] * u[2];
+                const double sr = gg.s * inv;
+                const double coef = gR0 * gg.ds + gg.ds * dot - sr * dot;
+                double gv[3];
+#pragma unroll
+                for (int bb = 0; bb < 3; ++bb) gv[bb] = fma(u[bb], coef, sr * ra[1 + bb]);
+                double *pg = pair_g + ((size_t)i * nm + slot) * 3;
+                pg[0] = gv[0];
+                pg[1] = gv[1];
+                pg[2] = gv[2];
+#pragma unroll
+                for (int aa = 0; aa < 3; ++aa) {
+                    fo[aa] += gv[aa];
+#pragma unroll
+                    for (int bb = 0; bb < 3; ++bb) vir[aa * 3 + bb] -= gg.d[aa] * gv[bb];
+                }
+            }
+            __syncwarp();
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+#pragma unroll
+            for (int q = 0; q < 3; ++q) fo[q] += __shfl_xor_sync(0xffffffffu, fo[q], off);
+#pragma unroll
+            for (int q = 0; q < 9; ++q) vir[q] += __shfl_xor_sync(0xffffffffu, vir[q], off);
+        }
+        if (lane == 0) {
+#pragma unroll
+            for (int q = 0; q < 3; ++q) f_own[(size_t)i * 3 + q] = fo[q];
+#pragma unroll
+            for (int q = 0; q < 9; ++q) vir_part[(size_t)i * 9 + q] = vir[q];
+        }
+        __syncwarp();
+    }
 }
 
 // ----------------------------------------------------------------- fitting --
@@ -1093,6 +1413,14 @@ size_t bwd_smem()
     return P::BEND + sizeof(double) * (4 * S::E3 + 48 + P::AB * 12) + sizeof(float) * 2 * P::AB * 4 * S::E3;
 }
 
+template <int E1>
+size_t tan_smem()
+{
+    using S = EmbShape<E1>;
+    using P = EmbPlan<E1, false>;
+    return P::BEND + sizeof(double) * (4 * 4 * S::E3 + tan_ab(E1) * 4 * S::E3) + sizeof(float) * 2 * 4 * 32 * 4;
+}
+
 // CTAs per SM that fit next to each other (shared memory; a 1 KB reserve per CTA)
 inline int ctas_per_sm(size_t smem) { return 2 * (smem + 2048) <= 232448 ? 2 : 1; }
 
@@ -1139,7 +1467,71 @@ cudaError_t launch_bwd(cudaStream_t st, const DevModel &m, const MixedModel &mx,
     return cudaGetLastError();
 }
 
+template <int E1>
+cudaError_t launch_tan(cudaStream_t st, const DevModel &m, const MixedModel &mx, const double *x,
+                       const int32_t *types, Box3 box, int N, const FormatBuffers &fb, const NlistBuffers &nb,
+                       EvalBuffers eb, int num_sms, int32_t *status)
+{
+    const size_t smem = tan_smem<E1>();
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(k_embed_tan_mx<E1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    int grid = ctas_per_sm(smem) * num_sms;
+    if (grid > (N + 7) / 8) grid = (N + 7) / 8;
+    k_embed_tan_mx<E1><<<grid, MXT, smem, st>>>(m, mx, x, types, box, N, nb.type_perm, nb.type_start, fb.nlist,
+                                                fb.nreal, eb.T, eb.D, eb.Gmx, status);
+    return cudaGetLastError();
+}
+
+template <int E1>
+cudaError_t launch_bwd_stmx(cudaStream_t st, const DevModel &m, const double *x, const int32_t *types, Box3 box,
+                            int N, const FormatBuffers &fb, EvalBuffers eb, int num_sms)
+{
+    int grid = (N + SMW - 1) / SMW;
+    if (grid > 4 * num_sms) grid = 4 * num_sms;
+    if (grid < 1) grid = 1;
+    k_embed_bwd_stmx<E1><<<grid, SMW * 32, 0, st>>>(m, x, types, box, N, fb.nlist, fb.nreal, eb.T, eb.gD, eb.Gmx,
+                                                    eb.pair_g, eb.f_own, eb.vir_part);
+    return cudaGetLastError();
+}
+
 }  // namespace
+
+size_t dp_mx_store_bytes(const DevModel &m, int64_t natoms)
+{
+    return (size_t)natoms * (size_t)m.nm * 2 * (size_t)m.M * sizeof(float);
+}
+
+cudaError_t dp_launch_embed_tan_mx(cudaStream_t st, const DevModel &m, const MixedModel &mx, const double *x,
+                                   const int32_t *types, Box3 box, int N, const FormatBuffers &fb,
+                                   const NlistBuffers &nb, EvalBuffers eb, int num_sms, int32_t *status,
+                                   int64_t *launches)
+{
+    *launches += 1;
+    if (mx.split) return cudaErrorInvalidValue;
+    switch (m.emb[0]) {
+    case 16: return launch_tan<16>(st, m, mx, x, types, box, N, fb, nb, eb, num_sms, status);
+    case 25: return launch_tan<25>(st, m, mx, x, types, box, N, fb, nb, eb, num_sms, status);
+    case 32: return launch_tan<32>(st, m, mx, x, types, box, N, fb, nb, eb, num_sms, status);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t dp_launch_embed_bwd_stmx(cudaStream_t st, const DevModel &m, const double *x, const int32_t *types,
+                                     Box3 box, int N, const FormatBuffers &fb, EvalBuffers eb, int num_sms,
+                                     int64_t *launches)
+{
+    *launches += 1;
+    switch (m.emb[0]) {
+    case 16: return launch_bwd_stmx<16>(st, m, x, types, box, N, fb, eb, num_sms);
+    case 25: return launch_bwd_stmx<25>(st, m, x, types, box, N, fb, eb, num_sms);
+    case 32: return launch_bwd_stmx<32>(st, m, x, types, box, N, fb, eb, num_sms);
+    default: return cudaErrorInvalidValue;
+    }
+}
 
 bool dp_mixed_supported(const DevModel &m)
 {

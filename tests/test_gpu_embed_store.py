@@ -100,8 +100,8 @@ def test_store_and_recompute_agree_at_full_size(dp, synth):
 
 def test_store_switch(dp, synth):
     """On/off/on on an FP64 context; DP_ERR_UNSUPPORTED for contexts whose
-    kernels have no store (mixed precision, FP64 units only), which keep
-    working."""
+    kernels have no store (split-operand mixed precision, FP64 units only),
+    which keep working."""
     w = system(synth, "water648")
     d = w["model"]
     model = dp.Model(d, synth.model_params(d, 0))
@@ -115,7 +115,7 @@ def test_store_switch(dp, synth):
         assert ctx.embed_store == on
         g = evaluate(dp, ctx, x, t, w["box"])
         assert rel(g["force"], ref["force"]) < 1e-13
-    for prec in (dp.DP_PREC_MIXED, dp.DP_PREC_FP64_SIMT):
+    for prec in (dp.DP_PREC_MIXED_SPLIT, dp.DP_PREC_FP64_SIMT):
         c2 = dp.Context(model, len(w["coords"]), precision=prec)
         assert not c2.embed_store
         with pytest.raises(dp.DPError) as ei:
@@ -125,3 +125,44 @@ def test_store_switch(dp, synth):
         dp.dp_build_nlist(c2, x, t, w["box"], 0.0)
         g = evaluate(dp, c2, x, t, w["box"])
         assert np.isfinite(g["force"]).all()
+
+
+# mixed precision (plain BF16 operands): G and dG/ds kept in FP32
+@pytest.mark.parametrize("name,student", [("water648", False), ("cu864", False), ("water648", True)])
+def test_mixed_store_and_recompute(dp, oracle, synth, name, student):
+    """k_embed_tan_mx + k_embed_bwd_stmx against k_embed_fwd_mx +
+    k_embed_bwd_mx: the same forward (atomic energies to rounding; the same
+    FP32 G in both), the backward's double-float sums in another order
+    (forces and virial to 1e-11 relative), and both within the mixed bars of
+    the FP64 oracle (relative force RMSE in plain BF16: <= 1e-2 for the water
+    model, 5e-2 for the student widths, measured 2.4e-2 on this machine, and
+    1e-1 for copper)."""
+    w = system(synth, name)
+    d = synth.WATER_STUDENT if student else w["model"]
+    P = synth.model_params(d, 0)
+    o = oracle.evaluate(d, P, w["coords"], w["types"], w["box"])
+    model = dp.Model(d, P)
+    ctx = dp.Context(model, len(w["coords"]), precision=dp.DP_PREC_MIXED)
+    assert ctx.embed_store
+    x = torch.tensor(w["coords"], dtype=torch.float64, device="cuda")
+    t = torch.tensor(w["types"], dtype=torch.int32, device="cuda")
+    dp.dp_build_nlist(ctx, x, t, w["box"], 2.0)
+    gs = evaluate(dp, ctx, x, t, w["box"])
+    gs2 = evaluate(dp, ctx, x, t, w["box"])
+    for k in ("energy", "force", "virial", "atom_energy"):
+        np.testing.assert_array_equal(gs[k], gs2[k])  # deterministic
+    ctx.set_embed_store(False)
+    assert not ctx.embed_store
+    gr = evaluate(dp, ctx, x, t, w["box"])
+    assert rel(gs["atom_energy"], gr["atom_energy"]) < 1e-14
+    assert rel(gs["force"], gr["force"]) < 1e-11
+    assert rel(gs["virial"], gr["virial"]) < 1e-11
+    bar = 1e-1 if name == "cu864" else (5e-2 if student else 1e-2)
+    for g in (gs, gr):
+        dF = g["force"] - o["force"]
+        relrmse = np.sqrt((dF ** 2).mean()) / np.sqrt((o["force"] ** 2).mean())
+        assert relrmse < bar, relrmse
+    ctx.set_embed_store(True)
+    assert ctx.embed_store
+    g3 = evaluate(dp, ctx, x, t, w["box"])
+    np.testing.assert_array_equal(g3["force"], gs["force"])

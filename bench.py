@@ -82,12 +82,14 @@ FORCE_RMSE_TARGET = 1e-3   # eV/A, against the FP64 full model
 #   pipe_busy         sm__inst_executed_pipe_fp64 share of the active cycles
 PROFILE_ROWS = 1046154
 TRAFFIC = {
-    "embed_tan": {"bytes_per_row": (10.062592e6 + 1811.035136e6) / PROFILE_ROWS, "file": "embed_x.cu",
-                  "src_sha": "258215490136614b"},
-    "embed_bwd_st": {"bytes_per_row": (1883.308288e6 + 28.450304e6) / PROFILE_ROWS, "file": "embed_x.cu",
-                     "src_sha": "258215490136614b"},
-    "embed_bwd_mx<25>": {"bytes_per_row": (204.772096e6 + 16.526848e6) / PROFILE_ROWS, "file": "mixed.cu",
-                         "src_sha": "8933a8cc793ba857"},
+    "embed_tan<25>": {"bytes_per_row": (10.468352e6 + 1811.331840e6) / PROFILE_ROWS, "file": "embed_x.cu",
+                      "src_sha": "bb7b71ebf4d4cf67"},
+    "embed_bwd_st<25>": {"bytes_per_row": (1883.360000e6 + 28.511232e6) / PROFILE_ROWS, "file": "embed_x.cu",
+                         "src_sha": "bb7b71ebf4d4cf67"},
+    "embed_tan_mx<25>": {"bytes_per_row": (49.605120e6 + 1008.945408e6) / PROFILE_ROWS, "file": "mixed.cu",
+                         "src_sha": "2e0166635493a3b1"},
+    "embed_bwd_st_mx<25>": {"bytes_per_row": (1043.964160e6 + 26.513920e6) / PROFILE_ROWS, "file": "mixed.cu",
+                            "src_sha": "2e0166635493a3b1"},
     "embed_bwd_mx<25, split>": {"bytes_per_row": (204.763904e6 + 17.992704e6) / PROFILE_ROWS, "file": "mixed.cu",
                                 "src_sha": "8933a8cc793ba857"},
 }
@@ -96,19 +98,21 @@ TRAFFIC = {
 # busy fractions of the FP64, FP32 (fma), integer (alu) and tensor pipes and
 # the schedulers' issue-active share.
 MODE_PIPES = {
-    "embed_bwd_mx<25>": {"fp64": 0.480, "fma": 0.190, "alu": 0.085, "tensor": 0.010, "issue_active": 0.311,
-                         "file": "mixed.cu", "src_sha": "8933a8cc793ba857"},
+    "embed_tan_mx<25>": {"fp64": 0.386, "fma": 0.196, "alu": 0.087, "tensor": 0.016, "issue_active": 0.333,
+                         "file": "mixed.cu", "src_sha": "2e0166635493a3b1"},
+    "embed_bwd_st_mx<25>": {"fp64": 0.689, "fma": 0.282, "alu": 0.041, "tensor": 0.0, "issue_active": 0.406,
+                            "file": "mixed.cu", "src_sha": "2e0166635493a3b1"},
     "embed_bwd_mx<25, split>": {"fp64": 0.448, "fma": 0.180, "alu": 0.094, "tensor": 0.028, "issue_active": 0.302,
                                 "file": "mixed.cu", "src_sha": "8933a8cc793ba857"},
 }
 FP64_ISSUED = {
     # k_embed_tan_x<25>: dfma 2.257e9, dadd 0.818e9, dmul 0.106e9 thread
     # instructions; FP64 pipe busy 41.2% (issue active 24.3%)
-    "embed_tan": {"fp64_flop_per_row": (2 * 2.257052574e9 + 0.817909986e9 + 0.105703644e9) / PROFILE_ROWS,
-                  "pipe_busy": 0.412, "file": "embed_x.cu", "src_sha": "258215490136614b"},
-    # k_embed_bwd_st<25>: dfma 1.070e9, dadd 0.100e9, dmul 0.044e9; FP64 pipe busy 94.4%
-    "embed_bwd_st": {"fp64_flop_per_row": (2 * 1.069532688e9 + 0.099939616e9 + 0.043622898e9) / PROFILE_ROWS,
-                     "pipe_busy": 0.944, "file": "embed_x.cu", "src_sha": "258215490136614b"},
+    "embed_tan<25>": {"fp64_flop_per_row": (2 * 2.257052574e9 + 0.817909986e9 + 0.105703644e9) / PROFILE_ROWS,
+                      "pipe_busy": 0.412, "file": "embed_x.cu", "src_sha": "bb7b71ebf4d4cf67"},
+    # k_embed_bwd_st<25>: dfma 1.070e9, dadd 0.101e9, dmul 0.044e9; FP64 pipe busy 93.9%
+    "embed_bwd_st<25>": {"fp64_flop_per_row": (2 * 1.069532688e9 + 0.100726048e9 + 0.043622898e9) / PROFILE_ROWS,
+                         "pipe_busy": 0.939, "file": "embed_x.cu", "src_sha": "bb7b71ebf4d4cf67"},
 }
 
 
@@ -590,7 +594,9 @@ def fp64_roofline(desc, groups, dom, rows, nreal, N, store=False):
     per_launch_s = groups[dom]["ms"] / groups[dom]["launches"] / 1000.0
     pk = measured_peaks()
     bf16_peak = pk.get("bf16_tflops_sustained", pk.get("bf16_tflops", 1720.9))
-    key = fp64_kernel_key(dom, store)
+    # counters are per kernel instantiation (the embedding width e1); other widths report the
+    # FP64-equivalent rate only
+    key = fp64_kernel_key(dom, store) + f"<{desc['emb'][0]}>"
     tr = _counter(TRAFFIC, key)
     issued = _counter(FP64_ISSUED, key)
     equiv = flops[dom] / per_launch_s / 1e12 if dom in flops else None
@@ -622,9 +628,10 @@ def fp64_roofline(desc, groups, dom, rows, nreal, N, store=False):
     if store and dom == "embed_fwd" and groups.get("embed_bwd", {}).get("launches"):
         # the streaming backward beside it: FP64 work issued, and its G / dG/ds reads against HBM
         bs = groups["embed_bwd"]["ms"] / groups["embed_bwd"]["launches"] / 1000.0
-        iss = _counter(FP64_ISSUED, "embed_bwd_st")
-        trb = _counter(TRAFFIC, "embed_bwd_st")
-        other = {"kernel": "embed_bwd_st", "ms_per_launch": bs * 1e3}
+        kb = f"embed_bwd_st<{desc['emb'][0]}>"
+        iss = _counter(FP64_ISSUED, kb)
+        trb = _counter(TRAFFIC, kb)
+        other = {"kernel": kb, "ms_per_launch": bs * 1e3}
         if iss:
             a = iss["fp64_flop_per_row"] * rows / bs / 1e12
             other["fp64_pipe"] = {"achieved": a, "peak": FP64_PEAK_TFLOPS, "frac": a / FP64_PEAK_TFLOPS,

@@ -54,6 +54,33 @@ def test_roofline_flop_counts_per_unit():
     assert b.kernel_flops(cu, rows=1, natoms=0)["embed_bwd"] == 43136
 
 
+def test_store_flop_counts_and_counter_keys():
+    """With G and dG/ds kept between the two embedding kernels the forward
+    does the net with its s-tangent (two passes of the GEMMs) and T, the
+    backward only the contractions with dE/dT; the sum over both equals the
+    recompute path's minus one embedding pass.  The ncu counter tables are
+    looked up per kernel instantiation (embedding width)."""
+    from paper_2004_11658_gb300 import synth
+    b = _bench_module()
+    w = synth.WATER_MODEL
+    st = b.kernel_flops(w, rows=1, natoms=0, store=True)
+    rc = b.kernel_flops(w, rows=1, natoms=0, store=False)
+    assert st["embed_fwd"] == 2 * 12550 + 8 * 100
+    assert st["embed_bwd"] == 16 * 100
+    assert st["embed_fwd"] + st["embed_bwd"] == rc["embed_fwd"] + rc["embed_bwd"] - 12550
+    assert b.kernel_flops(w, rows=0, natoms=1, store=True) == b.kernel_flops(w, rows=0, natoms=1)
+    mx = b.mixed_kernel_flops(w, rows=1, natoms=0, store=True)
+    assert mx["embed_bwd"]["tensor"] == 0 and mx["embed_fwd"]["tensor"] == 2 * (12550 - 50)
+    assert b.fp64_kernel_key("embed_fwd", True) == "embed_tan"
+    assert b.fp64_kernel_key("embed_bwd", True) == "embed_bwd_st"
+    assert b.fp64_kernel_key("embed_bwd", False) == "embed_bwd"
+    assert b.fp64_kernel_key("fit", True) == "fit"
+    for table in (b.TRAFFIC, b.FP64_ISSUED, b.MODE_PIPES):
+        for key, entry in table.items():
+            assert key.endswith(">"), key  # one entry per instantiation
+            assert entry["file"] in ("embed_x.cu", "mixed.cu")
+
+
 def test_reference_arm_under_torchrun_two_ranks():
     """Launched as the multi-GPU bench is (torchrun, two ranks): rank 0 alone
     prints the reference line, the other rank exits 0 without work."""

@@ -83,13 +83,13 @@ FORCE_RMSE_TARGET = 1e-3   # eV/A, against the FP64 full model
 PROFILE_ROWS = 1046154
 TRAFFIC = {
     "embed_tan<25>": {"bytes_per_row": (10.468352e6 + 1811.331840e6) / PROFILE_ROWS, "file": "embed_x.cu",
-                      "src_sha": "bb7b71ebf4d4cf67"},
+                      "src_sha": "c2c89c84fd00c488"},
     "embed_bwd_st<25>": {"bytes_per_row": (1883.360000e6 + 28.511232e6) / PROFILE_ROWS, "file": "embed_x.cu",
-                         "src_sha": "bb7b71ebf4d4cf67"},
+                         "src_sha": "c2c89c84fd00c488"},
     "embed_tan_mx<25>": {"bytes_per_row": (49.605120e6 + 1008.945408e6) / PROFILE_ROWS, "file": "mixed.cu",
-                         "src_sha": "2e0166635493a3b1"},
+                         "src_sha": "bd0c7271cc3b2bf4"},
     "embed_bwd_st_mx<25>": {"bytes_per_row": (1043.964160e6 + 26.513920e6) / PROFILE_ROWS, "file": "mixed.cu",
-                            "src_sha": "2e0166635493a3b1"},
+                            "src_sha": "bd0c7271cc3b2bf4"},
     "embed_bwd_mx<25, split>": {"bytes_per_row": (204.763904e6 + 17.992704e6) / PROFILE_ROWS, "file": "mixed.cu",
                                 "src_sha": "8933a8cc793ba857"},
 }
@@ -99,9 +99,9 @@ TRAFFIC = {
 # the schedulers' issue-active share.
 MODE_PIPES = {
     "embed_tan_mx<25>": {"fp64": 0.386, "fma": 0.196, "alu": 0.087, "tensor": 0.016, "issue_active": 0.333,
-                         "file": "mixed.cu", "src_sha": "2e0166635493a3b1"},
+                         "file": "mixed.cu", "src_sha": "bd0c7271cc3b2bf4"},
     "embed_bwd_st_mx<25>": {"fp64": 0.689, "fma": 0.282, "alu": 0.041, "tensor": 0.0, "issue_active": 0.406,
-                            "file": "mixed.cu", "src_sha": "2e0166635493a3b1"},
+                            "file": "mixed.cu", "src_sha": "bd0c7271cc3b2bf4"},
     "embed_bwd_mx<25, split>": {"fp64": 0.448, "fma": 0.180, "alu": 0.094, "tensor": 0.028, "issue_active": 0.302,
                                 "file": "mixed.cu", "src_sha": "8933a8cc793ba857"},
 }
@@ -109,10 +109,10 @@ FP64_ISSUED = {
     # k_embed_tan_x<25>: dfma 2.257e9, dadd 0.818e9, dmul 0.106e9 thread
     # instructions; FP64 pipe busy 41.2% (issue active 24.3%)
     "embed_tan<25>": {"fp64_flop_per_row": (2 * 2.257052574e9 + 0.817909986e9 + 0.105703644e9) / PROFILE_ROWS,
-                      "pipe_busy": 0.412, "file": "embed_x.cu", "src_sha": "bb7b71ebf4d4cf67"},
+                      "pipe_busy": 0.412, "file": "embed_x.cu", "src_sha": "c2c89c84fd00c488"},
     # k_embed_bwd_st<25>: dfma 1.070e9, dadd 0.101e9, dmul 0.044e9; FP64 pipe busy 93.9%
     "embed_bwd_st<25>": {"fp64_flop_per_row": (2 * 1.069532688e9 + 0.100726048e9 + 0.043622898e9) / PROFILE_ROWS,
-                         "pipe_busy": 0.939, "file": "embed_x.cu", "src_sha": "bb7b71ebf4d4cf67"},
+                         "pipe_busy": 0.939, "file": "embed_x.cu", "src_sha": "c2c89c84fd00c488"},
 }
 
 

@@ -16,10 +16,14 @@
 // of the 32 rows: it adds the bias, applies the FP64 tanh and the (h1, h1) skip,
 // and accumulates its column of T = R~^T G in registers; layer 1's epilogue
 // (an M = 64 accumulator: 16 lanes of each warp's quarter) writes h1 back as
-// FP64 rows.  One CTA (8 warps) per atom, persistent over the type-sorted
+// FP64 rows.  One CTA (16 warps) per SM, persistent over the type-sorted
 // atoms; the current net's weight digits and column exponents arrive by one
 // bulk copy.  Bounded waits; on a timeout the kernel sets DPF_MMA_TIMEOUT,
 // frees its tensor memory and returns.
+//
+// Kernels: k_embed_fwd_x (G, T, D) and k_embed_bwd_x (G and dG/ds recomputed,
+// contracted with dE/dT) when G is not kept; k_embed_tan_x (G and dG/ds once,
+// stored in HBM, with T and D) and the streaming k_embed_bwd_st when it is.
 #include <algorithm>
 #include <cmath>
 #include <cstring>

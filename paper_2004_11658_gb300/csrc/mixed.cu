@@ -22,6 +22,12 @@
 // CTAs still fit per SM.  That mode runs its fitting net on fit_oz.cu's exact
 // digit kernels, not on k_fit_mx.
 //
+// G store (plain BF16 operands): k_embed_tan_mx evaluates the net with its
+// s-tangent once and keeps G and dG/ds (FP32) of every real row in HBM, with T
+// and D as k_embed_fwd_mx forms them; k_embed_bwd_stmx streams them through the
+// double-float contractions with dE/dT.  Without the store k_embed_bwd_mx
+// recomputes them.
+//
 // Supported shapes: embedding widths (e1, 2 e1, 4 e1) with e1 in {16, 25, 32}
 // (the paper's doubling nets), fitting layers of equal width <= 256 after the
 // first one.  Every wait on the tensor core is bounded; on a timeout the

@@ -90,8 +90,12 @@ TRAFFIC = {
                          "src_sha": "bd0c7271cc3b2bf4"},
     "embed_bwd_st_mx<25>": {"bytes_per_row": (1043.964160e6 + 26.513920e6) / PROFILE_ROWS, "file": "mixed.cu",
                             "src_sha": "bd0c7271cc3b2bf4"},
-    "embed_bwd_mx<25, split>": {"bytes_per_row": (204.763904e6 + 17.992704e6) / PROFILE_ROWS, "file": "mixed.cu",
-                                "src_sha": "8933a8cc793ba857"},
+    "embed_bwd_mx<25, split>": {"bytes_per_row": (204.796928e6 + 17.978880e6) / PROFILE_ROWS, "file": "mixed.cu",
+                                "src_sha": "bd0c7271cc3b2bf4"},
+    "embed_tan_mx<16>": {"bytes_per_row": (7.999488e6 + 603.240704e6) / PROFILE_ROWS, "file": "mixed.cu",
+                         "src_sha": "bd0c7271cc3b2bf4"},
+    "embed_bwd_st_mx<16>": {"bytes_per_row": (669.597440e6 + 25.187072e6) / PROFILE_ROWS, "file": "mixed.cu",
+                            "src_sha": "bd0c7271cc3b2bf4"},
 }
 # Pipe shares of the mixed embedding kernels (ncu, one evaluation of the
 # 12,288-atom water box, --profile-precision mixed / split): active-cycle
@@ -103,7 +107,11 @@ MODE_PIPES = {
     "embed_bwd_st_mx<25>": {"fp64": 0.689, "fma": 0.282, "alu": 0.041, "tensor": 0.0, "issue_active": 0.406,
                             "file": "mixed.cu", "src_sha": "bd0c7271cc3b2bf4"},
     "embed_bwd_mx<25, split>": {"fp64": 0.448, "fma": 0.180, "alu": 0.094, "tensor": 0.028, "issue_active": 0.302,
-                                "file": "mixed.cu", "src_sha": "8933a8cc793ba857"},
+                                "file": "mixed.cu", "src_sha": "bd0c7271cc3b2bf4"},
+    "embed_tan_mx<16>": {"fp64": 0.442, "fma": 0.168, "alu": 0.081, "tensor": 0.006, "issue_active": 0.300,
+                         "file": "mixed.cu", "src_sha": "bd0c7271cc3b2bf4"},
+    "embed_bwd_st_mx<16>": {"fp64": 0.754, "fma": 0.239, "alu": 0.048, "tensor": 0.0, "issue_active": 0.366,
+                            "file": "mixed.cu", "src_sha": "bd0c7271cc3b2bf4"},
 }
 FP64_ISSUED = {
     # k_embed_tan_x<25>: dfma 2.257e9, dadd 0.818e9, dmul 0.106e9 thread

@@ -45,3 +45,7 @@ def test_host_calls(synth):
     h = ctypes.c_void_p()
     assert L.dp_model_create(None, None, 0, ctypes.byref(h)) == -1
     assert L.dp_last_error()
+    # the G-store switch on a NULL context: an argument error, and -1 from the query
+    assert L.dp_ctx_set_embed_store(None, 1) == -1
+    assert L.dp_ctx_set_embed_store(None, 0) == -1
+    assert L.dp_ctx_embed_store(None) == -1

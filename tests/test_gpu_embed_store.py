@@ -166,3 +166,26 @@ def test_mixed_store_and_recompute(dp, oracle, synth, name, student):
     assert ctx.embed_store
     g3 = evaluate(dp, ctx, x, t, w["box"])
     np.testing.assert_array_equal(g3["force"], gs["force"])
+
+
+def test_store_left_off_when_it_does_not_fit(dp, oracle, synth):
+    """dp_ctx_create keeps G and dG/ds only when they take at most half of
+    the free device memory: a copper context for 150,000 atoms (sel 512,
+    M = 128: 157 GB of rows, more than half of a GB300's memory) is created
+    without the store, and evaluates through the recompute kernels."""
+    c, t_, b = synth.copper_fcc(6)
+    d = synth.CU_MODEL
+    P = synth.model_params(d, 0)
+    need = 150000 * sum(d["sel"]) * 2 * d["emb"][-1] * 8
+    free, _ = torch.cuda.mem_get_info()
+    if need <= free // 2:
+        pytest.skip("this device holds the rows")
+    ctx = dp.Context(dp.Model(d, P), 150000)
+    assert not ctx.embed_store
+    x = torch.tensor(c, dtype=torch.float64, device="cuda")
+    t = torch.tensor(t_, dtype=torch.int32, device="cuda")
+    dp.dp_build_nlist(ctx, x, t, b, 0.0)
+    g = evaluate(dp, ctx, x, t, b)
+    o = oracle.evaluate(d, P, c, t_, b)
+    assert rel(g["force"], o["force"]) < TOL
+    ctx.close()
